@@ -1,0 +1,178 @@
+"""Oracle: SPD HSS construction by scaling-and-compression, quadratic cost.
+TEST INFRASTRUCTURE ONLY.
+
+On a dense SPD matrix M (the shifted kernel matrix, or the dense form of an H^2 matrix),
+in tree order, with a given sketch Omega (n x (r+p)).  The steps follow Alg. 4.1 (Sec. 4)
+with the bases of Sec. 5.2.1 (randomized, Alg. 5.1, applied to Lambda_{ii^c} Omega):
+
+leaf level (k = 1)
+  A_ii = S_i S_i^T (Cholesky), Lambda_i Omega = S_i^{-1} Y_i^(1),  Y^(k) = (M - blkdiag_k M) Omega
+  V_i = first r_i columns of Q from the pivoted QR of Lambda_i Omega
+  Phi_i = V_i^T S_i^{-1} (explicit r_i x |I_i| matrix), U_i = S_i V_i
+  B_ij = Phi_i M_ij Phi_j^T for ALL i != j in lvl(1)          (Eq. bij_hss)
+levels k = 2 .. L-1
+  bold B_ii from the children's B (zero diagonal blocks), (I + bold B_ii)^{+-1/2} by a
+  symmetric eigendecomposition (Eq. Si0)
+  Lambda_i Omega = (I + bold B_ii)^{-1/2} diag(Phi_children) Y_i^(k)
+  Vbar_i from its pivoted QR, Phi_i = Vbar_i^T (I + bold B_ii)^{-1/2} diag(Phi_children) (Eq. phi)
+  R_i = (I + bold B_ii)^{1/2} Vbar_i                          (Eq. Rik)
+  B_ij = Phi_i M_ij Phi_j^T for ALL i != j in lvl(k)
+
+No Type-1 / Type-3 shortcut is used: B_ij always comes from the matrix itself, so the
+accelerated algebra of Sec. 5.2.2 is checked independently.  ``factor="chol"`` replaces
+(I + bold B)^{1/2} by its Cholesky factor L (I + bold B = L L^T); the two differ by an
+orthogonal factor on the right, which column-pivoted QR absorbs, so the assembled HSS
+matrix is the same.  r_i = min(r, rows, numerical rank), the pivoted QR stopping when
+the largest remaining column norm is <= 1e-14 times the first.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+
+from .linalg import pivoted_qr
+from .tree import Tree
+
+RANK_RTOL = 1e-14
+
+
+@dataclass
+class HSS:
+    tree: Tree
+    D: dict = field(default_factory=dict)      # leaf -> dense diagonal block A_ii
+    U: dict = field(default_factory=dict)      # leaf -> U_i (|I_i| x r_i)
+    R: dict = field(default_factory=dict)      # nonleaf (levels 2..L-1) -> R_i (sum r_c x r_i)
+    B: dict = field(default_factory=dict)      # (i, j) -> B_ij for every i != j of a level
+    Phi: dict = field(default_factory=dict)    # node -> explicit Phi_i (r_i x |I_i|)
+    Vbar: dict = field(default_factory=dict)   # leaf: V_i; nonleaf: Vbar_i
+    S: dict = field(default_factory=dict)      # leaf -> Cholesky factor S_i
+    Bbold: dict = field(default_factory=dict)  # nonleaf -> bold B_ii
+    Fhalf: dict = field(default_factory=dict)  # nonleaf -> (I + bold B_ii)^{1/2} or its Cholesky factor
+    rank: dict = field(default_factory=dict)
+
+    def siblings_B(self):
+        """Coefficient matrices of the final HSS form: sibling pairs only."""
+        t = self.tree
+        return {(i, j): b for (i, j), b in self.B.items() if t.parent[i] == t.parent[j]}
+
+
+def sample_products(tree: Tree, M: np.ndarray, Omega: np.ndarray):
+    """Y^(k) = (M - blkdiag_k(M)) Omega for k = 1 .. L-1 (Eq. Yk), literally."""
+    Y = {}
+    full = M @ Omega
+    for k in range(1, tree.L):
+        Yk = full.copy()
+        for i in tree.nodes_at_level(k):
+            b, e = tree.begin[i], tree.end[i]
+            Yk[b:e] -= M[b:e, b:e] @ Omega[b:e]
+        Y[k] = Yk
+    return Y
+
+
+def _sym_power(Bb: np.ndarray, p: float) -> np.ndarray:
+    lam, Q = np.linalg.eigh(Bb)
+    d = 1.0 + lam
+    if np.any(d <= 0.0):
+        raise np.linalg.LinAlgError("I + bold B_ii is not SPD")
+    return (Q * d ** p) @ Q.T
+
+
+def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: str = "eig") -> HSS:
+    hss = HSS(tree)
+    Y = sample_products(tree, M, Omega)
+    Lv = tree.L
+    # leaf level
+    leaves = list(tree.nodes_at_level(1)) if Lv > 1 else [0]
+    for i in leaves:
+        b, e = tree.begin[i], tree.end[i]
+        Aii = M[b:e, b:e]
+        hss.D[i] = Aii.copy()
+        if Lv == 1:
+            break
+        S = np.linalg.cholesky(Aii)
+        lam = sla.solve_triangular(S, Y[1][b:e], lower=True)
+        k, piv, Rq, V = pivoted_qr(lam, r, RANK_RTOL)
+        hss.S[i] = S
+        hss.Vbar[i] = V
+        hss.rank[i] = k
+        hss.Phi[i] = sla.solve_triangular(S, V, lower=True, trans="T").T   # V^T S^{-1}
+        hss.U[i] = S @ V
+    if Lv == 1:
+        return hss
+    _all_pairs_B(hss, M, 1)
+    for k in range(2, Lv):
+        for i in tree.nodes_at_level(k):
+            kids = [int(c) for c in tree.children(i)]
+            rc = [hss.rank[c] for c in kids]
+            off = np.concatenate([[0], np.cumsum(rc)])
+            m = int(off[-1])
+            Bb = np.zeros((m, m))
+            for a, ca in enumerate(kids):
+                for bb, cb in enumerate(kids):
+                    if ca != cb:
+                        Bb[off[a]:off[a + 1], off[bb]:off[bb + 1]] = hss.B[(ca, cb)]
+            b, e = tree.begin[i], tree.end[i]
+            PhiStack = np.zeros((m, e - b))
+            for a, c in enumerate(kids):
+                PhiStack[off[a]:off[a + 1], tree.begin[c] - b:tree.end[c] - b] = hss.Phi[c]
+            if factor == "eig":
+                Fh = _sym_power(Bb, 0.5)
+                Fmh = _sym_power(Bb, -0.5)
+            else:
+                Fh = np.linalg.cholesky(np.eye(m) + Bb)
+                Fmh = sla.solve_triangular(Fh, np.eye(m), lower=True)
+            lam = Fmh @ (PhiStack @ Y[k][b:e])
+            kk, piv, Rq, Vb = pivoted_qr(lam, r, RANK_RTOL)
+            hss.Bbold[i] = Bb
+            hss.Fhalf[i] = Fh
+            hss.Vbar[i] = Vb
+            hss.rank[i] = kk
+            hss.Phi[i] = Vb.T @ Fmh @ PhiStack
+            hss.R[i] = Fh @ Vb
+        _all_pairs_B(hss, M, k)
+    return hss
+
+
+def _all_pairs_B(hss: HSS, M: np.ndarray, k: int) -> None:
+    """B_ij = Phi_i M_ij Phi_j^T for every i != j in lvl(k) (Eq. bij_hss)."""
+    tree = hss.tree
+    nodes = list(tree.nodes_at_level(k))
+    for i in nodes:
+        bi, ei = tree.begin[i], tree.end[i]
+        left = hss.Phi[i] @ M[bi:ei, :]
+        for j in nodes:
+            if i == j:
+                continue
+            bj, ej = tree.begin[j], tree.end[j]
+            hss.B[(i, j)] = left[:, bj:ej] @ hss.Phi[j].T
+
+
+def explicit_U(hss: HSS, i: int) -> np.ndarray:
+    """Full basis of node i, U_i = diag(U_children) R_i (Eq. nested)."""
+    tree = hss.tree
+    if i in hss.U:
+        return hss.U[i]
+    kids = [int(c) for c in tree.children(i)]
+    blocks = [explicit_U(hss, c) for c in kids]
+    Dg = sla.block_diag(*blocks)
+    return Dg @ hss.R[i]
+
+
+def assemble_dense(hss: HSS) -> np.ndarray:
+    """Dense HSS matrix from {A_ii, U_i, R_i, B_ij (siblings)} (Sec. 2, HSS representation)."""
+    tree = hss.tree
+    n = tree.n
+    H = np.zeros((n, n))
+    for i, Dii in hss.D.items():
+        b, e = tree.begin[i], tree.end[i]
+        H[b:e, b:e] = Dii
+    cache = {}
+    for (i, j), Bij in hss.siblings_B().items():
+        for v in (i, j):
+            if v not in cache:
+                cache[v] = explicit_U(hss, v)
+        bi, ei, bj, ej = tree.begin[i], tree.end[i], tree.begin[j], tree.end[j]
+        H[bi:ei, bj:ej] = cache[i] @ Bij @ cache[j].T
+    return H
