@@ -1,0 +1,180 @@
+/*
+ * spdhss.h - C ABI of the GB300 implementation of the SPD HSS preconditioner for
+ * SPD H^2 kernel matrices (Xing, Huang, Chow: "Efficient construction of an HSS
+ * preconditioner for symmetric positive definite H^2 matrices").
+ *
+ * Pipeline (problem statement of Sec. 5.2 and Sec. 6):
+ *   points + kernel + diagonal shift
+ *     -> h2_build      cluster tree, admissibility lists, proxy-point H^2 (Sec. 5.1, Sec. 6)
+ *     -> spdhss_build  SPD HSS by accelerated scaling-and-compression (Alg. 5.3)
+ *     -> ulv_factor    ULV factorization of the SPD HSS matrix (Sec. 1, Sec. 6)
+ *     -> pcg_solve     PCG with the H^2 matvec and the ULV preconditioner (Sec. 6.2)
+ *
+ * Conventions shared by every call:
+ *  - All floating point data is IEEE binary64 (double).
+ *  - Points are row-major n x dim (point p at points[p*dim .. p*dim+dim-1]).
+ *  - Block vectors (right-hand sides, products, sketches) are column-major n x ncol with
+ *    leading dimension ld >= n, and are in the ORIGINAL point order; the library applies
+ *    the tree permutation internally.
+ *  - Unless a call says otherwise, array arguments are device pointers (memory the caller
+ *    allocated with cudaMalloc or a PyTorch CUDA tensor); the caller owns them.  Handles
+ *    own their device memory and release it in the matching *_destroy call.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *    Calls enqueue their kernels on it.  Calls that must size allocations or return
+ *    host results synchronize that stream before returning.
+ *  - Every call returns a status and never exits or traps.  On failure a message is
+ *    available from spdhss_last_error() (thread-local, valid until the next call).
+ *  - Handles are not thread-safe: one handle must not be used by two threads at once.
+ */
+#ifndef SPDHSS_H
+#define SPDHSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPDHSS_OK = 0,
+  SPDHSS_EINVAL = 1,          /* invalid argument (size, pointer, layout) */
+  SPDHSS_ENOMEM = 2,          /* device or host allocation failed */
+  SPDHSS_NOT_SPD = 3,         /* a Cholesky factorization met a non-positive pivot */
+  SPDHSS_NO_CONVERGENCE = 4,  /* PCG reached maxit before the tolerance */
+  SPDHSS_NUMERIC = 5,         /* NaN or Inf met */
+  SPDHSS_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+  SPDHSS_ECUDA = 7            /* a CUDA runtime call failed */
+} spdhss_status;
+
+/* Kernel functions of Sec. 6, with a length scale ell that divides the distance r:
+ * EXP exp(-r/ell); GAUSS exp(-r^2/ell^2); MATERN32 (1+sqrt3 r/ell) exp(-sqrt3 r/ell);
+ * IMQ 1/sqrt(1 + r^2/ell^2).  K(x,x) = 1.  The matrix is A = shift*I + K(X,X). */
+typedef enum {
+  SPDHSS_K_EXP = 0,
+  SPDHSS_K_GAUSS = 1,
+  SPDHSS_K_MATERN32 = 2,
+  SPDHSS_K_IMQ = 3
+} spdhss_kernel_kind;
+
+typedef struct {
+  int kind;       /* spdhss_kernel_kind */
+  double ell;     /* length scale, > 0 */
+  double shift;   /* diagonal shift sigma >= 0 (Sec. 6.2) */
+} spdhss_kernel_desc;
+
+typedef struct spdhss_h2_s* h2_handle;
+typedef struct spdhss_hss_s* hss_handle;
+typedef struct spdhss_ulv_s* ulv_handle;
+
+/* ---- H^2 representation (Sec. 5.1; proxy point construction of Sec. 6) -------------
+ * h2_build: cluster tree (2^dim-ary box bisection until a box holds <= leaf_size points,
+ * shallow leaves padded to the deepest level), admissibility lists (Type-1 near pairs,
+ * Type-3 far pairs of Sec. 5.2.2) and a proxy-point H^2 representation whose
+ * interpolative decompositions stop at relative pivot size `tol` (the paper uses 1e-8).
+ *   points   n x dim row-major, HOST or DEVICE pointer (detected), read only.
+ *   n >= 1, dim in {2, 3}, leaf_size >= 1, tol >= 0 (0 keeps full rank: exact H^2).
+ *   out      receives a new handle; destroy with h2_destroy.
+ * Errors: EINVAL for bad sizes, ENOMEM, ECUDA. */
+spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
+                       int leaf_size, double tol, void* stream, h2_handle* out);
+
+/* Y = A X with the H^2 matrix A (Sec. 5.1): upward pass, Type-3 couplings, downward pass,
+ * and near-field kernel tiles evaluated on the fly (shift included).
+ *   X, Y  device, n x nrhs column-major, leading dimension ld >= n, original point order.
+ *   X and Y must not overlap.  nrhs >= 1. */
+spdhss_status h2_matmul(h2_handle h2, const double* X, double* Y, int nrhs, int64_t ld,
+                        void* stream);
+
+/* Sizes of the tree and the H^2 data, written to the HOST array info[16]:
+ *  [0] n  [1] dim  [2] number of tree nodes  [3] D (depth of the leaf level; HSS levels
+ *  L = D + 1)  [4] entries of all near lists  [5] entries of all far lists
+ *  [6] total skeleton size (sum of H^2 ranks)  [7] bytes of stored H^2 generators
+ *  (bases, transfers, couplings)  [8] near-field kernel entries per matvec
+ *  [9] coupling entries per matvec  [10] basis/transfer entries per matvec
+ *  [11] largest H^2 rank  [12..15] reserved (0). */
+spdhss_status h2_info(h2_handle h2, int64_t* info);
+
+/* Export of the cluster tree for parity checks; every pointer is a HOST array sized from
+ * h2_info (nn = info[2], nnear = info[4], nfar = info[5]); any pointer may be NULL.
+ *   perm[n]           sorted position -> original point index
+ *   depth_off[D+2]    nodes of depth t are [depth_off[t], depth_off[t+1])
+ *   begin[nn], end[nn]  point range in sorted order
+ *   parent[nn]        -1 for the root
+ *   cell_lo[nn*dim], cell_hi[nn*dim]  integer cell on the finest grid, row-major
+ *   near_off[nn+1], near_idx[nnear], far_off[nn+1], far_idx[nfar]  CSR lists */
+spdhss_status h2_export_tree(h2_handle h2, int64_t* perm, int64_t* depth_off, int64_t* begin,
+                             int64_t* end, int64_t* parent, int64_t* cell_lo, int64_t* cell_hi,
+                             int64_t* near_off, int64_t* near_idx, int64_t* far_off,
+                             int64_t* far_idx);
+
+/* Export of the H^2 skeletons (HOST arrays): skel_off[nn+1] (node i owns
+ * skel_idx[skel_off[i] .. skel_off[i+1]-1]), skel_idx[info[6]] = sorted-order point
+ * indices in pivot order.  Either pointer may be NULL. */
+spdhss_status h2_export_skeletons(h2_handle h2, int64_t* skel_off, int64_t* skel_idx);
+
+spdhss_status h2_destroy(h2_handle h2);
+
+/* ---- SPD HSS construction (Alg. 5.3 with Alg. 5.1 and Alg. 5.2) ----------------------
+ * Builds the SPD HSS approximation {A_ii, U_i, R_i, B_ij} of the H^2 matrix with rank cap
+ * `rank` (r) and oversampling `oversample` (p, the paper uses 10).  The Gaussian sketch
+ * Omega is n x (r+p):
+ *   omega   DEVICE pointer, column-major, leading dimension n, original point order; or
+ *           NULL, in which case Omega is drawn on the device from `seed`.
+ * (I + bold B_ii) is factored by Cholesky (equivalent to the symmetric square root of
+ * Eq. Si0 up to an orthogonal factor that the pivoted QR absorbs).
+ * Errors: NOT_SPD (message names the node) when a Cholesky factorization fails, EINVAL,
+ * ENOMEM, ECUDA. */
+spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
+                           uint64_t seed, void* stream, hss_handle* out);
+
+/* Y = H X with the HSS approximation H (same layout rules as h2_matmul). */
+spdhss_status hss_matmul(hss_handle hss, const double* X, double* Y, int nrhs, int64_t ld,
+                         void* stream);
+
+/* HOST info[8]: [0] number of HSS levels L  [1] largest rank r_i  [2] bytes of stored HSS
+ * generators  [3] number of nodes  [4..7] reserved. */
+spdhss_status hss_info(hss_handle hss, int64_t* info);
+
+spdhss_status hss_destroy(hss_handle hss);
+
+/* ---- ULV factorization and solve ---------------------------------------------------
+ * ulv_factor: symmetric ULV of the SPD HSS matrix (orthogonal compression of every
+ * basis, Cholesky elimination of the complement, Schur update, dense Cholesky at the
+ * root).  Errors: NOT_SPD if a pivot is not positive. */
+spdhss_status ulv_factor(hss_handle hss, void* stream, ulv_handle* out);
+
+/* X = H^{-1} B.  B, X device, n x nrhs column-major, leading dimension ld, original
+ * order; B and X may be the same array. */
+spdhss_status ulv_solve(ulv_handle ulv, const double* B, double* X, int nrhs, int64_t ld,
+                        void* stream);
+
+spdhss_status ulv_destroy(ulv_handle ulv);
+
+/* ---- PCG (Sec. 6.2) ------------------------------------------------------------------
+ * Solves A X = B with the H^2 matrix A and the ULV-factored SPD HSS preconditioner, from
+ * X_0 = 0, every column independently, until the relative residual of every column is
+ * <= relres_tol (recursive residual, confirmed by a recomputed true residual) or maxit
+ * iterations.
+ *   B, X          n x nrhs column-major, leading dimension ld, original order; HOST or
+ *                 DEVICE pointers (detected; host data is staged through the device).
+ *   iters_out     HOST int[nrhs] or NULL: iterations taken per column.
+ *   relres_out    HOST double[nrhs] or NULL: final true relative residual per column.
+ * Returns NO_CONVERGENCE if some column missed the tolerance (X holds the last iterate). */
+spdhss_status pcg_solve(h2_handle h2, ulv_handle ulv, const double* B, double* X, int nrhs,
+                        int64_t ld, double relres_tol, int maxit, int* iters_out,
+                        double* relres_out, void* stream);
+
+/* ---- diagnostics ---------------------------------------------------------------------- */
+const char* spdhss_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+int64_t spdhss_launch_count(void);
+
+/* Library version string. */
+const char* spdhss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPDHSS_H */

@@ -1,0 +1,201 @@
+"""Python binding of the spdhss C ABI (include/spdhss.h).
+
+Thin argument marshalling over the CUDA library: PyTorch tensors supply device memory
+and the current CUDA stream; every step of the method runs in the library's kernels.
+Block vectors are (n, ncol) tensors in the original point order; they are handed to the
+library column-major (a contiguous (ncol, n) buffer, leading dimension n).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import native as N
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _colmajor(X, device="cuda") -> torch.Tensor:
+    """(n,) or (n, ncol) -> contiguous float64 (ncol, n) buffer on the device."""
+    if isinstance(X, np.ndarray):
+        X = torch.from_numpy(X)
+    if X.dim() == 1:
+        X = X[:, None]
+    return X.to(device=device, dtype=torch.float64).t().contiguous()
+
+
+def _i64(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+class H2:
+    """H^2 representation of sigma*I + K(X, X) (h2_build)."""
+
+    def __init__(self, points, kernel: str = "exp", ell: float = 1.0, shift: float = 0.0,
+                 leaf_size: int = 64, tol: float = 1e-8, stream=None):
+        if isinstance(points, np.ndarray):
+            points = torch.from_numpy(np.ascontiguousarray(points, dtype=np.float64))
+        points = points.to(torch.float64).contiguous()
+        n, dim = points.shape
+        self.n, self.dim = int(n), int(dim)
+        self.kernel, self.ell, self.shift = kernel, float(ell), float(shift)
+        self.leaf_size, self.tol = int(leaf_size), float(tol)
+        kd = N.KernelDesc(N.KERNELS[kernel], float(ell), float(shift))
+        h = ctypes.c_void_p()
+        N.check(N.lib().h2_build(_ptr(points), self.n, self.dim, kd, int(leaf_size), float(tol),
+                                 _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def matmul(self, X, stream=None) -> torch.Tensor:
+        Xc = _colmajor(X)
+        Yc = torch.empty_like(Xc)
+        N.check(N.lib().h2_matmul(self._h, _ptr(Xc), _ptr(Yc), Xc.shape[0], self.n, _stream(stream)))
+        return Yc.t()
+
+    def info(self) -> dict:
+        a = np.zeros(16, np.int64)
+        N.check(N.lib().h2_info(self._h, _i64(a)))
+        keys = ["n", "dim", "nodes", "D", "near_entries", "far_entries", "skeleton_total",
+                "stored_bytes", "near_kernel_entries", "coupling_entries", "basis_entries",
+                "max_rank"]
+        return {k: int(a[i]) for i, k in enumerate(keys)}
+
+    def export_tree(self) -> dict:
+        inf = self.info()
+        nn, D, dim = inf["nodes"], inf["D"], inf["dim"]
+        out = {
+            "perm": np.zeros(self.n, np.int64), "depth_off": np.zeros(D + 2, np.int64),
+            "begin": np.zeros(nn, np.int64), "end": np.zeros(nn, np.int64),
+            "parent": np.zeros(nn, np.int64), "cell_lo": np.zeros(nn * dim, np.int64),
+            "cell_hi": np.zeros(nn * dim, np.int64), "near_off": np.zeros(nn + 1, np.int64),
+            "near_idx": np.zeros(max(inf["near_entries"], 1), np.int64),
+            "far_off": np.zeros(nn + 1, np.int64),
+            "far_idx": np.zeros(max(inf["far_entries"], 1), np.int64),
+        }
+        order = ["perm", "depth_off", "begin", "end", "parent", "cell_lo", "cell_hi",
+                 "near_off", "near_idx", "far_off", "far_idx"]
+        N.check(N.lib().h2_export_tree(self._h, *[_i64(out[k]) for k in order]))
+        out["near_idx"] = out["near_idx"][:inf["near_entries"]]
+        out["far_idx"] = out["far_idx"][:inf["far_entries"]]
+        out["cell_lo"] = out["cell_lo"].reshape(nn, dim)
+        out["cell_hi"] = out["cell_hi"].reshape(nn, dim)
+        out["D"] = D
+        return out
+
+    def export_skeletons(self):
+        inf = self.info()
+        off = np.zeros(inf["nodes"] + 1, np.int64)
+        idx = np.zeros(max(inf["skeleton_total"], 1), np.int64)
+        N.check(N.lib().h2_export_skeletons(self._h, _i64(off), _i64(idx)))
+        return off, idx[:inf["skeleton_total"]]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().h2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HSS:
+    """SPD HSS approximation built from an H^2 matrix (spdhss_build, Alg. 5.3)."""
+
+    def __init__(self, h2: H2, rank: int, oversample: int = 10, omega=None, seed: int = 0,
+                 stream=None):
+        self.h2 = h2
+        self.rank, self.oversample = int(rank), int(oversample)
+        om = None
+        if omega is not None:
+            om = _colmajor(omega)
+            assert om.shape == (rank + oversample, h2.n)
+        h = ctypes.c_void_p()
+        N.check(N.lib().spdhss_build(h2._h, int(rank), int(oversample),
+                                     _ptr(om) if om is not None else None, int(seed),
+                                     _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def matmul(self, X, stream=None) -> torch.Tensor:
+        Xc = _colmajor(X)
+        Yc = torch.empty_like(Xc)
+        N.check(N.lib().hss_matmul(self._h, _ptr(Xc), _ptr(Yc), Xc.shape[0], self.h2.n,
+                                   _stream(stream)))
+        return Yc.t()
+
+    def info(self) -> dict:
+        a = np.zeros(8, np.int64)
+        N.check(N.lib().hss_info(self._h, _i64(a)))
+        return {"levels": int(a[0]), "max_rank": int(a[1]), "stored_bytes": int(a[2]),
+                "nodes": int(a[3])}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().hss_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ULV:
+    """ULV factorization of an SPD HSS matrix (ulv_factor / ulv_solve)."""
+
+    def __init__(self, hss: HSS, stream=None):
+        self.hss = hss
+        h = ctypes.c_void_p()
+        N.check(N.lib().ulv_factor(hss._h, _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, B, stream=None) -> torch.Tensor:
+        Bc = _colmajor(B)
+        Xc = torch.empty_like(Bc)
+        N.check(N.lib().ulv_solve(self._h, _ptr(Bc), _ptr(Xc), Bc.shape[0], self.hss.h2.n,
+                                  _stream(stream)))
+        return Xc.t()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().ulv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=None,
+              raise_on_no_convergence: bool = False):
+    """PCG (Sec. 6.2): returns (X (n, nrhs), iterations per column, true relres per column).
+
+    B may be a CUDA tensor (device path) or a CPU tensor / numpy array (host buffers: the
+    library stages them through the device and X comes back on the host)."""
+    host = isinstance(B, np.ndarray) or (isinstance(B, torch.Tensor) and not B.is_cuda)
+    Bc = _colmajor(B, device="cpu" if host else "cuda")
+    if host:
+        Bc = Bc.contiguous()
+    nrhs = Bc.shape[0]
+    Xc = torch.empty_like(Bc)
+    it = (ctypes.c_int * nrhs)()
+    rr = (ctypes.c_double * nrhs)()
+    st = N.lib().pcg_solve(h2._h, ulv._h, _ptr(Bc), _ptr(Xc), nrhs, h2.n, float(tol),
+                           int(maxit), it, rr, _stream(stream))
+    if st != N.OK and not (st == N.NO_CONVERGENCE and not raise_on_no_convergence):
+        N.check(st)
+    return Xc.t(), np.array(list(it)), np.array(list(rr))

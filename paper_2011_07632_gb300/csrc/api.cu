@@ -1,0 +1,168 @@
+// C ABI entry points (include/spdhss.h): argument checks, error capture, and the H^2 calls.
+#include <atomic>
+#include <cstring>
+
+#include "h2.cuh"
+
+namespace spd {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+template <class F>
+spdhss_status guarded(const char* where, F&& f) {
+  try {
+    f();
+    return SPDHSS_OK;
+  } catch (const Error& e) {
+    set_last_error(std::string(where) + ": " + e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error(std::string(where) + ": host allocation failed");
+    return SPDHSS_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(std::string(where) + ": " + e.what());
+    return SPDHSS_ECUDA;
+  }
+}
+
+}  // namespace spd
+
+using namespace spd;
+
+extern "C" {
+
+const char* spdhss_last_error(void) { return g_last_error.c_str(); }
+int64_t spdhss_launch_count(void) { return g_launches.load(); }
+const char* spdhss_version(void) { return "spdhss-gb300 0.1 (sm_103a, fp64)"; }
+
+spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
+                       int leaf_size, double tol, void* stream, h2_handle* out) {
+  return guarded("h2_build", [&] {
+    SPD_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    SPD_REQUIRE(points != nullptr, "points is NULL");
+    SPD_REQUIRE(n >= 1 && n < (1LL << 40), "n out of range");
+    SPD_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+    SPD_REQUIRE(leaf_size >= 1, "leaf_size must be >= 1");
+    SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
+    SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 3, "unknown kernel kind");
+    SPD_REQUIRE(kernel.ell > 0.0, "kernel length scale must be > 0");
+    SPD_REQUIRE(kernel.shift >= 0.0, "shift must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<spdhss_h2_s> h(new spdhss_h2_s());
+    h->kfn.kind = kernel.kind;
+    h->kfn.inv_ell = 1.0 / kernel.ell;
+    h->kfn.shift = kernel.shift;
+    h->tol = tol;
+    const double* dp = points;
+    DevBuf<double> staged;
+    if (!is_device_pointer(points)) {
+      staged.alloc((size_t)n * dim);
+      SPD_CUDA(cudaMemcpyAsync(staged.p, points, (size_t)n * dim * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      dp = staged.p;
+    }
+    h2_build_impl(h.get(), dp, n, dim, leaf_size, s);
+    *out = h.release();
+  });
+}
+
+spdhss_status h2_matmul(h2_handle h, const double* X, double* Y, int nrhs, int64_t ld,
+                        void* stream) {
+  return guarded("h2_matmul", [&] {
+    SPD_REQUIRE(h && X && Y, "NULL argument");
+    SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    SPD_REQUIRE(ld >= h->th.n, "ld must be >= n");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto it = h->plans.find(nrhs);
+    if (it == h->plans.end()) {
+      std::unique_ptr<H2Plan> p(new H2Plan());
+      h2_plan_build(h, *p, nrhs, 1, s);
+      it = h->plans.emplace(nrhs, std::move(p)).first;
+    }
+    const H2Plan& p = *it->second;
+    permute_to_sorted(X, ld, p.xs.p, h->th.n, nrhs, h->td.perm.p, s);
+    h2_plan_run(h, p, s);
+    permute_from_sorted(p.ys.p, Y, ld, h->th.n, nrhs, h->td.perm.p, s);
+  });
+}
+
+spdhss_status h2_info(h2_handle h, int64_t* info) {
+  return guarded("h2_info", [&] {
+    SPD_REQUIRE(h && info, "NULL argument");
+    const TreeHost& T = h->th;
+    for (int k = 0; k < 16; ++k) info[k] = 0;
+    info[0] = T.n;
+    info[1] = T.dim;
+    info[2] = T.nn();
+    info[3] = T.D;
+    info[4] = (int64_t)T.near_idx.size();
+    info[5] = (int64_t)T.far_idx.size();
+    info[6] = h->Ktot;
+    info[7] = (int64_t)(h->basis.bytes() + h->coup.bytes());
+    int64_t nearE = 0, coupE = 0, basE = 0;
+    for (int64_t i = T.depth_off[T.D]; i < T.depth_off[T.D + 1]; ++i)
+      for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e)
+        nearE += T.size(i) * T.size(T.near_idx[e]);
+    for (int64_t i = 0; i < T.nn(); ++i) {
+      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e)
+        coupE += (int64_t)h->rank(i) * h->rank(T.far_idx[e]);
+      basE += (int64_t)h->U_rows[i] * h->rank(i);
+    }
+    info[8] = nearE;
+    info[9] = coupE;
+    info[10] = basE;
+    info[11] = h->max_rank;
+  });
+}
+
+spdhss_status h2_export_tree(h2_handle h, int64_t* perm, int64_t* depth_off, int64_t* begin,
+                             int64_t* end, int64_t* parent, int64_t* cell_lo, int64_t* cell_hi,
+                             int64_t* near_off, int64_t* near_idx, int64_t* far_off,
+                             int64_t* far_idx) {
+  return guarded("h2_export_tree", [&] {
+    SPD_REQUIRE(h != nullptr, "NULL handle");
+    const TreeHost& T = h->th;
+    auto cp = [](int64_t* dst, const std::vector<int64_t>& v) {
+      if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int64_t));
+    };
+    if (perm) {
+      std::vector<int64_t> hp = h->td.perm.download(0);
+      cp(perm, hp);
+    }
+    cp(depth_off, T.depth_off);
+    cp(begin, T.begin);
+    cp(end, T.end);
+    cp(parent, T.parent);
+    cp(cell_lo, T.cell_lo);
+    if (cell_hi) {
+      std::vector<int64_t> hi(T.cell_lo.size());
+      for (int64_t i = 0; i < T.nn(); ++i)
+        for (int a = 0; a < T.dim; ++a) hi[i * T.dim + a] = T.cell_lo[i * T.dim + a] + T.width[i];
+      cp(cell_hi, hi);
+    }
+    cp(near_off, T.near_off);
+    cp(near_idx, T.near_idx);
+    cp(far_off, T.far_off);
+    cp(far_idx, T.far_idx);
+  });
+}
+
+spdhss_status h2_export_skeletons(h2_handle h, int64_t* skel_off, int64_t* skel_idx) {
+  return guarded("h2_export_skeletons", [&] {
+    SPD_REQUIRE(h != nullptr, "NULL handle");
+    if (skel_off) std::memcpy(skel_off, h->skel_off.data(), h->skel_off.size() * sizeof(int64_t));
+    if (skel_idx && !h->skel_idx.empty())
+      std::memcpy(skel_idx, h->skel_idx.data(), h->skel_idx.size() * sizeof(int64_t));
+  });
+}
+
+spdhss_status h2_destroy(h2_handle h) {
+  return guarded("h2_destroy", [&] { delete h; });
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Shared host/device helpers of the spdhss library: status errors, device buffers,
+// launch accounting, the kernel functions of Sec. 6, and small launch utilities.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/spdhss.h"
+
+namespace spd {
+
+struct Error : std::runtime_error {
+  spdhss_status code;
+  Error(spdhss_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+void count_launches(int64_t k = 1);
+
+#define SPD_CUDA(x)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) {                                                               \
+      if (e_ == cudaErrorMemoryAllocation)                                                 \
+        throw ::spd::Error(SPDHSS_ENOMEM, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+      throw ::spd::Error(SPDHSS_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));    \
+    }                                                                                      \
+  } while (0)
+
+#define SPD_LAUNCHED()                   \
+  do {                                   \
+    ::spd::count_launches();             \
+    SPD_CUDA(cudaGetLastError());        \
+  } while (0)
+
+#define SPD_REQUIRE(cond, msg)                                  \
+  do {                                                          \
+    if (!(cond)) throw ::spd::Error(SPDHSS_EINVAL, (msg));      \
+  } while (0)
+
+// Plain device allocation owned by its object (cudaMalloc / cudaFree).
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { alloc(count); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count) SPD_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void zero(cudaStream_t s) {
+    if (n) SPD_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    alloc(h.size());
+    if (n) SPD_CUDA(cudaMemcpyAsync(p, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s) const {
+    std::vector<T> h(n);
+    if (n) {
+      SPD_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+      SPD_CUDA(cudaStreamSynchronize(s));
+    }
+    return h;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+inline bool is_device_pointer(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---- kernel functions (Sec. 6), length scale ell divides r ---------------------------
+struct KernelFn {
+  int kind;
+  double inv_ell;   // 1/ell
+  double shift;
+};
+
+__device__ __forceinline__ double kernel_r2(const KernelFn& k, double r2) {
+  switch (k.kind) {
+    case SPDHSS_K_EXP:
+      return exp(-sqrt(r2) * k.inv_ell);
+    case SPDHSS_K_GAUSS:
+      return exp(-r2 * (k.inv_ell * k.inv_ell));
+    case SPDHSS_K_MATERN32: {
+      double t = 1.7320508075688772 * sqrt(r2) * k.inv_ell;
+      return (1.0 + t) * exp(-t);
+    }
+    default:
+      return 1.0 / sqrt(1.0 + r2 * (k.inv_ell * k.inv_ell));
+  }
+}
+
+// Points are stored structure-of-arrays: coordinate a of point p at x[a * ldx + p].
+__device__ __forceinline__ double sqdist3(const double* __restrict__ x, int64_t ldx, int dim,
+                                          int64_t p, double y0, double y1, double y2) {
+  double d0 = x[p] - y0;
+  double d1 = x[ldx + p] - y1;
+  double r2 = d0 * d0 + d1 * d1;
+  if (dim == 3) {
+    double d2 = x[2 * ldx + p] - y2;
+    r2 += d2 * d2;
+  }
+  return r2;
+}
+
+}  // namespace spd

@@ -1,0 +1,526 @@
+// Batched FP64 dense kernels: grouped GEMM, Cholesky, triangular solves, Householder QR
+// with column pivoting (thread-block clusters split the columns of a large matrix), and
+// reflector application.  One launch covers all nodes of a tree level.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "dense.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace spd {
+
+// ---------------------------------------------------------------------------------------
+// grouped GEMM: 64x64 tile per CTA, 256 threads, 4x4 register tile per thread, K step 16
+// ---------------------------------------------------------------------------------------
+constexpr int GM = 64, GN = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs,
+                                              const GemmSeg* __restrict__ segs,
+                                              const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const GemmProb P = probs[t.x];
+  const int m0 = t.y, n0 = t.z;
+  __shared__ double As[GK][GM + 1];
+  __shared__ double Bs[GK][GN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int s = P.seg0; s < P.seg1; ++s) {
+    const GemmSeg S = segs[s];
+    for (int k0 = 0; k0 < S.K; k0 += GK) {
+#pragma unroll
+      for (int r = 0; r < (GM * GK) / 256; ++r) {
+        const int e = tid + 256 * r;
+        int mm, kk;
+        if (!S.tA) { mm = e % GM; kk = e / GM; } else { kk = e % GK; mm = e / GK; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < P.M && gk < S.K)
+          v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
+        As[kk][mm] = v;
+      }
+#pragma unroll
+      for (int r = 0; r < (GN * GK) / 256; ++r) {
+        const int e = tid + 256 * r;
+        int nn, kk;
+        if (!S.tB) { kk = e % GK; nn = e / GK; } else { nn = e % GN; kk = e / GN; }
+        const int gn = n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < P.N && gk < S.K)
+          v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= P.N) continue;
+      double* c = P.C + gm + (int64_t)gn * P.ldc;
+      double v = P.alpha * acc[i][j];
+      if (P.beta != 0.0) v += P.beta * (*c);
+      *c = v;
+    }
+  }
+}
+
+void GemmBatch::upload(cudaStream_t s) {
+  tiles.clear();
+  for (int p = 0; p < (int)probs.size(); ++p)
+    for (int m0 = 0; m0 < probs[p].M; m0 += GM)
+      for (int n0 = 0; n0 < probs[p].N; n0 += GN) tiles.push_back(make_int4(p, m0, n0, 0));
+  d_segs.upload(segs, s);
+  d_probs.upload(probs, s);
+  d_tiles.upload(tiles, s);
+}
+
+void GemmBatch::launch(cudaStream_t s) const {
+  const int64_t nt = (int64_t)tiles.size();
+  for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
+    const int nb = (int)std::min<int64_t>(nt - b0, 2147483647LL);
+    k_gemm<<<nb, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0);
+    SPD_LAUNCHED();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Cholesky, one CTA per matrix, right-looking in global memory
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ probs, int* info) {
+  const PotrfProb P = probs[blockIdx.x];
+  double* A = P.A;
+  const int64_t ld = P.lda;
+  const int n = P.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ double s_d;
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = A[j + j * ld];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = 1;
+        if (atomicCAS(info, 0, P.tag + 1) == 0) info[1] = j;
+      }
+      s_d = sqrt(d);
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const double d = s_d;
+    const double inv = 1.0 / d;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + j * ld] *= inv;
+    if (threadIdx.x == 0) A[j + j * ld] = d;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      const double ljc = A[c + j * ld];
+      for (int i = c + lane; i < n; i += 32) A[i + c * ld] -= A[i + j * ld] * ljc;
+    }
+    __syncthreads();
+  }
+  for (int c = warp; c < n; c += nw)
+    for (int i = lane; i < c; i += 32) A[i + c * ld] = 0.0;
+}
+
+void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
+  if (b.empty()) return;
+  k_potrf<<<(unsigned)b.size(), 256, 0, s>>>(b.d.p, d_info);
+  SPD_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------------------
+// triangular solves: one warp per right-hand-side column
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_trsm(const TrsmProb* __restrict__ probs,
+                                              const int2* __restrict__ work, int64_t nwork) {
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int lane = threadIdx.x & 31;
+  const int2 it = work[w];
+  const TrsmProb P = probs[it.x];
+  double* b = P.B + (int64_t)it.y * P.ldb;
+  const double* T = P.T;
+  const int64_t lt = P.ldt;
+  const int n = P.n;
+  // op(T)(i, j): element of the matrix actually solved with
+  const bool fwd = (P.lower && !P.trans) || (!P.lower && P.trans);
+  const bool direct = !P.trans;   // op(T)(i,j) = T[i + j*lt] when not transposed
+  if (fwd) {
+    for (int j = 0; j < n; ++j) {
+      __syncwarp();
+      const double xj = b[j] / T[j + j * lt];
+      __syncwarp();
+      if (lane == 0) b[j] = xj;
+      for (int i = j + 1 + lane; i < n; i += 32) {
+        const double tij = direct ? T[i + (int64_t)j * lt] : T[j + (int64_t)i * lt];
+        b[i] -= tij * xj;
+      }
+    }
+  } else {
+    for (int j = n - 1; j >= 0; --j) {
+      __syncwarp();
+      const double xj = b[j] / T[j + j * lt];
+      __syncwarp();
+      if (lane == 0) b[j] = xj;
+      for (int i = lane; i < j; i += 32) {
+        const double tij = direct ? T[i + (int64_t)j * lt] : T[j + (int64_t)i * lt];
+        b[i] -= tij * xj;
+      }
+    }
+  }
+}
+
+void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
+  if (b.empty()) return;
+  std::vector<int2> work;
+  for (int p = 0; p < (int)b.size(); ++p)
+    if (b.h[p].n > 0)
+      for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+  if (work.empty()) return;
+  DevBuf<int2> dw;
+  dw.upload(work, s);
+  const int64_t nw = (int64_t)work.size();
+  k_trsm<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
+  SPD_LAUNCHED();
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------------------
+// Householder QR with column pivoting; a cluster of C CTAs shares one matrix, CTA q owning
+// the column positions p with p % C == q.  Pivot norms are recomputed from the updated
+// trailing rows at every step; ties go to the lowest position.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void argmax_merge(double& v, int& p, double v2, int p2) {
+  if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs, int pivot) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
+  const QrProb P = probs[blockIdx.x / C];
+  extern __shared__ double s_v[];
+  __shared__ double s_wv[8];
+  __shared__ int s_wp[8];
+  __shared__ double s_cv;
+  __shared__ int s_cp;
+  __shared__ double s_first, s_tau, s_scale;
+  __shared__ int s_stop, s_piv;
+  const int m = P.m, n = P.n;
+  const int kmax = min(P.kmax, min(m, n));
+  double* A = P.A;
+  const int64_t ld = P.lda;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+
+  // first owned position >= start
+  auto first_owned = [&](int start) { return start + (((q - start) % C) + C) % C; };
+
+  if (pivot) {
+    int t = 0;
+    for (int p = first_owned(0); p < n; p += C, ++t) {
+      if (t % nw != warp) continue;
+      double s = 0.0;
+      for (int i = lane; i < m; i += 32) { const double a = A[i + (int64_t)p * ld]; s += a * a; }
+      s = warp_sum(s);
+      if (lane == 0) { P.norms[p] = sqrt(s); P.piv[p] = p; }
+    }
+  }
+  __threadfence();
+  cl.sync();
+
+  int j = 0;
+  for (; j < kmax; ++j) {
+    if (pivot) {
+      double bv = -1.0;
+      int bp = n;
+      int t = 0;
+      for (int p = first_owned(j); p < n; p += C, ++t)
+        if (t % nw == warp) argmax_merge(bv, bp, P.norms[p], p);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
+        argmax_merge(bv, bp, v2, p2);
+      }
+      if (lane == 0) { s_wv[warp] = bv; s_wp[warp] = bp; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) argmax_merge(bv, bp, s_wv[w], s_wp[w]);
+        s_cv = bv;
+        s_cp = bp;
+      }
+      cl.sync();
+      if (threadIdx.x == 0) {
+        double gv = -1.0;
+        int gp = n;
+        for (int r = 0; r < C; ++r) {
+          const double* pv = cl.map_shared_rank(&s_cv, r);
+          const int* pp = cl.map_shared_rank(&s_cp, r);
+          argmax_merge(gv, gp, *pv, *pp);
+        }
+        if (j == 0) s_first = gv;
+        s_stop = (gv <= 0.0) || (gv <= P.rtol * s_first) || (gp >= n);
+        s_piv = gp;
+      }
+      __syncthreads();
+      if (s_stop) break;
+    } else {
+      if (threadIdx.x == 0) s_piv = j;
+      __syncthreads();
+    }
+    const int pc = s_piv;
+    if (q == 0) {
+      if (pc != j) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          const double a = A[i + (int64_t)j * ld];
+          A[i + (int64_t)j * ld] = A[i + (int64_t)pc * ld];
+          A[i + (int64_t)pc * ld] = a;
+        }
+        if (threadIdx.x == 0) {
+          const int tp = P.piv[j]; P.piv[j] = P.piv[pc]; P.piv[pc] = tp;
+          const double tn = P.norms[j]; P.norms[j] = P.norms[pc]; P.norms[pc] = tn;
+        }
+      }
+      __syncthreads();
+      double s = 0.0;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+        const double a = A[i + (int64_t)j * ld];
+        s += a * a;
+      }
+      s = warp_sum(s);
+      if (lane == 0) s_wv[warp] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += s_wv[w];
+        const double normx = sqrt(tot);
+        const double alpha = A[j + (int64_t)j * ld];
+        double tau = 0.0, beta = alpha, scale = 0.0;
+        if (normx > 0.0) {
+          beta = alpha >= 0.0 ? -normx : normx;
+          scale = 1.0 / (alpha - beta);
+          tau = (beta - alpha) / beta;
+        }
+        s_tau = tau;
+        s_scale = scale;
+        P.tau[j] = tau;
+        A[j + (int64_t)j * ld] = beta;
+      }
+      __syncthreads();
+      const double scale = s_scale;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + (int64_t)j * ld] *= scale;
+      __threadfence();
+    }
+    cl.sync();
+    const double tau = P.tau[j];
+    const int len = m - j;
+    for (int i = threadIdx.x; i < len; i += blockDim.x)
+      s_v[i] = (i == 0) ? 1.0 : A[j + i + (int64_t)j * ld];
+    __syncthreads();
+    if (tau != 0.0) {
+      int t = 0;
+      for (int p = first_owned(j + 1); p < n; p += C, ++t) {
+        if (t % nw != warp) continue;
+        double* col = A + j + (int64_t)p * ld;
+        double w = 0.0;
+        for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
+        w = warp_sum(w) * tau;
+        double s = 0.0;
+        for (int i = lane; i < len; i += 32) {
+          const double a = col[i] - w * s_v[i];
+          col[i] = a;
+          if (i > 0) s += a * a;
+        }
+        if (pivot) {
+          s = warp_sum(s);
+          if (lane == 0) P.norms[p] = sqrt(s);
+        }
+      }
+    } else if (pivot) {
+      int t = 0;
+      for (int p = first_owned(j + 1); p < n; p += C, ++t) {
+        if (t % nw != warp) continue;
+        const double* col = A + j + (int64_t)p * ld;
+        double s = 0.0;
+        for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
+        s = warp_sum(s);
+        if (lane == 0) P.norms[p] = sqrt(s);
+      }
+    }
+    __threadfence();
+    cl.sync();
+  }
+  if (q == 0 && threadIdx.x == 0) *P.rank = j;
+  // keep every CTA of the cluster alive until peers are done reading its shared memory
+  cl.sync();
+}
+
+void geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s) {
+  if (b.empty()) return;
+  cluster = std::max(1, std::min(cluster, 8));
+  const size_t smem = (size_t)std::max(1, max_m) * sizeof(double);
+  SPD_REQUIRE(smem <= 200 * 1024, "geqp3: matrix too tall for the shared-memory reflector");
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    SPD_CUDA(cudaFuncSetAttribute(k_geqp3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
+    configured = 200 * 1024;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(b.size() * cluster), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, (const QrProb*)b.d.p, pivot));
+  SPD_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------------------
+// reflector application and explicit Q: one warp per column
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hh_apply(const HhApplyProb* __restrict__ probs,
+                                                  const int2* __restrict__ work, int64_t nwork,
+                                                  int trans) {
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int lane = threadIdx.x & 31;
+  const int2 it = work[w];
+  const HhApplyProb P = probs[it.x];
+  const int k = *P.k;
+  double* b = P.B + (int64_t)it.y * P.ldb;
+  for (int t = 0; t < k; ++t) {
+    const int j = trans ? t : k - 1 - t;
+    const double tau = P.tau[j];
+    if (tau == 0.0) continue;
+    const double* v = P.V + (int64_t)j * P.ldv;
+    double s = 0.0;
+    for (int i = j + lane; i < P.m; i += 32) s += (i == j ? 1.0 : v[i]) * b[i];
+    s = warp_sum(s) * tau;
+    for (int i = j + lane; i < P.m; i += 32) b[i] -= s * (i == j ? 1.0 : v[i]);
+    __syncwarp();
+  }
+}
+
+void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) {
+  if (b.empty()) return;
+  std::vector<int2> work;
+  for (int p = 0; p < (int)b.size(); ++p)
+    for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+  if (work.empty()) return;
+  DevBuf<int2> dw;
+  dw.upload(work, s);
+  const int64_t nw = (int64_t)work.size();
+  k_hh_apply<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw, trans);
+  SPD_LAUNCHED();
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+__global__ void __launch_bounds__(256) k_form_q(const FormQProb* __restrict__ probs,
+                                                const int2* __restrict__ work, int64_t nwork) {
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int lane = threadIdx.x & 31;
+  const int2 it = work[w];
+  const FormQProb P = probs[it.x];
+  const int k = *P.k;
+  const int c = it.y;
+  double* q = P.Q + (int64_t)c * P.ldq;
+  for (int i = lane; i < P.m; i += 32) q[i] = (i == c && c < k) ? 1.0 : 0.0;
+  __syncwarp();
+  if (c >= k) return;
+  for (int j = c; j >= 0; --j) {
+    const double tau = P.tau[j];
+    if (tau == 0.0) continue;
+    const double* v = P.V + (int64_t)j * P.ldv;
+    double s = 0.0;
+    for (int i = j + lane; i < P.m; i += 32) s += (i == j ? 1.0 : v[i]) * q[i];
+    s = warp_sum(s) * tau;
+    for (int i = j + lane; i < P.m; i += 32) q[i] -= s * (i == j ? 1.0 : v[i]);
+    __syncwarp();
+  }
+}
+
+void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s) {
+  if (b.empty()) return;
+  std::vector<int2> work;
+  for (int p = 0; p < (int)b.size(); ++p)
+    for (int c = 0; c < b.h[p].kcols; ++c) work.push_back(make_int2(p, c));
+  if (work.empty()) return;
+  DevBuf<int2> dw;
+  dw.upload(work, s);
+  const int64_t nw = (int64_t)work.size();
+  k_form_q<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
+  SPD_LAUNCHED();
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------------------
+// batched 2-D copies
+// ---------------------------------------------------------------------------------------
+__global__ void k_copy(const CopyProb* __restrict__ probs, int ident) {
+  const CopyProb P = probs[blockIdx.y];
+  const int64_t tot = (int64_t)P.m * P.n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % P.m), j = (int)(e / P.m);
+    double v;
+    if (ident) v = (i == j) ? 1.0 : 0.0;
+    else v = P.alpha * (P.trans ? P.src[j + (int64_t)i * P.lds] : P.src[i + (int64_t)j * P.lds]);
+    double* d = P.dst + i + (int64_t)j * P.ldd;
+    if (P.accumulate) *d += v; else *d = v;
+  }
+}
+
+static void copy_common(const Batch<CopyProb>& b, int ident, cudaStream_t s) {
+  if (b.empty()) return;
+  int64_t mx = 1;
+  for (const auto& p : b.h) mx = std::max<int64_t>(mx, (int64_t)p.m * p.n);
+  const int gx = (int)std::min<int64_t>(ceil_div(mx, 256), 64);
+  for (size_t y0 = 0; y0 < b.size(); y0 += 65535) {
+    const unsigned gy = (unsigned)std::min<size_t>(65535, b.size() - y0);
+    k_copy<<<dim3(gx, gy), 256, 0, s>>>(b.d.p + y0, ident);
+    SPD_LAUNCHED();
+  }
+}
+
+void copy_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 0, s); }
+void identity_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 1, s); }
+
+}  // namespace spd

@@ -1,0 +1,162 @@
+// Batched FP64 dense kernels over per-node matrices of uneven sizes.  All matrices are
+// column-major with an explicit leading dimension; every batch entry carries its own
+// pointers and sizes, so one launch covers all nodes of a tree level.
+#pragma once
+
+#include "common.cuh"
+
+namespace spd {
+
+// ---- grouped, segmented GEMM:  C = alpha * sum_s op(A_s) op(B_s) + beta * C -----------
+struct GemmSeg {
+  const double* A;
+  const double* B;
+  int64_t lda, ldb;
+  int K;
+  int tA, tB;   // 1: use the transpose
+};
+struct GemmProb {
+  double* C;
+  int64_t ldc;
+  int M, N;
+  int seg0, seg1;
+  double alpha, beta;
+};
+
+// Host-side builder of one grouped GEMM launch.
+struct GemmBatch {
+  std::vector<GemmSeg> segs;
+  std::vector<GemmProb> probs;
+  // Start a problem; add its segments with seg(); beta applies once.
+  void prob(double* C, int64_t ldc, int M, int N, double alpha, double beta) {
+    GemmProb p;
+    p.C = C; p.ldc = ldc; p.M = M; p.N = N; p.alpha = alpha; p.beta = beta;
+    p.seg0 = p.seg1 = (int)segs.size();
+    probs.push_back(p);
+  }
+  void seg(const double* A, int64_t lda, int tA, const double* B, int64_t ldb, int tB, int K) {
+    GemmSeg s;
+    s.A = A; s.B = B; s.lda = lda; s.ldb = ldb; s.K = K; s.tA = tA; s.tB = tB;
+    segs.push_back(s);
+    probs.back().seg1 = (int)segs.size();
+  }
+  // single-segment convenience
+  void add(double* C, int64_t ldc, int M, int N, const double* A, int64_t lda, int tA,
+           const double* B, int64_t ldb, int tB, int K, double alpha, double beta) {
+    prob(C, ldc, M, N, alpha, beta);
+    seg(A, lda, tA, B, ldb, tB, K);
+  }
+  bool empty() const { return probs.empty(); }
+  // upload() copies the descriptors to the device once; launch() may then be repeated.
+  void upload(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+  void run(cudaStream_t s) { upload(s); launch(s); }
+  void clear() { segs.clear(); probs.clear(); tiles.clear(); }
+  std::vector<int4> tiles;   // (prob, m0, n0, 0)
+  DevBuf<GemmSeg> d_segs;
+  DevBuf<GemmProb> d_probs;
+  DevBuf<int4> d_tiles;
+};
+
+// A batch of descriptors of one kind with its device copy.
+template <class P>
+struct Batch {
+  std::vector<P> h;
+  DevBuf<P> d;
+  void upload(cudaStream_t s) { d.upload(h, s); }
+  size_t size() const { return h.size(); }
+  bool empty() const { return h.empty(); }
+  void push(const P& p) { h.push_back(p); }
+};
+
+// ---- batched Cholesky, in place (lower), upper triangle zeroed --------------------------
+struct PotrfProb {
+  double* A;
+  int64_t lda;
+  int n;
+  int tag;   // reported in the failure record
+};
+// info[0] receives tag+1 of a failing matrix (0 if all succeed); info[1] the failing column.
+void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s);
+
+// ---- batched triangular solves, in place on B (n x ncol): op(T) X = B -------------------
+// lower=1: T lower triangular; trans=1: solve with T^T.
+struct TrsmProb {
+  const double* T;
+  int64_t ldt;
+  double* B;
+  int64_t ldb;
+  int n, ncol;
+  int lower, trans;
+};
+void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s);
+
+// ---- batched Householder QR with optional column pivoting -----------------------------
+// On exit A holds R in its upper triangle (first `rank` rows, all columns in pivot order)
+// and the reflectors v (v_0 = 1 implicit) below the diagonal of its first `rank` columns.
+// piv[0..n) receives the column order (indices of the input columns).  The factorization
+// stops after kmax steps, or before step j when the largest remaining column norm is
+// <= rtol * (first pivot norm).  pivot=0 disables pivoting (plain QR of kmax columns).
+struct QrProb {
+  double* A;
+  int64_t lda;
+  int m, n, kmax;
+  double rtol;
+  int* piv;       // n entries (may be null when pivot == 0)
+  double* tau;    // kmax entries
+  int* rank;      // 1 entry
+  double* norms;  // n entries of scratch
+};
+void geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s);
+
+// Apply the k reflectors stored in (V, ldv, tau) to B (m x ncol) in place:
+// trans=1: B <- Q^T B;  trans=0: B <- Q B.   Q = H_0 H_1 ... H_{k-1}.
+struct HhApplyProb {
+  const double* V;
+  int64_t ldv;
+  const double* tau;
+  const int* k;     // device pointer to the reflector count (rank of the QR)
+  double* B;
+  int64_t ldb;
+  int m, ncol;
+};
+void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s);
+
+// Q(:, 0:k) explicitly into Q (m x kcols, only columns < *k written; others zeroed).
+struct FormQProb {
+  const double* V;
+  int64_t ldv;
+  const double* tau;
+  const int* k;
+  double* Q;
+  int64_t ldq;
+  int m, kcols;
+};
+void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s);
+
+// ---- batched strided 2-D copies: dst(i,j) = alpha*src(i,j) (+ dst if accumulate) --------
+struct CopyProb {
+  const double* src;
+  int64_t lds;
+  double* dst;
+  int64_t ldd;
+  int m, n;
+  int trans;        // 1: dst(i,j) = src(j,i)
+  int accumulate;   // 1: dst += ...
+  double alpha;
+};
+void copy_launch(const Batch<CopyProb>& b, cudaStream_t s);
+// dst(0:m, 0:m) = I for every entry (src unused)
+void identity_launch(const Batch<CopyProb>& b, cudaStream_t s);
+
+// one-shot helpers: upload and launch (descriptors freed when the call returns)
+template <class P, class F>
+void run_once(std::vector<P> h, cudaStream_t s, F launch) {
+  if (h.empty()) return;
+  Batch<P> b;
+  b.h = std::move(h);
+  b.upload(s);
+  launch(b);
+}
+
+}  // namespace spd

@@ -1,0 +1,442 @@
+// Proxy-point H^2 construction and H^2 products.
+//
+// Construction, bottom-up over the depths: for every node with a far field, the proxy
+// matrix K(P_i, X_cand) (candidates: the node's points at the leaf level, the children's
+// skeleton points above) is factored by column-pivoted QR stopped at |R_kk| <= tol |R_00|;
+// the interpolative decomposition U = Pi [I; (R11^{-1} R12)^T] is the leaf basis / transfer
+// matrix and the first k pivots are the skeleton.  Couplings B_ij = K(X_skel_i, X_skel_j)
+// for the Type-3 pairs (Sec. 5.2.2) are stored once per unordered pair.
+#include <algorithm>
+
+#include "h2.cuh"
+
+namespace spd {
+
+// ---- ID: U (m x k) from the pivots and T = R11^{-1} R12 stored over R12 ---------------
+struct IdProb {
+  const double* G;   // QR workspace, ld np: T[b, a-k] at G[b + a*np] for a >= k
+  int64_t ldg;
+  const int* piv;
+  const int* rank;
+  double* U;         // m x k, ld m
+  int m;
+};
+
+__global__ void k_id_assemble(const IdProb* __restrict__ probs) {
+  const IdProb P = probs[blockIdx.x];
+  const int k = *P.rank;
+  const int m = P.m;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * k; e += blockDim.x) {
+    const int a = (int)(e % m), b = (int)(e / m);
+    const double v = (a < k) ? (a == b ? 1.0 : 0.0) : P.G[b + (int64_t)a * P.ldg];
+    P.U[P.piv[a] + (int64_t)b * m] = v;
+  }
+}
+
+__global__ void k_gather_coords(const double* __restrict__ xs, int64_t n, int dim,
+                                const int64_t* __restrict__ idx, int64_t K,
+                                double* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= K) return;
+  for (int a = 0; a < dim; ++a) out[a * K + r] = xs[a * n + idx[r]];
+}
+
+__global__ void k_perm_to(const double* __restrict__ X, int64_t ldx, double* __restrict__ Xs,
+                          int64_t n, int ncol, const int64_t* __restrict__ perm) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * ncol) return;
+  const int64_t p = e % n, c = e / n;
+  Xs[p + c * n] = X[perm[p] + c * ldx];
+}
+
+__global__ void k_perm_from(const double* __restrict__ Xs, double* __restrict__ Y, int64_t ldy,
+                            int64_t n, int ncol, const int64_t* __restrict__ perm) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * ncol) return;
+  const int64_t p = e % n, c = e / n;
+  Y[perm[p] + c * ldy] = Xs[p + c * n];
+}
+
+void permute_to_sorted(const double* X, int64_t ldx, double* Xs, int64_t n, int ncol,
+                       const int64_t* perm, cudaStream_t s) {
+  k_perm_to<<<ceil_div(n * ncol, 256), 256, 0, s>>>(X, ldx, Xs, n, ncol, perm);
+  SPD_LAUNCHED();
+}
+
+void permute_from_sorted(const double* Xs, double* Y, int64_t ldy, int64_t n, int ncol,
+                         const int64_t* perm, cudaStream_t s) {
+  k_perm_from<<<ceil_div(n * ncol, 256), 256, 0, s>>>(Xs, Y, ldy, n, ncol, perm);
+  SPD_LAUNCHED();
+}
+
+static bool has_far_field(const TreeHost& T, int64_t i) {
+  const int64_t wd = T.width[i];
+  const int64_t top = 1LL << T.B;
+  for (int a = 0; a < T.dim; ++a) {
+    const int64_t lo = T.cell_lo[i * T.dim + a];
+    if (lo - wd > 0 || top - (lo + wd) - wd > 0) return true;
+  }
+  return false;
+}
+
+void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, int leaf_size,
+                   cudaStream_t s) {
+  build_tree(d_points, n, dim, leaf_size, s, h->th, h->td);
+  const TreeHost& T = h->th;
+  const int64_t NN = T.nn();
+  const int D = T.D;
+  const int np = proxy_count(dim);
+  const double hg = T.w / (double)(1LL << T.B);
+
+  std::vector<int> rank(NN, 0), mrows(NN, 0);
+  std::vector<std::vector<int64_t>> skel_local(NN);   // skeleton (sorted point indices)
+  std::vector<DevBuf<double>> sx(D + 2);              // per-depth skeleton coordinates
+  std::vector<std::vector<int64_t>> soff(D + 2);      // per-depth local skeleton offsets
+  std::vector<std::unique_ptr<DevBuf<double>>> upool;
+  std::vector<double*> Uptr(NN, nullptr);
+
+  for (int t = D; t >= 1; --t) {
+    const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
+    // candidate rows
+    for (int64_t k = 0; k < nn; ++k) {
+      const int64_t i = o + k;
+      if (t == D) mrows[i] = (int)T.size(i);
+      else {
+        int m = 0;
+        for (int64_t c = T.child_begin[i]; c < T.child_end[i]; ++c) m += rank[c];
+        mrows[i] = m;
+      }
+    }
+    // batches bounded by scratch memory
+    std::vector<int64_t> todo;
+    for (int64_t k = 0; k < nn; ++k)
+      if (mrows[o + k] > 0 && has_far_field(T, o + k)) todo.push_back(o + k);
+    const size_t budget = (size_t)3 << 30;
+    size_t pos = 0;
+    while (pos < todo.size()) {
+      size_t end = pos, bytes = 0;
+      while (end < todo.size()) {
+        const size_t b = (size_t)np * mrows[todo[end]] * sizeof(double);
+        if (end > pos && bytes + b > budget) break;
+        bytes += b;
+        ++end;
+      }
+      const size_t nb = end - pos;
+      std::vector<int64_t> goff(nb + 1, 0), coff(nb + 1, 0);
+      int maxm = 0;
+      for (size_t b = 0; b < nb; ++b) {
+        const int m = mrows[todo[pos + b]];
+        goff[b + 1] = goff[b] + (int64_t)np * m;
+        coff[b + 1] = coff[b] + m;
+        maxm = std::max(maxm, m);
+      }
+      DevBuf<double> G(goff[nb]), tau(coff[nb]), norms(coff[nb]);
+      DevBuf<int> piv(coff[nb]), rk(nb);
+      Batch<ProxyProb> pb;
+      Batch<QrProb> qb;
+      for (size_t b = 0; b < nb; ++b) {
+        const int64_t i = todo[pos + b];
+        ProxyProb p;
+        const double side = (double)T.width[i] * hg;
+        const double hh = 0.5 * side;
+        double H = 0.0;
+        for (int a = 0; a < 3; ++a) p.c[a] = 0.0;
+        for (int a = 0; a < dim; ++a) {
+          const double blo = T.lo[a] + (double)T.cell_lo[i * dim + a] * hg;
+          p.c[a] = blo + hh;
+          H = std::max(H, std::max(p.c[a] - T.lo[a], T.lo[a] + T.w - p.c[a]));
+        }
+        p.h = hh;
+        p.H = std::max(H, 3.0 * hh * (1.0 + 1e-12));
+        if (t == D) {
+          p.xc = h->td.xs.p; p.ldxc = n; p.c0 = T.begin[i];
+        } else {
+          const int64_t cb = T.child_begin[i] - T.depth_off[t + 1];
+          p.xc = sx[t + 1].p; p.ldxc = (int64_t)sx[t + 1].n / dim; p.c0 = soff[t + 1][cb];
+        }
+        p.cols = mrows[i];
+        p.out = G.p + goff[b];
+        p.ldo = np;
+        pb.push(p);
+        QrProb q;
+        q.A = G.p + goff[b]; q.lda = np; q.m = np; q.n = mrows[i];
+        q.kmax = std::min(np, mrows[i]); q.rtol = h->tol;
+        q.piv = piv.p + coff[b]; q.tau = tau.p + coff[b]; q.rank = rk.p + b;
+        q.norms = norms.p + coff[b];
+        qb.push(q);
+      }
+      pb.upload(s);
+      proxy_launch(pb, h->kfn, dim, s);
+      qb.upload(s);
+      const int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
+      geqp3_launch(qb, 1, cl, np, s);
+      std::vector<int> hrk = rk.download(s);
+      std::vector<int> hpiv = piv.download(s);
+      // T = R11^{-1} R12 in place, then U
+      Batch<TrsmProb> tb;
+      Batch<IdProb> ib;
+      size_t ubytes = 0;
+      for (size_t b = 0; b < nb; ++b) ubytes += (size_t)mrows[todo[pos + b]] * hrk[b];
+      upool.emplace_back(new DevBuf<double>(std::max<size_t>(ubytes, 1)));
+      double* up = upool.back()->p;
+      for (size_t b = 0; b < nb; ++b) {
+        const int64_t i = todo[pos + b];
+        const int k = hrk[b], m = mrows[i];
+        rank[i] = k;
+        Uptr[i] = up;
+        if (k < m && k > 0) {
+          TrsmProb tp;
+          tp.T = G.p + goff[b]; tp.ldt = np;
+          tp.B = G.p + goff[b] + (int64_t)k * np; tp.ldb = np;
+          tp.n = k; tp.ncol = m - k; tp.lower = 0; tp.trans = 0;
+          tb.push(tp);
+        }
+        IdProb ip;
+        ip.G = G.p + goff[b]; ip.ldg = np; ip.piv = piv.p + coff[b]; ip.rank = rk.p + b;
+        ip.U = up; ip.m = m;
+        ib.push(ip);
+        up += (size_t)m * k;
+        // skeleton: candidates in pivot order
+        std::vector<int64_t>& sk = skel_local[i];
+        sk.resize(k);
+        for (int a = 0; a < k; ++a) {
+          const int pv = hpiv[coff[b] + a];
+          if (t == D) sk[a] = T.begin[i] + pv;
+          else {
+            int acc = 0;
+            int64_t cnode = T.child_begin[i];
+            for (; cnode < T.child_end[i]; ++cnode) {
+              if (pv < acc + rank[cnode]) break;
+              acc += rank[cnode];
+            }
+            sk[a] = skel_local[cnode][pv - acc];
+          }
+        }
+      }
+      tb.upload(s);
+      trsm_launch(tb, s);
+      ib.upload(s);
+      if (!ib.empty()) {
+        k_id_assemble<<<(unsigned)ib.size(), 256, 0, s>>>(ib.d.p);
+        SPD_LAUNCHED();
+      }
+      SPD_CUDA(cudaStreamSynchronize(s));
+      pos = end;
+    }
+    // per-depth skeleton offsets and coordinates
+    soff[t].assign(nn + 1, 0);
+    std::vector<int64_t> sidx;
+    for (int64_t k = 0; k < nn; ++k) {
+      soff[t][k + 1] = soff[t][k] + rank[o + k];
+      for (int64_t v : skel_local[o + k]) sidx.push_back(v);
+    }
+    const int64_t Kt = soff[t][nn];
+    sx[t].alloc((size_t)std::max<int64_t>(Kt, 1) * dim);
+    if (Kt > 0) {
+      DevBuf<int64_t> di;
+      di.upload(sidx, s);
+      k_gather_coords<<<ceil_div(Kt, 256), 256, 0, s>>>(h->td.xs.p, n, dim, di.p, Kt, sx[t].p);
+      SPD_LAUNCHED();
+      SPD_CUDA(cudaStreamSynchronize(s));
+    }
+    // sx[t].n is used as the leading dimension holder: dim * Kt entries
+    if (Kt == 0) sx[t].n = dim;
+  }
+
+  // global skeleton arrays (node-major) and bases
+  h->skel_off.assign(NN + 1, 0);
+  h->skel_idx.clear();
+  h->U_rows.assign(NN, 0);
+  h->U_off.assign(NN, 0);
+  int mxr = 0;
+  for (int64_t i = 0; i < NN; ++i) {
+    h->skel_off[i + 1] = h->skel_off[i] + rank[i];
+    for (int64_t v : skel_local[i]) h->skel_idx.push_back(v);
+    h->U_rows[i] = mrows[i];
+    mxr = std::max(mxr, rank[i]);
+  }
+  h->max_rank = mxr;
+  h->Ktot = h->skel_off[NN];
+  // one contiguous basis pool
+  int64_t btot = 0;
+  for (int64_t i = 0; i < NN; ++i) { h->U_off[i] = btot; btot += (int64_t)mrows[i] * rank[i]; }
+  h->basis.alloc(std::max<int64_t>(btot, 1));
+  for (int64_t i = 0; i < NN; ++i)
+    if ((int64_t)mrows[i] * rank[i] > 0)
+      SPD_CUDA(cudaMemcpyAsync(h->basis.p + h->U_off[i], Uptr[i],
+                               (size_t)mrows[i] * rank[i] * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  SPD_CUDA(cudaStreamSynchronize(s));
+  upool.clear();
+  const int64_t K = h->Ktot;
+  h->skel_x.alloc((size_t)std::max<int64_t>(K, 1) * dim);
+  if (K > 0) {
+    DevBuf<int64_t> di;
+    di.upload(h->skel_idx, s);
+    k_gather_coords<<<ceil_div(K, 256), 256, 0, s>>>(h->td.xs.p, n, dim, di.p, K, h->skel_x.p);
+    SPD_LAUNCHED();
+    SPD_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // couplings, once per unordered far pair
+  const int64_t nfar = (int64_t)T.far_idx.size();
+  h->far_boff.assign(nfar, 0);
+  h->far_trans.assign(nfar, 0);
+  int64_t ctot = 0;
+  std::vector<int64_t> own(nfar, -1);
+  for (int64_t i = 0; i < NN; ++i)
+    for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+      const int64_t j = T.far_idx[e];
+      if (i < j) { own[e] = ctot; ctot += (int64_t)rank[i] * rank[j]; }
+    }
+  for (int64_t i = 0; i < NN; ++i)
+    for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+      const int64_t j = T.far_idx[e];
+      if (i < j) { h->far_boff[e] = own[e]; h->far_trans[e] = 0; }
+      else {
+        const auto b0 = T.far_idx.begin() + T.far_off[j], b1 = T.far_idx.begin() + T.far_off[j + 1];
+        const auto it = std::lower_bound(b0, b1, i);
+        SPD_REQUIRE(it != b1 && *it == i, "h2_build: far lists are not symmetric");
+        h->far_boff[e] = own[it - T.far_idx.begin()];
+        h->far_trans[e] = 1;
+      }
+    }
+  h->coup.alloc(std::max<int64_t>(ctot, 1));
+  Batch<TileProb> tb;
+  for (int64_t i = 0; i < NN; ++i)
+    for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+      const int64_t j = T.far_idx[e];
+      if (!(i < j) || rank[i] == 0 || rank[j] == 0) continue;
+      TileProb p;
+      p.xr = h->skel_x.p; p.ldxr = K; p.r0 = h->skel_off[i]; p.rows = rank[i];
+      p.xc = h->skel_x.p; p.ldxc = K; p.c0 = h->skel_off[j]; p.cols = rank[j];
+      p.out = h->coup.p + own[e]; p.ldo = rank[i]; p.diag_add = 0.0;
+      tb.push(p);
+      if (tb.size() >= 200000) { tb.upload(s); tile_launch(tb, h->kfn, dim, s); tb.h.clear(); }
+    }
+  tb.upload(s);
+  tile_launch(tb, h->kfn, dim, s);
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------------------
+// products
+// ---------------------------------------------------------------------------------------
+static int lca_level(const TreeHost& T, int64_t i, int64_t j) {
+  while (i != j) { i = T.parent[i]; j = T.parent[j]; }
+  return T.level_of_depth(T.depth_of(i));
+}
+
+void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s) {
+  const TreeHost& T = h->th;
+  const int64_t n = T.n, K = std::max<int64_t>(h->Ktot, 1);
+  const int D = T.D;
+  p.ncol = ncol;
+  p.nslot = nslot;
+  const int W = ncol * nslot;
+  p.xs.alloc((size_t)n * ncol);
+  p.ys.alloc((size_t)n * W);
+  p.xhat.alloc((size_t)K * ncol);
+  p.yhat.alloc((size_t)K * W);
+  const double* Ub = h->basis.p;
+  auto U = [&](int64_t i) { return Ub + h->U_off[i]; };
+  // upward
+  p.up_leaf = GemmBatch();
+  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i)
+    if (h->rank(i) > 0)
+      p.up_leaf.add(p.xhat.p + h->skel_off[i], K, h->rank(i), ncol, U(i), h->U_rows[i], 1,
+                    p.xs.p + T.begin[i], n, 0, h->U_rows[i], 1.0, 0.0);
+  p.up.clear();
+  for (int t = D - 1; t >= 1; --t) {
+    p.up.emplace_back();
+    GemmBatch& g = p.up.back();
+    for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i)
+      if (h->rank(i) > 0)
+        g.add(p.xhat.p + h->skel_off[i], K, h->rank(i), ncol, U(i), h->U_rows[i], 1,
+              p.xhat.p + h->skel_off[T.child_begin[i]], K, 0, h->U_rows[i], 1.0, 0.0);
+  }
+  // coupling
+  p.coupling = GemmBatch();
+  for (int64_t i = 0; i < T.nn(); ++i) {
+    if (h->rank(i) == 0) continue;
+    const int lev = T.level_of_depth(T.depth_of(i));
+    for (int sl = 0; sl < nslot; ++sl) {
+      bool opened = false;
+      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+        const int64_t j = T.far_idx[e];
+        if (h->rank(j) == 0) continue;
+        if (nslot > 1 && lca_level(T, i, j) - 2 != sl) continue;
+        if (!opened) {
+          p.coupling.prob(p.yhat.p + h->skel_off[i] + (int64_t)sl * ncol * K, K, h->rank(i),
+                          ncol, 1.0, 1.0);
+          opened = true;
+        }
+        const int tr = h->far_trans[e];
+        p.coupling.seg(h->coup.p + h->far_boff[e], tr ? h->rank(j) : h->rank(i), tr,
+                       p.xhat.p + h->skel_off[j], K, 0, h->rank(j));
+      }
+    }
+    (void)lev;
+  }
+  // downward
+  p.down.clear();
+  for (int t = 1; t <= D - 1; ++t) {
+    p.down.emplace_back();
+    GemmBatch& g = p.down.back();
+    for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i) {
+      if (h->rank(i) == 0) continue;
+      const int lev = T.level_of_depth(t);
+      const int s0 = nslot == 1 ? 0 : lev - 1;
+      if (s0 >= nslot) continue;
+      const int64_t cs = (int64_t)s0 * ncol * K;
+      g.add(p.yhat.p + h->skel_off[T.child_begin[i]] + cs, K, h->U_rows[i], (nslot - s0) * ncol,
+            U(i), h->U_rows[i], 0, p.yhat.p + h->skel_off[i] + cs, K, 0, h->rank(i), 1.0, 1.0);
+    }
+  }
+  // leaves
+  p.leaf_out = GemmBatch();
+  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
+    p.leaf_out.prob(p.ys.p + T.begin[i], n, (int)T.size(i), W, 1.0, 0.0);
+    if (h->rank(i) > 0)
+      p.leaf_out.seg(U(i), h->U_rows[i], 0, p.yhat.p + h->skel_off[i], K, 0, h->rank(i));
+  }
+  // near field
+  p.near = NearBatch();
+  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
+    for (int sl = 0; sl < nslot; ++sl) {
+      bool opened = false;
+      for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
+        const int64_t j = T.near_idx[e];
+        if (nslot > 1) {
+          if (j == i) continue;
+          if (lca_level(T, i, j) - 2 != sl) continue;
+        }
+        if (!opened) {
+          p.near.prob(T.begin[i], (int)T.size(i), p.ys.p + T.begin[i] + (int64_t)sl * ncol * n, n,
+                      ncol, 1);
+          opened = true;
+        }
+        p.near.seg(T.begin[j], (int)T.size(j), p.xs.p + T.begin[j], n, j == i ? 1 : 0);
+      }
+    }
+  }
+  p.up_leaf.upload(s);
+  for (auto& g : p.up) g.upload(s);
+  p.coupling.upload(s);
+  for (auto& g : p.down) g.upload(s);
+  p.leaf_out.upload(s);
+  p.near.upload(s);
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s) {
+  p.up_leaf.launch(s);
+  for (const auto& g : p.up) g.launch(s);
+  SPD_CUDA(cudaMemsetAsync(p.yhat.p, 0, p.yhat.bytes(), s));
+  p.coupling.launch(s);
+  for (const auto& g : p.down) g.launch(s);
+  p.leaf_out.launch(s);
+  p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);
+}
+
+}  // namespace spd

@@ -1,0 +1,93 @@
+// Kernel-matrix evaluation on the device: dense tiles K(X_r, X_c) (+ shift on the
+// diagonal), proxy-point matrices K(P_i, X_cand) of the H^2 construction, and the
+// near-field product Y_i += sum_j K(X_i, X_j) X_j with tiles evaluated on the fly.
+#pragma once
+
+#include "dense.cuh"
+
+namespace spd {
+
+// Points are structure-of-arrays: coordinate a of point p at x[a * ldx + p].
+struct TileProb {
+  const double* xr;
+  int64_t ldxr, r0;
+  int rows;
+  const double* xc;
+  int64_t ldxc, c0;
+  int cols;
+  double* out;
+  int64_t ldo;
+  double diag_add;   // added where r0 + i == c0 + j and xr == xc (self block)
+};
+void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStream_t s);
+
+// Proxy points of one node (reading of the proxy point method): 6 cube surfaces of
+// half-width h_t = 3h + (H - 3h) (t/5)^2 around the cell centre c, each face carrying a
+// q x q cell-centred grid (q = 8 in 3D, 32 points per edge in 2D).
+constexpr int PROXY_SHELLS = 6;
+__host__ __device__ inline int proxy_grid(int dim) { return dim == 3 ? 8 : 32; }
+__host__ __device__ inline int proxy_count(int dim) {
+  const int q = proxy_grid(dim);
+  return PROXY_SHELLS * 2 * dim * (dim == 3 ? q * q : q);
+}
+struct ProxyProb {
+  double c[3];
+  double h, H;
+  const double* xc;
+  int64_t ldxc, c0;
+  int cols;
+  double* out;     // proxy_count(dim) x cols, column-major
+  int64_t ldo;
+};
+void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s);
+
+// Near-field product.  Problem: rows [row0, row0 + rows) of the sorted points; output
+// out (rows x ncol, ld ldo), accumulated (beta = 1) or overwritten (beta = 0).
+// Segment: columns [col0, col0 + cols) of the sorted points with their input block x
+// (cols x ncol, ld ldx); self = 1 adds shift * x on the diagonal.
+struct NearProb {
+  int64_t row0;
+  int rows;
+  double* out;
+  int64_t ldo;
+  int ncol;
+  int seg0, seg1;
+  int beta;
+};
+struct NearSeg {
+  int64_t col0;
+  int cols;
+  const double* x;
+  int64_t ldx;
+  int self;
+};
+struct NearBatch {
+  std::vector<NearProb> probs;
+  std::vector<NearSeg> segs;
+  std::vector<int2> work;   // (prob, first column)
+  DevBuf<NearProb> d_probs;
+  DevBuf<NearSeg> d_segs;
+  DevBuf<int2> d_work;
+  int cb = 8;               // column block per CTA (8, 16, 32 or 64)
+  void prob(int64_t row0, int rows, double* out, int64_t ldo, int ncol, int beta) {
+    NearProb p;
+    p.row0 = row0; p.rows = rows; p.out = out; p.ldo = ldo; p.ncol = ncol; p.beta = beta;
+    p.seg0 = p.seg1 = (int)segs.size();
+    probs.push_back(p);
+  }
+  void seg(int64_t col0, int cols, const double* x, int64_t ldx, int self) {
+    NearSeg g;
+    g.col0 = col0; g.cols = cols; g.x = x; g.ldx = ldx; g.self = self;
+    segs.push_back(g);
+    probs.back().seg1 = (int)segs.size();
+  }
+  bool empty() const { return probs.empty(); }
+  void upload(cudaStream_t s);
+  void launch(const KernelFn& k, const double* xs, int64_t ldx, int dim, cudaStream_t s) const;
+  void run(const KernelFn& k, const double* xs, int64_t ldx, int dim, cudaStream_t s) {
+    upload(s);
+    launch(k, xs, ldx, dim, s);
+  }
+};
+
+}  // namespace spd
