@@ -166,3 +166,114 @@ spdhss_status h2_destroy(h2_handle h) {
 }
 
 }  // extern "C"
+
+// ---- SPD HSS -------------------------------------------------------------------------
+#include "spdhss.cuh"
+
+extern "C" {
+
+spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
+                           uint64_t seed, void* stream, hss_handle* out) {
+  return spd::guarded("spdhss_build", [&] {
+    SPD_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    SPD_REQUIRE(h2 != nullptr, "NULL H2 handle");
+    SPD_REQUIRE(rank >= 1, "rank must be >= 1");
+    SPD_REQUIRE(oversample >= 0, "oversample must be >= 0");
+    SPD_REQUIRE(omega == nullptr || spd::is_device_pointer(omega), "omega must be a device pointer");
+    std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
+    spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream);
+    *out = hs.release();
+  });
+}
+
+spdhss_status hss_matmul(hss_handle hs, const double* X, double* Y, int nrhs, int64_t ld,
+                         void* stream) {
+  return spd::guarded("hss_matmul", [&] {
+    SPD_REQUIRE(hs && X && Y, "NULL argument");
+    SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    SPD_REQUIRE(ld >= hs->h2->th.n, "ld must be >= n");
+    spd::hss_matmul_impl(hs, X, Y, nrhs, ld, (cudaStream_t)stream);
+  });
+}
+
+spdhss_status hss_info(hss_handle hs, int64_t* info) {
+  return spd::guarded("hss_info", [&] {
+    SPD_REQUIRE(hs && info, "NULL argument");
+    for (int k = 0; k < 8; ++k) info[k] = 0;
+    info[0] = hs->L;
+    int mr = 0;
+    for (int v : hs->rk) mr = std::max(mr, v);
+    info[1] = mr;
+    info[2] = (int64_t)hs->stored_bytes();
+    info[3] = (int64_t)hs->rk.size();
+  });
+}
+
+spdhss_status hss_destroy(hss_handle hs) {
+  return spd::guarded("hss_destroy", [&] { delete hs; });
+}
+
+}  // extern "C"
+
+// ---- ULV and PCG ---------------------------------------------------------------------
+#include "ulv.cuh"
+
+namespace spd {
+void pcg_impl(const spdhss_h2_s* h2, spdhss_ulv_s* u, const double* B, double* X, int nrhs,
+              int64_t ld, double tol, int maxit, int* iters_out, double* relres_out,
+              bool& converged, cudaStream_t s);
+}
+
+extern "C" {
+
+spdhss_status ulv_factor(hss_handle hs, void* stream, ulv_handle* out) {
+  return spd::guarded("ulv_factor", [&] {
+    SPD_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    SPD_REQUIRE(hs != nullptr, "NULL HSS handle");
+    std::unique_ptr<spdhss_ulv_s> u(new spdhss_ulv_s());
+    spd::ulv_factor_impl(u.get(), hs, (cudaStream_t)stream);
+    *out = u.release();
+  });
+}
+
+spdhss_status ulv_solve(ulv_handle u, const double* B, double* X, int nrhs, int64_t ld,
+                        void* stream) {
+  return spd::guarded("ulv_solve", [&] {
+    SPD_REQUIRE(u && B && X, "NULL argument");
+    SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const int64_t n = u->hs->h2->th.n;
+    SPD_REQUIRE(ld >= n, "ld must be >= n");
+    cudaStream_t s = (cudaStream_t)stream;
+    spd::UlvPlan& P = spd::ulv_plan(u, nrhs, s);
+    const int64_t* perm = u->hs->h2->td.perm.p;
+    spd::permute_to_sorted(B, ld, P.bw[0].p, n, nrhs, perm, s);
+    spd::ulv_solve_sorted(u, P, s);
+    spd::permute_from_sorted(P.bw[0].p, X, ld, n, nrhs, perm, s);
+  });
+}
+
+spdhss_status ulv_destroy(ulv_handle u) {
+  return spd::guarded("ulv_destroy", [&] { delete u; });
+}
+
+spdhss_status pcg_solve(h2_handle h2, ulv_handle u, const double* B, double* X, int nrhs,
+                        int64_t ld, double relres_tol, int maxit, int* iters_out,
+                        double* relres_out, void* stream) {
+  spdhss_status st = spd::guarded("pcg_solve", [&] {
+    SPD_REQUIRE(h2 && u && B && X, "NULL argument");
+    SPD_REQUIRE(u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
+    SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    SPD_REQUIRE(ld >= h2->th.n, "ld must be >= n");
+    SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
+    SPD_REQUIRE(maxit >= 1, "maxit must be >= 1");
+    bool conv = false;
+    spd::pcg_impl(h2, u, B, X, nrhs, ld, relres_tol, maxit, iters_out, relres_out, conv,
+                  (cudaStream_t)stream);
+    if (!conv) throw spd::Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
+  });
+  return st;
+}
+
+}  // extern "C"

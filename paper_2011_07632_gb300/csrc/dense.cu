@@ -195,12 +195,29 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmProb* __restrict__ probs
   }
 }
 
-void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
-  if (b.empty()) return;
+static std::vector<int2> trsm_work(const Batch<TrsmProb>& b) {
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
     if (b.h[p].n > 0)
       for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+  return work;
+}
+
+void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
+  std::vector<int2> w = trsm_work(b);
+  b.work.upload(w, s);
+  b.nwork = (int64_t)w.size();
+}
+
+void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
+  if (b.empty()) return;
+  if (b.nwork >= 0) {
+    if (b.nwork == 0) return;
+    k_trsm<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork);
+    SPD_LAUNCHED();
+    return;
+  }
+  std::vector<int2> work = trsm_work(b);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);
@@ -438,11 +455,28 @@ __global__ void __launch_bounds__(256) k_hh_apply(const HhApplyProb* __restrict_
   }
 }
 
-void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) {
-  if (b.empty()) return;
+static std::vector<int2> hh_work(const Batch<HhApplyProb>& b) {
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
     for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+  return work;
+}
+
+void householder_prepare(Batch<HhApplyProb>& b, cudaStream_t s) {
+  std::vector<int2> w = hh_work(b);
+  b.work.upload(w, s);
+  b.nwork = (int64_t)w.size();
+}
+
+void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) {
+  if (b.empty()) return;
+  if (b.nwork >= 0) {
+    if (b.nwork == 0) return;
+    k_hh_apply<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork, trans);
+    SPD_LAUNCHED();
+    return;
+  }
+  std::vector<int2> work = hh_work(b);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);

@@ -63,6 +63,9 @@ template <class P>
 struct Batch {
   std::vector<P> h;
   DevBuf<P> d;
+  // optional prepared (problem, column) work list of the column-parallel kernels
+  DevBuf<int2> work;
+  int64_t nwork = -1;
   void upload(cudaStream_t s) { d.upload(h, s); }
   size_t size() const { return h.size(); }
   bool empty() const { return h.empty(); }
@@ -90,6 +93,8 @@ struct TrsmProb {
   int lower, trans;
 };
 void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s);
+// builds the (problem, column) work list once so that later launches need no allocation
+void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s);
 
 // ---- batched Householder QR with optional column pivoting -----------------------------
 // On exit A holds R in its upper triangle (first `rank` rows, all columns in pivot order)
@@ -121,6 +126,7 @@ struct HhApplyProb {
   int m, ncol;
 };
 void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s);
+void householder_prepare(Batch<HhApplyProb>& b, cudaStream_t s);
 
 // Q(:, 0:k) explicitly into Q (m x kcols, only columns < *k written; others zeroed).
 struct FormQProb {

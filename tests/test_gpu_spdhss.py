@@ -1,0 +1,91 @@
+"""GPU parity: SPD-HSS construction (Alg. 5.3) against the oracle's quadratic
+construction on the same matrix and the same sketch; HSS properties at small n."""
+import numpy as np
+import pytest
+
+from oracle import h2 as OH
+from oracle import kernels as OK
+from oracle import spdhss as OS
+from oracle import tree as OT
+from paper_2011_07632_gb300 import inputs
+
+from gpu_util import need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def unsort(Hs, perm):
+    H = np.empty_like(Hs)
+    H[np.ix_(perm, perm)] = Hs
+    return H
+
+
+def gpu_dense(hs, n):
+    return hs.matmul(np.eye(n)).cpu().numpy()
+
+
+def oracle_dense(X, leaf, kind, ell, sigma, tol, Om, r):
+    tr = OT.build_tree(X, leaf)
+    if tol == 0.0:
+        M = OK.dense_matrix(OK.NAMES[kind], ell, sigma, X[tr.perm])
+    else:
+        M = OH.dense(OH.build_h2(tr, X, OK.NAMES[kind], ell, sigma, tol))
+    hss = OS.build_spdhss(tr, M, Om[tr.perm], r)
+    return unsort(OS.assemble_dense(hss), tr.perm), unsort(M, tr.perm)
+
+
+CASES = [
+    # n, dim, leaf, kernel, ell, sigma, H2 tol, r
+    (4096, 3, 64, "exp", 1.0, 1e-2, 1e-8, 50),
+    (2048, 2, 32, "matern32", 0.2, 1e-3, 1e-8, 20),
+    (1000, 3, 16, "gauss", 0.3, 1e-4, 1e-6, 8),
+    (1500, 3, 40, "imq", 0.5, 1e-3, 1e-8, 30),
+]
+
+
+@pytest.mark.parametrize("n,dim,leaf,kind,ell,sigma,tol,r", CASES)
+def test_hss_matches_oracle(n, dim, leaf, kind, ell, sigma, tol, r):
+    api = need_gpu()
+    X = inputs.uniform_cube(n, dim, 0)
+    Om = inputs.sketch(n, r + 10, 2)
+    h = api.H2(X, kind, ell, sigma, leaf, tol)
+    hs = api.HSS(h, r, 10, omega=Om)
+    Hg = gpu_dense(hs, n)
+    Ho, M = oracle_dense(X, leaf, kind, ell, sigma, tol, Om, r)
+    assert rel(Hg, Ho) < 1e-10
+
+
+def test_full_rank_hss_equals_matrix():
+    api = need_gpu()
+    n = 600
+    X = inputs.uniform_cube(n, 3, 4)
+    Om = inputs.sketch(n, n + 10, 5)
+    h = api.H2(X, "exp", 0.5, 1e-2, 32, 0.0)
+    hs = api.HSS(h, n, 10, omega=Om)
+    A = OK.dense_matrix(OK.EXP, 0.5, 1e-2, X)
+    assert rel(gpu_dense(hs, n), A) < 1e-12
+
+
+@pytest.mark.parametrize("kind,sigma,r", [("gauss", 1e-6, 4), ("matern32", 1e-5, 10)])
+def test_gpu_hss_is_spd(kind, sigma, r):
+    api = need_gpu()
+    n = 512
+    X = inputs.uniform_cube(n, 3, 6)
+    h = api.H2(X, kind, 0.2, sigma, 16, 1e-8)
+    hs = api.HSS(h, r, 10, seed=11)           # sketch drawn on the device
+    Hg = gpu_dense(hs, n)
+    Hg = 0.5 * (Hg + Hg.T)
+    assert np.linalg.eigvalsh(Hg).min() > 0.0
+
+
+def test_device_sketch_statistics():
+    """With omega=None the library draws Omega from Philox4x32-10: the HSS it yields is
+    an approximation of the same quality as with a host-drawn Gaussian sketch."""
+    api = need_gpu()
+    n = 4096
+    X = inputs.uniform_cube(n, 3, 0)
+    h = api.H2(X, "exp", 1.0, 1e-2, 64, 1e-8)
+    A = OK.dense_matrix(OK.EXP, 1.0, 1e-2, X)
+    e_dev = rel(gpu_dense(api.HSS(h, 50, 10, seed=3), n), A)
+    e_host = rel(gpu_dense(api.HSS(h, 50, 10, omega=inputs.sketch(n, 60, 2)), n), A)
+    assert e_dev < 3 * e_host and e_host < 3 * e_dev
