@@ -29,6 +29,7 @@
 #ifndef SPDHSS_H
 #define SPDHSS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -172,6 +173,15 @@ int64_t spdhss_launch_count(void);
 
 /* Library version string. */
 const char* spdhss_version(void);
+
+/* Kernel timing for diagnostics.  spdhss_profile(1) clears the counters and brackets every
+ * later launch with CUDA events on its stream (adds a small host cost per launch);
+ * spdhss_profile(0) stops.  spdhss_profile_report writes a NUL-terminated JSON object
+ * {"family": {"launches", "ms", "flops", "bytes"}, ...} into the HOST buffer buf of len
+ * bytes (truncated if short) and returns the length the full report needs.  flops and
+ * bytes are the algorithmic FP64 operations and operand bytes of the timed launches. */
+void spdhss_profile(int enable);
+int64_t spdhss_profile_report(char* buf, int64_t len);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,9 @@
 // C ABI entry points (include/spdhss.h): argument checks, error capture, and the H^2 calls.
 #include <atomic>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "h2.cuh"
 
@@ -11,6 +14,68 @@ static std::atomic<int64_t> g_launches{0};
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---- per-kernel-family timing with CUDA events on the launching stream ------------------
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+static std::mutex g_pm;
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+struct ProfAcc { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
+static std::map<std::string, ProfAcc> g_acc;
+
+static cudaEvent_t pool_event() {
+  if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
+  cudaEvent_t e;
+  SPD_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+static void prof_drain() {
+  for (auto& r : g_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ProfAcc& a = g_acc[r.name];
+      a.launches += 1;
+      a.ms += ms;
+      a.flops += r.flops;
+      a.bytes += r.bytes;
+    } else {
+      cudaGetLastError();
+    }
+    g_pool.push_back(r.a);
+    g_pool.push_back(r.b);
+  }
+  g_recs.clear();
+}
+
+bool prof_enabled() { return g_prof; }
+
+int prof_begin(const char* name, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_pm);
+  if (g_recs.size() >= 200000) prof_drain();
+  ProfRec r{name, pool_event(), pool_event(), 0.0, 0.0};
+  SPD_CUDA(cudaEventRecord(r.a, s));
+  g_recs.push_back(r);
+  return (int)g_recs.size() - 1;
+}
+
+void prof_add_flops(int slot, double flops) {
+  std::lock_guard<std::mutex> lk(g_pm);
+  if (slot >= 0 && slot < (int)g_recs.size()) g_recs[slot].flops += flops;
+}
+
+void prof_end(int slot, cudaStream_t s, double flops, double bytes) {
+  std::lock_guard<std::mutex> lk(g_pm);
+  if (slot < 0 || slot >= (int)g_recs.size()) return;
+  g_recs[slot].flops = flops;
+  g_recs[slot].bytes = bytes;
+  cudaEventRecord(g_recs[slot].b, s);
+}
 
 template <class F>
 spdhss_status guarded(const char* where, F&& f) {
@@ -38,6 +103,37 @@ extern "C" {
 const char* spdhss_last_error(void) { return g_last_error.c_str(); }
 int64_t spdhss_launch_count(void) { return g_launches.load(); }
 const char* spdhss_version(void) { return "spdhss-gb300 0.1 (sm_103a, fp64)"; }
+
+void spdhss_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_pm);
+  if (enable) {
+    prof_drain();
+    g_acc.clear();
+  }
+  g_prof = enable != 0;
+}
+
+int64_t spdhss_profile_report(char* buf, int64_t len) {
+  std::lock_guard<std::mutex> lk(g_pm);
+  prof_drain();
+  std::string out = "{";
+  bool first = true;
+  char tmp[256];
+  for (const auto& kv : g_acc) {
+    std::snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+                  first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms,
+                  kv.second.flops, kv.second.bytes);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  if (buf && len > 0) {
+    const size_t n = std::min<size_t>((size_t)len - 1, out.size());
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return (int64_t)out.size() + 1;
+}
 
 spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
                        int leaf_size, double tol, void* stream, h2_handle* out) {

@@ -21,6 +21,32 @@ struct Error : std::runtime_error {
 void set_last_error(const std::string& msg);
 void count_launches(int64_t k = 1);
 
+// Optional per-kernel-family timing: when enabled, every instrumented launch is bracketed
+// by CUDA events on its stream; flops are the algorithmic FP64 operations of the launch.
+bool prof_enabled();
+int prof_begin(const char* name, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s, double flops, double bytes);
+// add algorithmic flops to a finished record (work known only after the launch, e.g. a rank)
+void prof_add_flops(int slot, double flops);
+struct ProfScope {
+  int slot;
+  cudaStream_t s;
+  double flops, bytes;
+  ProfScope(const char* name, cudaStream_t st, double f = 0.0, double b = 0.0)
+      : slot(prof_enabled() ? prof_begin(name, st) : -1), s(st), flops(f), bytes(b) {}
+  ~ProfScope() {
+    if (slot >= 0) prof_end(slot, s, flops, bytes);
+  }
+};
+
+// Householder QR flops for k steps on an m x n matrix: per step, every trailing column
+// takes a dot product and an update (4 flops per entry) and a recomputed norm (2 flops).
+inline double qr_flops(int64_t m, int64_t n, int64_t k, bool pivot) {
+  double f = 0.0;
+  for (int64_t j = 0; j < k; ++j) f += (double)(m - j) * (double)(n - j - 1) * (pivot ? 6.0 : 4.0);
+  return f;
+}
+
 #define SPD_CUDA(x)                                                                        \
   do {                                                                                     \
     cudaError_t e_ = (x);                                                                  \

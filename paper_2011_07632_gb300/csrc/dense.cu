@@ -89,11 +89,90 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
   }
 }
 
+// Skinny variant for N <= 32 columns: 64-row tiles, 256 threads = 64 rows x 4 column
+// groups of NB/4 columns each, K step 32.  No FMA is spent on padding columns.
+template <int NB>
+__global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ probs,
+                                                const GemmSeg* __restrict__ segs,
+                                                const int4* __restrict__ tiles) {
+  constexpr int MB = 64, KB = 32, CPT = NB / 4;
+  const int4 t = tiles[blockIdx.x];
+  const GemmProb P = probs[t.x];
+  const int m0 = t.y, n0 = t.z;
+  __shared__ double As[KB][MB + 1];
+  __shared__ double Bs[KB][NB + 1];
+  const int tid = threadIdx.x;
+  const int row = tid & 63, cg = tid >> 6;
+  double acc[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) acc[c] = 0.0;
+  for (int sg = P.seg0; sg < P.seg1; ++sg) {
+    const GemmSeg S = segs[sg];
+    for (int k0 = 0; k0 < S.K; k0 += KB) {
+#pragma unroll
+      for (int r = 0; r < (MB * KB) / 256; ++r) {
+        const int e = tid + 256 * r;
+        int mm, kk;
+        if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < P.M && gk < S.K)
+          v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
+        As[kk][mm] = v;
+      }
+      for (int e = tid; e < KB * NB; e += 256) {
+        int nn, kk;
+        if (!S.tB) { kk = e % KB; nn = e / KB; } else { nn = e % NB; kk = e / NB; }
+        const int gn = n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < P.N && gk < S.K)
+          v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < KB; ++kk) {
+        const double a = As[kk][row];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[c] = fma(a, Bs[kk][cg * CPT + c], acc[c]);
+      }
+      __syncthreads();
+    }
+  }
+  const int gm = m0 + row;
+  if (gm < P.M) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int gn = n0 + cg * CPT + c;
+      if (gn < P.N) {
+        double* cp = P.C + gm + (int64_t)gn * P.ldc;
+        double v = P.alpha * acc[c];
+        if (P.beta != 0.0) v += P.beta * (*cp);
+        *cp = v;
+      }
+    }
+  }
+}
+
 void GemmBatch::upload(cudaStream_t s) {
   tiles.clear();
-  for (int p = 0; p < (int)probs.size(); ++p)
-    for (int m0 = 0; m0 < probs[p].M; m0 += GM)
-      for (int n0 = 0; n0 < probs[p].N; n0 += GN) tiles.push_back(make_int4(p, m0, n0, 0));
+  flops = 0.0;
+  bytes = 0.0;
+  int maxn = 0;
+  for (const auto& p : probs) maxn = std::max(maxn, p.N);
+  nb = maxn <= 8 ? 8 : (maxn <= 16 ? 16 : (maxn <= 32 ? 32 : 0));
+  const int tm = nb ? 64 : GM, tn = nb ? nb : GN;
+  for (int p = 0; p < (int)probs.size(); ++p) {
+    for (int m0 = 0; m0 < probs[p].M; m0 += tm)
+      for (int n0 = 0; n0 < probs[p].N; n0 += tn) tiles.push_back(make_int4(p, m0, n0, 0));
+    double kk = 0.0;
+    for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
+      kk += segs[g].K;
+      bytes += 8.0 * ((double)probs[p].M * segs[g].K + (double)segs[g].K * probs[p].N);
+    }
+    flops += 2.0 * probs[p].M * (double)probs[p].N * kk;
+    bytes += 8.0 * (double)probs[p].M * probs[p].N * (probs[p].beta != 0.0 ? 2.0 : 1.0);
+  }
   d_segs.upload(segs, s);
   d_probs.upload(probs, s);
   d_tiles.upload(tiles, s);
@@ -101,9 +180,16 @@ void GemmBatch::upload(cudaStream_t s) {
 
 void GemmBatch::launch(cudaStream_t s) const {
   const int64_t nt = (int64_t)tiles.size();
+  if (nt == 0) return;
+  ProfScope ps(tag, s, flops, bytes);
   for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
-    const int nb = (int)std::min<int64_t>(nt - b0, 2147483647LL);
-    k_gemm<<<nb, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0);
+    const int g = (int)std::min<int64_t>(nt - b0, 2147483647LL);
+    switch (nb) {
+      case 8: k_gemm_n<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
+      case 16: k_gemm_n<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
+      case 32: k_gemm_n<32><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
+      default: k_gemm<<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
+    }
     SPD_LAUNCHED();
   }
 }
@@ -149,6 +235,9 @@ __global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ pro
 
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
   if (b.empty()) return;
+  double f = 0.0;
+  for (const auto& p : b.h) f += (double)p.n * p.n * p.n / 3.0;
+  ProfScope ps("potrf", s, f);
   k_potrf<<<(unsigned)b.size(), 256, 0, s>>>(b.d.p, d_info);
   SPD_LAUNCHED();
 }
@@ -211,8 +300,11 @@ void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
 
 void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
   if (b.empty()) return;
+  double f = 0.0;
+  for (const auto& p : b.h) f += (double)p.n * p.n * p.ncol;
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
+    ProfScope ps("trsm", s, f);
     k_trsm<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork);
     SPD_LAUNCHED();
     return;
@@ -222,8 +314,11 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
   DevBuf<int2> dw;
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
-  k_trsm<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
-  SPD_LAUNCHED();
+  {
+    ProfScope ps("trsm", s, f);
+    k_trsm<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
+    SPD_LAUNCHED();
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -403,8 +498,8 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
   cl.sync();
 }
 
-void geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s) {
-  if (b.empty()) return;
+int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s) {
+  if (b.empty()) return -1;
   cluster = std::max(1, std::min(cluster, 8));
   const size_t smem = (size_t)std::max(1, max_m) * sizeof(double);
   SPD_REQUIRE(smem <= 200 * 1024, "geqp3: matrix too tall for the shared-memory reflector");
@@ -425,8 +520,14 @@ void geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cud
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, (const QrProb*)b.d.p, pivot));
-  SPD_LAUNCHED();
+  int slot;
+  {
+    ProfScope ps(pivot ? "geqp3" : "geqrf", s);
+    slot = ps.slot;
+    SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, (const QrProb*)b.d.p, pivot));
+    SPD_LAUNCHED();
+  }
+  return slot;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -472,6 +573,7 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   if (b.empty()) return;
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
+    ProfScope ps("householder", s);
     k_hh_apply<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork, trans);
     SPD_LAUNCHED();
     return;
@@ -481,8 +583,11 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   DevBuf<int2> dw;
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
-  k_hh_apply<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw, trans);
-  SPD_LAUNCHED();
+  {
+    ProfScope ps("householder", s);
+    k_hh_apply<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw, trans);
+    SPD_LAUNCHED();
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -520,8 +625,11 @@ void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s) {
   DevBuf<int2> dw;
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
-  k_form_q<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
-  SPD_LAUNCHED();
+  {
+    ProfScope ps("form_q", s);
+    k_form_q<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
+    SPD_LAUNCHED();
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -544,6 +652,7 @@ __global__ void k_copy(const CopyProb* __restrict__ probs, int ident) {
 
 static void copy_common(const Batch<CopyProb>& b, int ident, cudaStream_t s) {
   if (b.empty()) return;
+  ProfScope ps("copy", s);
   int64_t mx = 1;
   for (const auto& p : b.h) mx = std::max<int64_t>(mx, (int64_t)p.m * p.n);
   const int gx = (int)std::min<int64_t>(ceil_div(mx, 256), 64);

@@ -53,6 +53,9 @@ struct GemmBatch {
   void run(cudaStream_t s) { upload(s); launch(s); }
   void clear() { segs.clear(); probs.clear(); tiles.clear(); }
   std::vector<int4> tiles;   // (prob, m0, n0, 0)
+  const char* tag = "gemm";
+  int nb = 0;                        // 8/16/32: skinny kernel column block; 0: 64x64 tiles
+  double flops = 0.0, bytes = 0.0;   // algorithmic work of one launch
   DevBuf<GemmSeg> d_segs;
   DevBuf<GemmProb> d_probs;
   DevBuf<int4> d_tiles;
@@ -112,7 +115,9 @@ struct QrProb {
   int* rank;      // 1 entry
   double* norms;  // n entries of scratch
 };
-void geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s);
+// returns the profiler record of the launch (-1 when profiling is off); the caller adds
+// the flops with prof_add_flops once the ranks are known
+int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s);
 
 // Apply the k reflectors stored in (V, ldv, tau) to B (m x ncol) in place:
 // trans=1: B <- Q^T B;  trans=0: B <- Q B.   Q = H_0 H_1 ... H_{k-1}.

@@ -169,8 +169,13 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
       proxy_launch(pb, h->kfn, dim, s);
       qb.upload(s);
       const int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
-      geqp3_launch(qb, 1, cl, np, s);
+      const int pslot = geqp3_launch(qb, 1, cl, np, s);
       std::vector<int> hrk = rk.download(s);
+      if (pslot >= 0) {
+        double f = 0.0;
+        for (size_t b = 0; b < nb; ++b) f += qr_flops(np, mrows[todo[pos + b]], hrk[b], true);
+        prof_add_flops(pslot, f);
+      }
       std::vector<int> hpiv = piv.download(s);
       // T = R11^{-1} R12 in place, then U
       Batch<TrsmProb> tb;
@@ -420,6 +425,10 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
       }
     }
   }
+  p.coupling.tag = "h2_coupling";
+  p.up_leaf.tag = p.leaf_out.tag = "h2_basis";
+  for (auto& g : p.up) g.tag = "h2_basis";
+  for (auto& g : p.down) g.tag = "h2_basis";
   p.up_leaf.upload(s);
   for (auto& g : p.up) g.upload(s);
   p.coupling.upload(s);

@@ -38,8 +38,11 @@ void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStrea
   if (work.empty()) return;
   DevBuf<int4> dw;
   dw.upload(work, s);
-  k_tiles<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
-  SPD_LAUNCHED();
+  {
+    ProfScope ps("tile", s);
+    k_tiles<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
+    SPD_LAUNCHED();
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -112,8 +115,11 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
   if (work.empty()) return;
   DevBuf<int4> dw;
   dw.upload(work, s);
-  k_proxy<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
-  SPD_LAUNCHED();
+  {
+    ProfScope ps("proxy", s);
+    k_proxy<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
+    SPD_LAUNCHED();
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -203,8 +209,16 @@ void NearBatch::upload(cudaStream_t s) {
   int mx = 1;
   for (const auto& p : probs) mx = std::max(mx, p.ncol);
   cb = mx <= 8 ? 8 : (mx <= 16 ? 16 : (mx <= 32 ? 32 : 64));
-  for (int p = 0; p < (int)probs.size(); ++p)
+  flops = 0.0;
+  evals = 0.0;
+  for (int p = 0; p < (int)probs.size(); ++p) {
     for (int c0 = 0; c0 < probs[p].ncol; c0 += cb) work.push_back(make_int2(p, c0));
+    for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
+      const double e = (double)probs[p].rows * segs[g].cols;
+      evals += e;
+      flops += 2.0 * e * probs[p].ncol;
+    }
+  }
   d_probs.upload(probs, s);
   d_segs.upload(segs, s);
   d_work.upload(work, s);
@@ -213,6 +227,7 @@ void NearBatch::upload(cudaStream_t s) {
 void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
                        cudaStream_t s) const {
   if (work.empty()) return;
+  ProfScope ps("near", s, flops, 8.0 * evals);
   const unsigned g = (unsigned)work.size();
   switch (cb) {
     case 8: k_near<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;

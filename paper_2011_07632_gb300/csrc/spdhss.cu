@@ -305,8 +305,13 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
       }
       cb.upload(s); copy_launch(cb, s);
       qb.upload(s);
-      geqp3_launch(qb, 1, 1, maxm, s);
+      const int pslot = geqp3_launch(qb, 1, 1, maxm, s);
       std::vector<int> hr = rkd.download(s);
+      if (pslot >= 0) {
+        double f = 0.0;
+        for (int64_t a = 0; a < nn; ++a) f += qr_flops(mrow[o + a], sc, hr[a], true);
+        prof_add_flops(pslot, f);
+      }
       for (int64_t a = 0; a < nn; ++a) rk[o + a] = mrow[o + a] > 0 ? hr[a] : 0;
     }
     // sizes that depend on the ranks

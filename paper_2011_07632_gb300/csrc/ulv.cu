@@ -171,7 +171,12 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
         qb.push(q);
       }
       qb.upload(s);
-      geqp3_launch(qb, 0, 1, maxm, s);
+      const int pslot = geqp3_launch(qb, 0, 1, maxm, s);
+      if (pslot >= 0) {
+        double f = 0.0;
+        for (const auto& q : qb.h) f += qr_flops(q.m, q.n, q.kmax, false);
+        prof_add_flops(pslot, f);
+      }
       std::vector<const double*> src;
       std::vector<double*> dst;
       std::vector<int64_t> lds;
@@ -404,6 +409,7 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
     P.q[k].upload(s); householder_prepare(P.q[k], s);
     P.fw[k].upload(s); trsm_prepare(P.fw[k], s);
     P.bk[k].upload(s); trsm_prepare(P.bk[k], s);
+    P.upd_f[k].tag = P.upd_b[k].tag = "ulv_solve_gemm";
     P.upd_f[k].upload(s);
     P.upd_b[k].upload(s);
     P.up[k].upload(s);

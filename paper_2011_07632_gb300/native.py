@@ -73,6 +73,10 @@ def lib():
         L.spdhss_launch_count.argtypes = []
         L.spdhss_version.restype = ctypes.c_char_p
         L.spdhss_version.argtypes = []
+        L.spdhss_profile.restype = None
+        L.spdhss_profile.argtypes = [ctypes.c_int]
+        L.spdhss_profile_report.restype = ctypes.c_int64
+        L.spdhss_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
         _lib = L
     return _lib
 
@@ -86,5 +90,14 @@ def launch_count() -> int:
     return int(lib().spdhss_launch_count())
 
 
+def profile_report() -> dict:
+    import json
+    need = int(lib().spdhss_profile_report(None, 0))
+    buf = ctypes.create_string_buffer(need + 16)
+    lib().spdhss_profile_report(buf, need + 16)
+    return json.loads(buf.value.decode())
+
+
 def exported_symbols() -> list:
-    return list(_SIGS) + ["spdhss_last_error", "spdhss_launch_count", "spdhss_version"]
+    return list(_SIGS) + ["spdhss_last_error", "spdhss_launch_count", "spdhss_version",
+                          "spdhss_profile", "spdhss_profile_report"]
