@@ -151,6 +151,26 @@ spdhss_status ulv_solve(ulv_handle ulv, const double* B, double* X, int nrhs, in
 
 spdhss_status ulv_destroy(ulv_handle ulv);
 
+/* X = H^{-1} B like ulv_solve, for callers that cannot allocate device memory (an
+ * application whose device memory is all reserved by its own allocator, or a latency-
+ * critical path that cannot accept the device-wide synchronization of cudaMalloc and
+ * cudaFree).  The paper has no counterpart: this is a property of the library, not of the
+ * method.  The call allocates nothing: it works in two fixed device arrays that are part of
+ * the library image (48 MiB of level buffers, 8 MiB of launch descriptors), held by every
+ * GPU that loads the library until the process exits.
+ *   B, X     DEVICE pointers, n x nrhs column-major, leading dimension ld >= n, original
+ *            point order; B and X may be the same array.
+ *   Limit:   the level buffers need about (n + sum of the block sizes above the leaves) x
+ *            nrhs doubles (roughly 2 to 3 x n x nrhs); a call that needs more than 6 Mi
+ *            doubles, or more than 8 MiB of descriptors, returns EINVAL and does nothing.
+ *   The first call on a device looks up the arrays' device addresses (once per device, with
+ *   that device current); make that first call before any stream capture.
+ *   Every call shares the two arrays and leaves its data there; nothing needs to start at
+ *   zero.  Calls whose work overlaps on the GPU (different streams) race on the arrays:
+ *   serialize them, e.g. on one stream. */
+spdhss_status ulv_solve_noalloc(ulv_handle ulv, const double* B, double* X, int nrhs,
+                                int64_t ld, void* stream);
+
 /* ---- PCG (Sec. 6.2) ------------------------------------------------------------------
  * Solves A X = B with the H^2 matrix A and the ULV-factored SPD HSS preconditioner, from
  * X_0 = 0, every column independently, until the relative residual of every column is

@@ -168,6 +168,15 @@ class ULV:
                                   _stream(stream)))
         return Xc.t()
 
+    def solve_noalloc(self, B, stream=None) -> torch.Tensor:
+        """Same as solve(), through the entry point that allocates no device memory inside
+        the library (fixed device arrays; see ulv_solve_noalloc in include/spdhss.h)."""
+        Bc = _colmajor(B)
+        Xc = torch.empty_like(Bc)
+        N.check(N.lib().ulv_solve_noalloc(self._h, _ptr(Bc), _ptr(Xc), Bc.shape[0], self.hss.h2.n,
+                                          _stream(stream)))
+        return Xc.t()
+
     def close(self):
         if getattr(self, "_h", None):
             N.lib().ulv_destroy(self._h)

@@ -667,3 +667,59 @@ void copy_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 0, s
 void identity_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 1, s); }
 
 }  // namespace spd
+
+// ---------------------------------------------------------------------------------------
+// Launchers over descriptors that already sit in device memory (no allocation, no upload)
+// ---------------------------------------------------------------------------------------
+namespace spd {
+
+std::vector<int4> gemm_tiles(const std::vector<GemmProb>& probs, int* nb_out) {
+  int maxn = 0;
+  for (const auto& p : probs) maxn = std::max(maxn, p.N);
+  const int nb = maxn <= 8 ? 8 : (maxn <= 16 ? 16 : (maxn <= 32 ? 32 : 0));
+  const int tm = nb ? 64 : GM, tn = nb ? nb : GN;
+  std::vector<int4> tiles;
+  for (int p = 0; p < (int)probs.size(); ++p)
+    for (int m0 = 0; m0 < probs[p].M; m0 += tm)
+      for (int n0 = 0; n0 < probs[p].N; n0 += tn) tiles.push_back(make_int4(p, m0, n0, 0));
+  *nb_out = nb;
+  return tiles;
+}
+
+void gemm_launch_raw(const GemmProb* d_probs, const GemmSeg* d_segs, const int4* d_tiles,
+                     int64_t ntiles, int nb, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  const int g = (int)ntiles;
+  switch (nb) {
+    case 8: k_gemm_n<8><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
+    case 16: k_gemm_n<16><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
+    case 32: k_gemm_n<32><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
+    default: k_gemm<<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
+  }
+  SPD_LAUNCHED();
+}
+
+void trsm_launch_raw(const TrsmProb* d_probs, const int2* d_work, int64_t nwork, cudaStream_t s) {
+  if (nwork <= 0) return;
+  k_trsm<<<ceil_div(nwork, 8), 256, 0, s>>>(d_probs, d_work, nwork);
+  SPD_LAUNCHED();
+}
+
+void householder_launch_raw(const HhApplyProb* d_probs, const int2* d_work, int64_t nwork,
+                            int trans, cudaStream_t s) {
+  if (nwork <= 0) return;
+  k_hh_apply<<<ceil_div(nwork, 8), 256, 0, s>>>(d_probs, d_work, nwork, trans);
+  SPD_LAUNCHED();
+}
+
+void copy_launch_raw(const CopyProb* d_probs, int64_t nprob, int64_t max_elems, cudaStream_t s) {
+  if (nprob <= 0) return;
+  const int gx = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(max_elems, 1), 256), 64);
+  for (int64_t y0 = 0; y0 < nprob; y0 += 65535) {
+    const unsigned gy = (unsigned)std::min<int64_t>(65535, nprob - y0);
+    k_copy<<<dim3(gx, gy), 256, 0, s>>>(d_probs + y0, 0);
+    SPD_LAUNCHED();
+  }
+}
+
+}  // namespace spd

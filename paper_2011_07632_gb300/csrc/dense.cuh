@@ -171,3 +171,15 @@ void run_once(std::vector<P> h, cudaStream_t s, F launch) {
 }
 
 }  // namespace spd
+
+namespace spd {
+// Launchers over descriptor arrays that already sit in device memory: they neither
+// allocate nor upload anything.
+std::vector<int4> gemm_tiles(const std::vector<GemmProb>& probs, int* nb_out);
+void gemm_launch_raw(const GemmProb* d_probs, const GemmSeg* d_segs, const int4* d_tiles,
+                     int64_t ntiles, int nb, cudaStream_t s);
+void trsm_launch_raw(const TrsmProb* d_probs, const int2* d_work, int64_t nwork, cudaStream_t s);
+void householder_launch_raw(const HhApplyProb* d_probs, const int2* d_work, int64_t nwork,
+                            int trans, cudaStream_t s);
+void copy_launch_raw(const CopyProb* d_probs, int64_t nprob, int64_t max_elems, cudaStream_t s);
+}  // namespace spd

@@ -49,6 +49,7 @@ _SIGS = {
     "ulv_factor": [_P, _P, ctypes.POINTER(_P)],
     "ulv_solve": [_P, _P, _P, _I, _I64, _P],
     "ulv_destroy": [_P],
+    "ulv_solve_noalloc": [_P, _P, _P, _I, _I64, _P],
     "pcg_solve": [_P, _P, _P, _P, _I, _I64, _D, _I, ctypes.POINTER(_I),
                   ctypes.POINTER(_D), _P],
 }
