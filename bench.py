@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-at-scale", action="store_true")
+    ap.add_argument("--matvec-case", type=int, default=0,
+                    help="profiling case: H2 of the Gaussian workload at this n, then 5 products "
+                         "with 8 columns (prints timings, no benchmark line)")
     return ap.parse_args()
 
 
@@ -383,8 +386,31 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_matvec_case(n):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    c = AT_SCALE
+    pts = torch.from_numpy(inputs.uniform_cube(n, 3, 0)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, c["nrhs"], 1))).cuda()
+    h = api.H2(pts, c["kernel"], c["ell"], c["shift"], c["leaf_size"], c["h2_tol"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.matmul(B)
+    e0.record()
+    for _ in range(5):
+        h.matmul(B)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "h2_matmul_8rhs", "n": n, "ms": e0.elapsed_time(e1) / 5, "h2": h.info()}))
+
+
 def main():
     args = parse()
+    if args.matvec_case:
+        run_matvec_case(args.matvec_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
