@@ -5,8 +5,9 @@ preconditioner; it fixes only the stopping rule (relative residual).  Reading:
 textbook PCG from x_0 = 0, every right-hand side column independent; the recursive
 residual is tested after every iteration and, when it passes, the true residual
 b - A x is recomputed: the column stops if that passes too, otherwise the recursive
-residual is replaced by the true one and the iteration continues.  The iteration
-count is the number of products with A.
+residual is replaced by the true one and the search direction restarts from the
+preconditioned residual (beta = 0), so that conjugacy is not assumed across the
+replacement.  The iteration count is the number of products with A.
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ def pcg(apply_A, apply_M, b: np.ndarray, tol: float, maxit: int):
     rz = np.einsum("ij,ij->j", r, z)
     iters = np.zeros(nrhs, np.int64)
     done = np.linalg.norm(r, axis=0) / bnorm <= tol
+    restart = np.zeros(nrhs, bool)
     for it in range(1, maxit + 1):
         if done.all():
             break
@@ -48,12 +50,14 @@ def pcg(apply_A, apply_M, b: np.ndarray, tol: float, maxit: int):
                     done[c] = True
                 else:
                     r[:, c] = rt[:, c]
+                    restart[c] = True
         act = ~done
         if not act.any():
             break
         z = apply_M(r)
         rz_new = np.einsum("ij,ij->j", r, z)
-        beta = np.where(act, rz_new / np.where(rz == 0.0, 1.0, rz), 0.0)
+        beta = np.where(act & ~restart, rz_new / np.where(rz == 0.0, 1.0, rz), 0.0)
+        restart[:] = False
         p = np.where(act, z + beta * p, p)
         rz = np.where(act, rz_new, rz)
     rel = np.linalg.norm(b - apply_A(x), axis=0) / bnorm

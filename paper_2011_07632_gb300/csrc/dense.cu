@@ -154,13 +154,109 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
   }
 }
 
+// Very skinny variant for N <= 4 columns (matrix-vector like): 64-row tiles, 256 threads =
+// 64 rows x 4 groups that split every 32-wide K chunk; the four partial sums are added in
+// a fixed order through shared memory.
+template <int NB>
+__global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ probs,
+                                                const GemmSeg* __restrict__ segs,
+                                                const int4* __restrict__ tiles) {
+  constexpr int MB = 64, KB = 32;
+  const int4 t = tiles[blockIdx.x];
+  const GemmProb P = probs[t.x];
+  const int m0 = t.y, n0 = t.z;
+  __shared__ double As[KB][MB + 1];
+  __shared__ double Bs[KB][NB];
+  __shared__ double red[4][NB][MB];
+  const int tid = threadIdx.x;
+  const int row = tid & 63, kg = tid >> 6;
+  double acc[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) acc[c] = 0.0;
+  for (int sg = P.seg0; sg < P.seg1; ++sg) {
+    const GemmSeg S = segs[sg];
+    for (int k0 = 0; k0 < S.K; k0 += KB) {
+#pragma unroll
+      for (int r = 0; r < (MB * KB) / 256; ++r) {
+        const int e = tid + 256 * r;
+        int mm, kk;
+        if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < P.M && gk < S.K)
+          v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
+        As[kk][mm] = v;
+      }
+      if (tid < KB * NB) {
+        const int kk = tid % KB, nn = tid / KB;
+        const int gn = n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < P.N && gk < S.K)
+          v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < KB / 4; ++q) {
+        const int kk = kg * (KB / 4) + q;
+        const double a = As[kk][row];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) acc[c] = fma(a, Bs[kk][c], acc[c]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c) red[kg][c][row] = acc[c];
+  __syncthreads();
+  if (kg == 0) {
+    const int gm = m0 + row;
+    if (gm < P.M) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const int gn = n0 + c;
+        if (gn < P.N) {
+          const double v0 = (red[0][c][row] + red[1][c][row]) + (red[2][c][row] + red[3][c][row]);
+          double* cp = P.C + gm + (int64_t)gn * P.ldc;
+          double v = P.alpha * v0;
+          if (P.beta != 0.0) v += P.beta * (*cp);
+          *cp = v;
+        }
+      }
+    }
+  }
+}
+
+static int gemm_variant(int maxn) {
+  if (maxn <= 1) return 1;
+  if (maxn <= 2) return 2;
+  if (maxn <= 4) return 4;
+  if (maxn <= 8) return 8;
+  if (maxn <= 16) return 16;
+  if (maxn <= 32) return 32;
+  return 0;
+}
+
+static void gemm_dispatch(int nb, int g, const GemmProb* pr, const GemmSeg* sg, const int4* tl,
+                          cudaStream_t s) {
+  switch (nb) {
+    case 1: k_gemm_k<1><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 2: k_gemm_k<2><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 4: k_gemm_k<4><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 8: k_gemm_n<8><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 16: k_gemm_n<16><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 32: k_gemm_n<32><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    default: k_gemm<<<g, 256, 0, s>>>(pr, sg, tl); break;
+  }
+}
+
 void GemmBatch::upload(cudaStream_t s) {
   tiles.clear();
   flops = 0.0;
   bytes = 0.0;
   int maxn = 0;
   for (const auto& p : probs) maxn = std::max(maxn, p.N);
-  nb = maxn <= 8 ? 8 : (maxn <= 16 ? 16 : (maxn <= 32 ? 32 : 0));
+  nb = gemm_variant(maxn);
   const int tm = nb ? 64 : GM, tn = nb ? nb : GN;
   for (int p = 0; p < (int)probs.size(); ++p) {
     for (int m0 = 0; m0 < probs[p].M; m0 += tm)
@@ -184,12 +280,7 @@ void GemmBatch::launch(cudaStream_t s) const {
   ProfScope ps(tag, s, flops, bytes);
   for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
     const int g = (int)std::min<int64_t>(nt - b0, 2147483647LL);
-    switch (nb) {
-      case 8: k_gemm_n<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
-      case 16: k_gemm_n<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
-      case 32: k_gemm_n<32><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
-      default: k_gemm<<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_tiles.p + b0); break;
-    }
+    gemm_dispatch(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s);
     SPD_LAUNCHED();
   }
 }
@@ -233,12 +324,119 @@ __global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ pro
     for (int i = lane; i < c; i += 32) A[i + c * ld] = 0.0;
 }
 
+// Blocked right-looking Cholesky, one CTA per matrix, 32 x 32 tiles: one warp factors the
+// diagonal tile in shared memory, every thread solves panel rows against it, and the
+// trailing lower triangle is updated tile by tile from shared-memory copies of the panel.
+constexpr int PB = 32;
+
+__global__ void __launch_bounds__(256) k_potrf_blk(const PotrfProb* __restrict__ probs, int* info) {
+  const PotrfProb P = probs[blockIdx.x];
+  double* A = P.A;
+  const int64_t ld = P.lda;
+  const int n = P.n;
+  __shared__ double dk[PB][PB + 1];
+  __shared__ double li[PB][PB + 1];
+  __shared__ double lj[PB][PB + 1];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_fail = 0;
+  for (int k0 = 0; k0 < n; k0 += PB) {
+    const int kb = min(PB, n - k0);
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+      const int i = e % PB, j = e / PB;
+      dk[i][j] = (i < kb && j < kb && i >= j) ? A[(k0 + i) + (int64_t)(k0 + j) * ld] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < kb; ++j) {
+        if (lane == 0) {
+          const double d = dk[j][j];
+          if (!(d > 0.0) || !isfinite(d)) {
+            if (!s_fail && atomicCAS(info, 0, P.tag + 1) == 0) info[1] = k0 + j;
+            s_fail = 1;
+            dk[j][j] = 1.0;
+          } else {
+            dk[j][j] = sqrt(d);
+          }
+        }
+        __syncwarp();
+        const double dj = dk[j][j];
+        if (lane > j && lane < kb) dk[lane][j] /= dj;
+        __syncwarp();
+        if (lane > j && lane < kb) {
+          const double lij = dk[lane][j];
+          for (int jj = j + 1; jj <= lane; ++jj) dk[lane][jj] -= lij * dk[jj][j];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (s_fail) return;
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+      const int i = e % PB, j = e / PB;
+      if (i < kb && j < kb && i >= j) A[(k0 + i) + (int64_t)(k0 + j) * ld] = dk[i][j];
+    }
+    // panel rows below the diagonal tile: L_ik = A_ik L_kk^{-T}
+    for (int i = k0 + kb + tid; i < n; i += blockDim.x) {
+      double x[PB];
+#pragma unroll
+      for (int j = 0; j < PB; ++j) x[j] = (j < kb) ? A[i + (int64_t)(k0 + j) * ld] : 0.0;
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        if (j < kb) {
+          double v = x[j];
+#pragma unroll
+          for (int l = 0; l < j; ++l) v -= x[l] * dk[j][l];
+          x[j] = v / dk[j][j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PB; ++j)
+        if (j < kb) A[i + (int64_t)(k0 + j) * ld] = x[j];
+    }
+    __syncthreads();
+    // trailing update of the lower triangle, one 32 x 32 tile at a time
+    const int r0 = k0 + kb;
+    const int nt = (n - r0 + PB - 1) / PB;
+    for (int ti = 0; ti < nt; ++ti) {
+      const int i0 = r0 + ti * PB, ib = min(PB, n - i0);
+      for (int e = tid; e < PB * PB; e += blockDim.x) {
+        const int r = e % PB, l = e / PB;
+        li[r][l] = (r < ib && l < kb) ? A[(i0 + r) + (int64_t)(k0 + l) * ld] : 0.0;
+      }
+      for (int tj = 0; tj <= ti; ++tj) {
+        const int j0 = r0 + tj * PB, jb = min(PB, n - j0);
+        for (int e = tid; e < PB * PB; e += blockDim.x) {
+          const int r = e % PB, l = e / PB;
+          lj[r][l] = (r < jb && l < kb) ? A[(j0 + r) + (int64_t)(k0 + l) * ld] : 0.0;
+        }
+        __syncthreads();
+        const int r = tid & 31;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = (tid >> 5) + 8 * q;
+          const int gi = i0 + r, gj = j0 + c;
+          if (r < ib && c < jb && gi >= gj) {
+            double acc = 0.0;
+#pragma unroll 8
+            for (int l = 0; l < kb; ++l) acc = fma(li[r][l], lj[c][l], acc);
+            A[gi + (int64_t)gj * ld] -= acc;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int c = warp; c < n; c += (int)(blockDim.x >> 5))
+    for (int i = lane; i < c; i += 32) A[i + (int64_t)c * ld] = 0.0;
+}
+
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
   if (b.empty()) return;
   double f = 0.0;
   for (const auto& p : b.h) f += (double)p.n * p.n * p.n / 3.0;
-  ProfScope ps("potrf", s, f);
-  k_potrf<<<(unsigned)b.size(), 256, 0, s>>>(b.d.p, d_info);
+  ProfScope ps(b.tag ? b.tag : "potrf", s, f);
+  k_potrf_blk<<<(unsigned)b.size(), 256, 0, s>>>(b.d.p, d_info);
   SPD_LAUNCHED();
 }
 
@@ -284,16 +482,147 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmProb* __restrict__ probs
   }
 }
 
-static std::vector<int2> trsm_work(const Batch<TrsmProb>& b) {
+// Blocked variant: one CTA per (problem, 8 right-hand-side columns) keeps its columns in
+// shared memory; 32-row diagonal blocks are solved by one warp from a staged tile, the
+// remaining rows are updated by the whole CTA.  The dependent chain is n/32 block steps
+// of shared-memory latency instead of n steps of global-memory latency.
+constexpr int TRB = 32;
+
+template <int TRC>
+__global__ void __launch_bounds__(256) k_trsm_blk(const TrsmProb* __restrict__ probs,
+                                                  const int2* __restrict__ work) {
+  const int2 it = work[blockIdx.x];
+  const TrsmProb P = probs[it.x];
+  const int c0 = it.y;
+  const int nc = min(TRC, P.ncol - c0);
+  const int n = P.n;
+  extern __shared__ double sm[];
+  double* bs = sm;                        // column c at bs + c * n
+  double* td = sm + (size_t)n * TRC;      // 32 x 33 diagonal tile of op(T)
+  const double* T = P.T;
+  const int64_t lt = P.ldt;
+  const bool fwd = (P.lower && !P.trans) || (!P.lower && P.trans);
+  const bool direct = !P.trans;
+  for (int e = threadIdx.x; e < n * TRC; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    bs[e] = (c < nc) ? P.B[i + (int64_t)(c0 + c) * P.ldb] : 0.0;
+  }
+  __syncthreads();
+  const int nb = (n + TRB - 1) / TRB;
+  for (int bb = 0; bb < nb; ++bb) {
+    const int blk = fwd ? bb : nb - 1 - bb;
+    const int j0 = blk * TRB, jb = min(TRB, n - j0);
+    for (int e = threadIdx.x; e < TRB * TRB; e += blockDim.x) {
+      const int ii = e % TRB, jj = e / TRB;
+      double v = 0.0;
+      if (ii < jb && jj < jb)
+        v = direct ? T[(j0 + ii) + (int64_t)(j0 + jj) * lt] : T[(j0 + jj) + (int64_t)(j0 + ii) * lt];
+      td[ii * 33 + jj] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int ii = threadIdx.x;
+      // reciprocal diagonal once per block (off the dependent chain)
+      const double dinv = (ii < jb) ? 1.0 / td[ii * 33 + ii] : 0.0;
+      for (int c = 0; c < nc; ++c) {
+        double* b = bs + (size_t)c * n + j0;
+        double bi = (ii < jb) ? b[ii] : 0.0;
+        if (fwd) {
+          for (int jj = 0; jj < jb; ++jj) {
+            const double xj = __shfl_sync(0xffffffffu, bi * dinv, jj);
+            if (ii == jj) bi = xj;
+            if (ii > jj) bi -= td[ii * 33 + jj] * xj;
+          }
+        } else {
+          for (int jj = jb - 1; jj >= 0; --jj) {
+            const double xj = __shfl_sync(0xffffffffu, bi * dinv, jj);
+            if (ii == jj) bi = xj;
+            if (ii < jj) bi -= td[ii * 33 + jj] * xj;
+          }
+        }
+        if (ii < jb) b[ii] = bi;
+      }
+    }
+    __syncthreads();
+    const int r0 = fwd ? j0 + jb : 0, r1 = fwd ? n : j0;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double acc[TRC];
+#pragma unroll
+      for (int c = 0; c < TRC; ++c) acc[c] = 0.0;
+      if (jb == TRB) {
+        // full block: the 32 loads of this row are independent and issued together
+        double tv[TRB];
+#pragma unroll
+        for (int jj = 0; jj < TRB; ++jj)
+          tv[jj] = direct ? T[i + (int64_t)(j0 + jj) * lt] : T[(j0 + jj) + (int64_t)i * lt];
+#pragma unroll
+        for (int jj = 0; jj < TRB; ++jj)
+#pragma unroll
+          for (int c = 0; c < TRC; ++c) acc[c] = fma(tv[jj], bs[(size_t)c * n + j0 + jj], acc[c]);
+      } else {
+        for (int jj = 0; jj < jb; ++jj) {
+          const double tv = direct ? T[i + (int64_t)(j0 + jj) * lt] : T[(j0 + jj) + (int64_t)i * lt];
+#pragma unroll
+          for (int c = 0; c < TRC; ++c) acc[c] = fma(tv, bs[(size_t)c * n + j0 + jj], acc[c]);
+        }
+      }
+      for (int c = 0; c < nc; ++c) bs[(size_t)c * n + i] -= acc[c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * TRC; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    if (c < nc) P.B[i + (int64_t)(c0 + c) * P.ldb] = bs[e];
+  }
+}
+
+static constexpr size_t kTrsmMaxSmem = 200 * 1024;
+
+// work list and variant: blocked kernel (variant = columns per CTA: 1, 2, 4 or 8) when every
+// problem's columns fit shared memory; the column-per-warp kernel otherwise (variant 0)
+static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_t* smem) {
+  int maxn = 0, maxc = 0;
+  for (const auto& p : b.h) { maxn = std::max(maxn, p.n); maxc = std::max(maxc, p.ncol); }
+  const int cw = maxc <= 1 ? 1 : (maxc <= 2 ? 2 : (maxc <= 4 ? 4 : 8));
+  const size_t need = (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double);
+  *variant = (need <= kTrsmMaxSmem) ? cw : 0;
+  *smem = *variant ? need : 0;
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
     if (b.h[p].n > 0)
-      for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+      for (int c = 0; c < b.h[p].ncol; c += (*variant ? *variant : 1)) work.push_back(make_int2(p, c));
   return work;
 }
 
+template <int C>
+static void trsm_blk_go(const TrsmProb* probs, const int2* work, int64_t nwork, size_t smem,
+                        cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    SPD_CUDA(cudaFuncSetAttribute(k_trsm_blk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kTrsmMaxSmem));
+    configured = true;
+  }
+  k_trsm_blk<C><<<(unsigned)nwork, 256, smem, s>>>(probs, work);
+}
+
+static void trsm_go(const TrsmProb* probs, const int2* work, int64_t nwork, int variant,
+                    size_t smem, cudaStream_t s) {
+  if (variant) {
+    switch (variant) {
+      case 1: trsm_blk_go<1>(probs, work, nwork, smem, s); break;
+      case 2: trsm_blk_go<2>(probs, work, nwork, smem, s); break;
+      case 4: trsm_blk_go<4>(probs, work, nwork, smem, s); break;
+      default: trsm_blk_go<8>(probs, work, nwork, smem, s); break;
+    }
+  } else {
+    k_trsm<<<ceil_div(nwork, 8), 256, 0, s>>>(probs, work, nwork);
+  }
+  SPD_LAUNCHED();
+}
+
 void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
-  std::vector<int2> w = trsm_work(b);
+  std::vector<int2> w = trsm_work(b, &b.variant, &b.smem);
   b.work.upload(w, s);
   b.nwork = (int64_t)w.size();
 }
@@ -304,20 +633,19 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
   for (const auto& p : b.h) f += (double)p.n * p.n * p.ncol;
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
-    ProfScope ps("trsm", s, f);
-    k_trsm<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork);
-    SPD_LAUNCHED();
+    ProfScope ps(b.tag ? b.tag : "trsm", s, f);
+    trsm_go(b.d.p, b.work.p, b.nwork, b.variant, b.smem, s);
     return;
   }
-  std::vector<int2> work = trsm_work(b);
+  int variant;
+  size_t smem;
+  std::vector<int2> work = trsm_work(b, &variant, &smem);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);
-  const int64_t nw = (int64_t)work.size();
   {
-    ProfScope ps("trsm", s, f);
-    k_trsm<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
-    SPD_LAUNCHED();
+    ProfScope ps(b.tag ? b.tag : "trsm", s, f);
+    trsm_go(b.d.p, dw.p, (int64_t)work.size(), variant, smem, s);
   }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
@@ -522,7 +850,7 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
   cfg.numAttrs = 1;
   int slot;
   {
-    ProfScope ps(pivot ? "geqp3" : "geqrf", s);
+    ProfScope ps(b.tag ? b.tag : (pivot ? "geqp3" : "geqrf"), s);
     slot = ps.slot;
     SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, (const QrProb*)b.d.p, pivot));
     SPD_LAUNCHED();
@@ -573,7 +901,7 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   if (b.empty()) return;
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
-    ProfScope ps("householder", s);
+    ProfScope ps(b.tag ? b.tag : "householder", s);
     k_hh_apply<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork, trans);
     SPD_LAUNCHED();
     return;
@@ -584,7 +912,7 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
   {
-    ProfScope ps("householder", s);
+    ProfScope ps(b.tag ? b.tag : "householder", s);
     k_hh_apply<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw, trans);
     SPD_LAUNCHED();
   }
@@ -626,7 +954,7 @@ void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s) {
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
   {
-    ProfScope ps("form_q", s);
+    ProfScope ps(b.tag ? b.tag : "form_q", s);
     k_form_q<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
     SPD_LAUNCHED();
   }
@@ -652,7 +980,7 @@ __global__ void k_copy(const CopyProb* __restrict__ probs, int ident) {
 
 static void copy_common(const Batch<CopyProb>& b, int ident, cudaStream_t s) {
   if (b.empty()) return;
-  ProfScope ps("copy", s);
+  ProfScope ps(b.tag ? b.tag : "copy", s);
   int64_t mx = 1;
   for (const auto& p : b.h) mx = std::max<int64_t>(mx, (int64_t)p.m * p.n);
   const int gx = (int)std::min<int64_t>(ceil_div(mx, 256), 64);
@@ -676,7 +1004,7 @@ namespace spd {
 std::vector<int4> gemm_tiles(const std::vector<GemmProb>& probs, int* nb_out) {
   int maxn = 0;
   for (const auto& p : probs) maxn = std::max(maxn, p.N);
-  const int nb = maxn <= 8 ? 8 : (maxn <= 16 ? 16 : (maxn <= 32 ? 32 : 0));
+  const int nb = gemm_variant(maxn);
   const int tm = nb ? 64 : GM, tn = nb ? nb : GN;
   std::vector<int4> tiles;
   for (int p = 0; p < (int)probs.size(); ++p)
@@ -689,13 +1017,7 @@ std::vector<int4> gemm_tiles(const std::vector<GemmProb>& probs, int* nb_out) {
 void gemm_launch_raw(const GemmProb* d_probs, const GemmSeg* d_segs, const int4* d_tiles,
                      int64_t ntiles, int nb, cudaStream_t s) {
   if (ntiles <= 0) return;
-  const int g = (int)ntiles;
-  switch (nb) {
-    case 8: k_gemm_n<8><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
-    case 16: k_gemm_n<16><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
-    case 32: k_gemm_n<32><<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
-    default: k_gemm<<<g, 256, 0, s>>>(d_probs, d_segs, d_tiles); break;
-  }
+  gemm_dispatch(nb, (int)ntiles, d_probs, d_segs, d_tiles, s);
   SPD_LAUNCHED();
 }
 

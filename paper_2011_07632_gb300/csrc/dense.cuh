@@ -54,7 +54,7 @@ struct GemmBatch {
   void clear() { segs.clear(); probs.clear(); tiles.clear(); }
   std::vector<int4> tiles;   // (prob, m0, n0, 0)
   const char* tag = "gemm";
-  int nb = 0;                        // 8/16/32: skinny kernel column block; 0: 64x64 tiles
+  int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
   double flops = 0.0, bytes = 0.0;   // algorithmic work of one launch
   DevBuf<GemmSeg> d_segs;
   DevBuf<GemmProb> d_probs;
@@ -69,6 +69,9 @@ struct Batch {
   // optional prepared (problem, column) work list of the column-parallel kernels
   DevBuf<int2> work;
   int64_t nwork = -1;
+  const char* tag = nullptr;   // profiler label of the call site
+  int variant = 0;        // kernel variant chosen when the work list was prepared
+  size_t smem = 0;        // dynamic shared memory of that variant
   void upload(cudaStream_t s) { d.upload(h, s); }
   size_t size() const { return h.size(); }
   bool empty() const { return h.empty(); }

@@ -167,6 +167,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
       }
       pb.upload(s);
       proxy_launch(pb, h->kfn, dim, s);
+      qb.tag = "geqp3_h2_id";
       qb.upload(s);
       const int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
       const int pslot = geqp3_launch(qb, 1, cl, np, s);
@@ -218,6 +219,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
           }
         }
       }
+      tb.tag = "trsm_h2_id";
       tb.upload(s);
       trsm_launch(tb, s);
       ib.upload(s);
@@ -425,7 +427,8 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
       }
     }
   }
-  p.coupling.tag = "h2_coupling";
+  p.coupling.tag = nslot > 1 ? "h2_coupling_sample" : "h2_coupling";
+  p.near.tag = nslot > 1 ? "near_sample" : "near_h2";
   p.up_leaf.tag = p.leaf_out.tag = "h2_basis";
   for (auto& g : p.up) g.tag = "h2_basis";
   for (auto& g : p.down) g.tag = "h2_basis";

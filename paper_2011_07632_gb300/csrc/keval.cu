@@ -204,15 +204,120 @@ __global__ void __launch_bounds__(256) k_near(const NearProb* __restrict__ probs
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// near field with few columns (NC <= 16): one thread per target row; when a leaf has fewer
+// than 256 points, G = 256 / rows groups of threads split the source points between them
+// and a fixed-order sum in shared memory combines the groups.  Every kernel entry is
+// evaluated exactly once per column block, and no FMA is spent on padding.
+// ---------------------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__ probs,
+                                                    const NearSeg* __restrict__ segs,
+                                                    const int2* __restrict__ work, KernelFn kf,
+                                                    const double* __restrict__ xs, int64_t ldx,
+                                                    int dim) {
+  // source points staged per chunk; the staging area is reused for the final reduction
+  constexpr int CH = NC >= 16 ? 192 : (NC >= 8 ? 256 : 512);
+  constexpr int STAGE = CH * (4 + NC);
+  constexpr int RED = NC * 256;
+  __shared__ double smem[STAGE > RED ? STAGE : RED];
+  double (*red)[256] = reinterpret_cast<double (*)[256]>(smem);
+  double (*sx)[CH] = reinterpret_cast<double (*)[CH]>(smem);
+  double (*sv)[CH] = reinterpret_cast<double (*)[CH]>(smem + 3 * CH);
+  int64_t* sg_idx = reinterpret_cast<int64_t*>(smem + (3 + NC) * CH);
+  const int2 w = work[blockIdx.x];
+  const NearProb P = probs[w.x];
+  const int col0 = w.y;
+  const int ncb = min(NC, P.ncol - col0);
+  __shared__ int s_seg, s_q;   // chunk start: segment and offset inside it
+  const int t = threadIdx.x;
+  for (int rb = 0; rb < P.rows; rb += 256) {
+    const int m = min(256, P.rows - rb);
+    const int G = max(1, 256 / m);
+    const int p = t % m, g = t / m;
+    const int64_t gp = P.row0 + rb + p;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    if (g < G) {
+      y0 = xs[gp];
+      y1 = xs[ldx + gp];
+      if (dim == 3) y2 = xs[2 * ldx + gp];
+    }
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    if (t == 0) { s_seg = P.seg0; s_q = 0; }
+    __syncthreads();
+    while (s_seg < P.seg1) {
+      // flatten the next CH source points of the concatenated segments into shared memory
+      int cnt = 0;
+      {
+        int sg = s_seg, q = s_q;
+        while (sg < P.seg1 && cnt < CH) {
+          const NearSeg S = segs[sg];
+          const int take = min(S.cols - q, CH - cnt);
+          const double* xin = S.x + (int64_t)col0 * S.ldx;
+          for (int e = t; e < take; e += 256) {
+            const int64_t gq = S.col0 + q + e;
+            sx[0][cnt + e] = xs[gq];
+            sx[1][cnt + e] = xs[ldx + gq];
+            sx[2][cnt + e] = (dim == 3) ? xs[2 * ldx + gq] : 0.0;
+            sg_idx[cnt + e] = S.self ? gq : -1;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              sv[c][cnt + e] = (c < ncb) ? xin[q + e + (int64_t)c * S.ldx] : 0.0;
+          }
+          cnt += take;
+          q += take;
+          if (q >= S.cols) { ++sg; q = 0; }
+        }
+        __syncthreads();
+        if (t == 0) { s_seg = sg; s_q = q; }
+      }
+      if (g < G) {
+#pragma unroll 4
+        for (int q = g; q < cnt; q += G) {
+          const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q];
+          double r2 = d0 * d0 + d1 * d1;
+          if (dim == 3) {
+            const double d2 = y2 - sx[2][q];
+            r2 += d2 * d2;
+          }
+          double kv = kernel_r2(kf, r2);
+          if (sg_idx[q] == gp) kv += kf.shift;
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            if (c < ncb) acc[c] = fma(kv, sv[c][q], acc[c]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) red[c][t] = acc[c];
+    __syncthreads();
+    if (t < m) {
+      for (int c = 0; c < ncb; ++c) {
+        double sum = 0.0;
+        for (int gg = 0; gg < G; ++gg) sum += red[c][t + gg * m];
+        double* o = P.out + (rb + t) + (int64_t)(col0 + c) * P.ldo;
+        *o = P.beta ? (*o + sum) : sum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 void NearBatch::upload(cudaStream_t s) {
   work.clear();
   int mx = 1;
   for (const auto& p : probs) mx = std::max(mx, p.ncol);
-  cb = mx <= 8 ? 8 : (mx <= 16 ? 16 : (mx <= 32 ? 32 : 64));
+  // few columns: thread-per-row kernel (cb = -NC); otherwise shared-memory kernel tiles
+  if (mx <= 16) cb = -(mx <= 1 ? 1 : (mx <= 2 ? 2 : (mx <= 4 ? 4 : (mx <= 8 ? 8 : 16))));
+  else cb = mx <= 32 ? 32 : 64;
+  const int step = cb < 0 ? -cb : cb;
   flops = 0.0;
   evals = 0.0;
   for (int p = 0; p < (int)probs.size(); ++p) {
-    for (int c0 = 0; c0 < probs[p].ncol; c0 += cb) work.push_back(make_int2(p, c0));
+    for (int c0 = 0; c0 < probs[p].ncol; c0 += step) work.push_back(make_int2(p, c0));
     for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
       const double e = (double)probs[p].rows * segs[g].cols;
       evals += e;
@@ -227,9 +332,14 @@ void NearBatch::upload(cudaStream_t s) {
 void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
                        cudaStream_t s) const {
   if (work.empty()) return;
-  ProfScope ps("near", s, flops, 8.0 * evals);
+  ProfScope ps(tag, s, flops, 8.0 * evals);
   const unsigned g = (unsigned)work.size();
   switch (cb) {
+    case -1: k_near_small<1><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
+    case -2: k_near_small<2><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
+    case -4: k_near_small<4><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
+    case -8: k_near_small<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
+    case -16: k_near_small<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
     case 8: k_near<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
     case 16: k_near<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
     case 32: k_near<32><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;

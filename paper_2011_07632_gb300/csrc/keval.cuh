@@ -68,9 +68,10 @@ struct NearBatch {
   DevBuf<NearProb> d_probs;
   DevBuf<NearSeg> d_segs;
   DevBuf<int2> d_work;
-  int cb = 8;               // column block per CTA (8, 16, 32 or 64)
+  int cb = 8;               // column block per CTA: 32/64 tile kernel, -NC few-column kernel
   double flops = 0.0;       // 2 * (kernel entries) * columns: the block product
   double evals = 0.0;       // kernel entries of one launch
+  const char* tag = "near";
   void prob(int64_t row0, int rows, double* out, int64_t ldo, int ncol, int beta) {
     NearProb p;
     p.row0 = row0; p.rows = rows; p.out = out; p.ldo = ldo; p.ncol = ncol; p.beta = beta;

@@ -61,21 +61,22 @@ __global__ void k_axpy_xr(double* __restrict__ x, double* __restrict__ r,
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * ncol) return;
   const int c = (int)(e / n);
-  if (done[c]) return;
+  if (done[c] == 1) return;
   const double alpha = pq[c] != 0.0 ? rz[c] / pq[c] : 0.0;
   x[e] += alpha * p[e];
   r[e] -= alpha * q[e];
 }
 
-// p = z + beta p with beta = rz_new / rz (active columns); then rz = rz_new
+// p = z + beta p with beta = rz_new / rz (active columns; beta = 0 right after a residual
+// replacement, done[c] == 2); then rz = rz_new
 __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                            int ncol, const double* __restrict__ rzn, const double* __restrict__ rz,
                            const int* __restrict__ done) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * ncol) return;
   const int c = (int)(e / n);
-  if (done[c]) return;
-  const double beta = rz[c] != 0.0 ? rzn[c] / rz[c] : 0.0;
+  if (done[c] == 1) return;
+  const double beta = (done[c] == 0 && rz[c] != 0.0) ? rzn[c] / rz[c] : 0.0;
   p[e] = z[e] + beta * p[e];
 }
 
@@ -169,7 +170,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     SPD_CUDA(cudaStreamSynchronize(s));
     bool any_pass = false;
     for (int c = 0; c < nrhs; ++c) {
-      if (hdone[c]) continue;
+      if (hdone[c] == 1) continue;
       hit[c] = it;
       if (!std::isfinite(hrr[c])) throw Error(SPDHSS_NUMERIC, "pcg_solve: residual is not finite");
       if (std::sqrt(std::max(hrr[c], 0.0)) / bn[c] <= tol) any_pass = true;
@@ -179,18 +180,22 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       true_residual(trel, true);
       bool changed = false;
       for (int c = 0; c < nrhs; ++c) {
-        if (hdone[c]) continue;
+        if (hdone[c] == 1) continue;
         if (std::sqrt(std::max(hrr[c], 0.0)) / bn[c] > tol) continue;
         if (trel[c] <= tol) { hdone[c] = 1; changed = true; }
-        else
+        else {
+          // residual replacement: r = b - A x, and the next direction restarts (beta = 0)
           SPD_CUDA(cudaMemcpyAsync(r.p + (int64_t)c * n, PR.ys.p + (int64_t)c * n, n * sizeof(double),
                                    cudaMemcpyDeviceToDevice, s));
+          hdone[c] = 2;
+          changed = true;
+        }
       }
       if (changed)
         SPD_CUDA(cudaMemcpyAsync(done.p, hdone.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     }
     bool all = true;
-    for (int c = 0; c < nrhs; ++c) all = all && hdone[c];
+    for (int c = 0; c < nrhs; ++c) all = all && hdone[c] == 1;
     if (all) break;
     SPD_CUDA(cudaMemcpyAsync(z, r.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ulv_solve_sorted(u, PU, s);                   // z = M^{-1} r
@@ -198,6 +203,11 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     k_update_p<<<gb, 256, 0, s>>>(p, z, n, nrhs, rzn, rz, done.p);
     SPD_LAUNCHED();
     SPD_CUDA(cudaMemcpyAsync(rz, rzn, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    bool restarted = false;
+    for (int c = 0; c < nrhs; ++c)
+      if (hdone[c] == 2) { hdone[c] = 0; restarted = true; }
+    if (restarted)
+      SPD_CUDA(cudaMemcpyAsync(done.p, hdone.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
   }
   std::vector<double> trel;
   true_residual(trel, false);

@@ -241,6 +241,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
       for (int64_t a = 0; a < nn; ++a)
         if (mrow[o + a] > 0) pb.push(PotrfProb{F.p + mmo[a], mrow[o + a], mrow[o + a], (int)a});
       info.zero(s);
+      pb.tag = "potrf_hss";
       pb.upload(s);
       potrf_launch(pb, info.p, s);
       check_info(info, "spdhss_build", o, s);
@@ -270,6 +271,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         tb.push(tp);
       }
       cb.upload(s); copy_launch(cb, s);
+      tb.tag = "trsm_hss_lambda";
       tb.upload(s); trsm_launch(tb, s);
     }
     // Lambda of slot k (the current level) for node a: pointer and ld
@@ -304,6 +306,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         qb.push(q);
       }
       cb.upload(s); copy_launch(cb, s);
+      qb.tag = "geqp3_hss";
       qb.upload(s);
       const int pslot = geqp3_launch(qb, 1, 1, maxm, s);
       std::vector<int> hr = rkd.download(s);
@@ -374,6 +377,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         tp.lower = 1; tp.trans = 1;
         tb.push(tp);
       }
+      tb.tag = "trsm_hss_G";
       tb.upload(s);
       trsm_launch(tb, s);
       // Phi U^H2: leaf G^T U^H2; nonleaf Gbar^T (diag(PhiU_c) R^H2_i)
@@ -527,6 +531,8 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
           }
           to += tmp_rows(jb) * rj;
         }
+        nb.tag = "near_hss_type1";
+        g1.tag = g2.tag = "gemm_hss_pairs";
         nb.upload(s);
         nb.launch(h2->kfn, xs, n, dim, s);
         g1.run(s);

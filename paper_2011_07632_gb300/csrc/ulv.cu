@@ -217,6 +217,7 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
         cp.src = Dt.p + sz[i - o]; cp.dst = Dp(i); cp.trans = 0;
         back.push(cp);
       }
+      h1.tag = h2b.tag = "hh_ulv_factor";
       h1.upload(s); householder_launch(h1, 1, s);
       tr.upload(s); copy_launch(tr, s);
       h2b.upload(s); householder_launch(h2b, 1, s);
@@ -242,6 +243,9 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
         }
       }
       info.zero(s);
+      pb.tag = "potrf_ulv";
+      tb.tag = "trsm_ulv_factor";
+      gb.tag = "gemm_ulv_factor";
       pb.upload(s);
       potrf_launch(pb, info.p, s);
       std::vector<int> hi = info.download(s);
@@ -405,6 +409,9 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
     P.root_b.push(TrsmProb{u->root.p, mr, P.bw[nlev].p, P.ldk[nlev], mr, ncol, 1, 1});
   }
   for (int k = 0; k < nlev; ++k) {
+    P.qt[k].tag = P.q[k].tag = "hh_ulv_solve";
+    P.fw[k].tag = P.bk[k].tag = "trsm_ulv_solve";
+    P.up[k].tag = P.down[k].tag = "copy_ulv_solve";
     P.qt[k].upload(s); householder_prepare(P.qt[k], s);
     P.q[k].upload(s); householder_prepare(P.q[k], s);
     P.fw[k].upload(s); trsm_prepare(P.fw[k], s);
@@ -415,6 +422,7 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
     P.up[k].upload(s);
     P.down[k].upload(s);
   }
+  P.root_f.tag = P.root_b.tag = "trsm_ulv_root";
   P.root_f.upload(s); trsm_prepare(P.root_f, s);
   P.root_b.upload(s); trsm_prepare(P.root_b, s);
   SPD_CUDA(cudaStreamSynchronize(s));

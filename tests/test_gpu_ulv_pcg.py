@@ -70,12 +70,18 @@ def test_pcg_matches_oracle_iterations():
 
 
 def test_pcg_tight_tolerance_vs_dense_solve():
+    """PCG to relres 1e-10 (above kappa * eps for this system) against a dense solve of the
+    same H^2 matrix: the error is bounded by kappa * relres."""
     n, r = 4096, 50
     api, X, h, hs, u, tr, Mh, ohss = setup(n, 3, 64, "exp", 1.0, 1e-2, 1e-8, r)
     b = inputs.rhs(n, 1, 1)
-    x, it, rr = api.pcg_solve(h, u, b, tol=1e-12, maxit=3000)
+    x, it, rr = api.pcg_solve(h, u, b, tol=1e-10, maxit=3000, raise_on_no_convergence=True)
+    assert rr[0] <= 1e-10
     xs = x.cpu().numpy()[tr.perm]
     xd = np.linalg.solve(Mh, b[tr.perm])
+    lam = np.linalg.eigvalsh(Mh)
+    kappa = lam.max() / lam.min()
+    assert rel(xs, xd) <= 2.0 * kappa * 1e-10
     assert rel(xs, xd) < 1e-8
     A = OK.dense_matrix(OK.EXP, 1.0, 1e-2, X)
     xa = np.linalg.solve(A, b)
