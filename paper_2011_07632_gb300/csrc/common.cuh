@@ -144,6 +144,18 @@ __device__ __forceinline__ double kernel_r2(const KernelFn& k, double r2) {
   }
 }
 
+// The same kernel with its kind fixed at compile time (no per-entry branch).
+template <int KIND>
+__device__ __forceinline__ double kernel_r2_k(double r2, double inv_ell) {
+  if (KIND == SPDHSS_K_EXP) return exp(-sqrt(r2) * inv_ell);
+  if (KIND == SPDHSS_K_GAUSS) return exp(-r2 * (inv_ell * inv_ell));
+  if (KIND == SPDHSS_K_MATERN32) {
+    const double t = 1.7320508075688772 * sqrt(r2) * inv_ell;
+    return (1.0 + t) * exp(-t);
+  }
+  return 1.0 / sqrt(1.0 + r2 * (inv_ell * inv_ell));
+}
+
 // Points are stored structure-of-arrays: coordinate a of point p at x[a * ldx + p].
 __device__ __forceinline__ double sqdist3(const double* __restrict__ x, int64_t ldx, int dim,
                                           int64_t p, double y0, double y1, double y2) {

@@ -124,93 +124,12 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 }
 
 // ---------------------------------------------------------------------------------------
-// near field: CTA = (problem, column block of CB); 256 threads = 128 rows x 2 column halves.
-// For every segment, 32-point chunks: evaluate the 128 x 32 kernel tile into shared
-// memory, stage the 32 x CB input rows, accumulate in registers.
-// ---------------------------------------------------------------------------------------
-template <int CB>
-__global__ void __launch_bounds__(256) k_near(const NearProb* __restrict__ probs,
-                                              const NearSeg* __restrict__ segs,
-                                              const int2* __restrict__ work, KernelFn kf,
-                                              const double* __restrict__ xs, int64_t ldx,
-                                              int dim) {
-  constexpr int HC = CB / 2;
-  const int2 w = work[blockIdx.x];
-  const NearProb P = probs[w.x];
-  const int col0 = w.y;
-  const int ncb = min(CB, P.ncol - col0);
-  __shared__ double Kt[32][129];
-  __shared__ double Xt[32][CB + 1];
-  __shared__ double rx[3][128];
-  __shared__ double cx[3][32];
-  const int t = threadIdx.x;
-  const int row = t & 127, half = t >> 7;
-  for (int rb = 0; rb < P.rows; rb += 128) {
-    const int nr = min(128, P.rows - rb);
-    if (t < 128 && t < nr)
-      for (int a = 0; a < dim; ++a) rx[a][t] = xs[a * ldx + P.row0 + rb + t];
-    double acc[HC];
-#pragma unroll
-    for (int c = 0; c < HC; ++c) acc[c] = 0.0;
-    __syncthreads();
-    for (int sg = P.seg0; sg < P.seg1; ++sg) {
-      const NearSeg S = segs[sg];
-      for (int q0 = 0; q0 < S.cols; q0 += 32) {
-        const int nq = min(32, S.cols - q0);
-        if (t < 32 && t < nq)
-          for (int a = 0; a < dim; ++a) cx[a][t] = xs[a * ldx + S.col0 + q0 + t];
-        for (int e = t; e < 32 * CB; e += 256) {
-          const int qq = e % 32, cc = e / 32;
-          double v = 0.0;
-          if (qq < nq && cc < ncb) v = S.x[(q0 + qq) + (int64_t)(col0 + cc) * S.ldx];
-          Xt[qq][cc] = v;
-        }
-        __syncthreads();
-        for (int e = t; e < 32 * 128; e += 256) {
-          const int rr = e & 127, qq = e >> 7;
-          double v = 0.0;
-          if (rr < nr && qq < nq) {
-            double r2 = 0.0;
-            for (int a = 0; a < dim; ++a) {
-              const double d = rx[a][rr] - cx[a][qq];
-              r2 += d * d;
-            }
-            v = kernel_r2(kf, r2);
-            if (S.self && (P.row0 + rb + rr) == (S.col0 + q0 + qq)) v += kf.shift;
-          }
-          Kt[qq][rr] = v;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int qq = 0; qq < 32; ++qq) {
-          const double kv = Kt[qq][row];
-#pragma unroll
-          for (int c = 0; c < HC; ++c) acc[c] = fma(kv, Xt[qq][half * HC + c], acc[c]);
-        }
-        __syncthreads();
-      }
-    }
-    if (row < nr) {
-#pragma unroll
-      for (int c = 0; c < HC; ++c) {
-        const int cc = half * HC + c;
-        if (cc < ncb) {
-          double* o = P.out + (rb + row) + (int64_t)(col0 + cc) * P.ldo;
-          *o = P.beta ? (*o + acc[c]) : acc[c];
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // near field with few columns (NC <= 16): one thread per target row; when a leaf has fewer
 // than 256 points, G = 256 / rows groups of threads split the source points between them
 // and a fixed-order sum in shared memory combines the groups.  Every kernel entry is
 // evaluated exactly once per column block, and no FMA is spent on padding.
 // ---------------------------------------------------------------------------------------
-template <int NC>
+template <int NC, int KIND>
 __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__ probs,
                                                     const NearSeg* __restrict__ segs,
                                                     const int2* __restrict__ work, KernelFn kf,
@@ -218,17 +137,17 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
                                                     int dim) {
   // source points staged per chunk; the staging area is reused for the final reduction
   constexpr int CH = NC >= 16 ? 192 : (NC >= 8 ? 256 : 512);
-  constexpr int STAGE = CH * (4 + NC);
+  constexpr int STAGE = CH * (3 + NC);
   constexpr int RED = NC * 256;
   __shared__ double smem[STAGE > RED ? STAGE : RED];
   double (*red)[256] = reinterpret_cast<double (*)[256]>(smem);
   double (*sx)[CH] = reinterpret_cast<double (*)[CH]>(smem);
   double (*sv)[CH] = reinterpret_cast<double (*)[CH]>(smem + 3 * CH);
-  int64_t* sg_idx = reinterpret_cast<int64_t*>(smem + (3 + NC) * CH);
   const int2 w = work[blockIdx.x];
   const NearProb P = probs[w.x];
   const int col0 = w.y;
   const int ncb = min(NC, P.ncol - col0);
+  const double inv_ell = kf.inv_ell;
   __shared__ int s_seg, s_q;   // chunk start: segment and offset inside it
   const int t = threadIdx.x;
   for (int rb = 0; rb < P.rows; rb += 256) {
@@ -248,7 +167,6 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
     if (t == 0) { s_seg = P.seg0; s_q = 0; }
     __syncthreads();
     while (s_seg < P.seg1) {
-      // flatten the next CH source points of the concatenated segments into shared memory
       int cnt = 0;
       {
         int sg = s_seg, q = s_q;
@@ -261,7 +179,6 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
             sx[0][cnt + e] = xs[gq];
             sx[1][cnt + e] = xs[ldx + gq];
             sx[2][cnt + e] = (dim == 3) ? xs[2 * ldx + gq] : 0.0;
-            sg_idx[cnt + e] = S.self ? gq : -1;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
               sv[c][cnt + e] = (c < ncb) ? xin[q + e + (int64_t)c * S.ldx] : 0.0;
@@ -274,19 +191,22 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
         if (t == 0) { s_seg = sg; s_q = q; }
       }
       if (g < G) {
+        if (dim == 3) {
 #pragma unroll 4
-        for (int q = g; q < cnt; q += G) {
-          const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q];
-          double r2 = d0 * d0 + d1 * d1;
-          if (dim == 3) {
-            const double d2 = y2 - sx[2][q];
-            r2 += d2 * d2;
-          }
-          double kv = kernel_r2(kf, r2);
-          if (sg_idx[q] == gp) kv += kf.shift;
+          for (int q = g; q < cnt; q += G) {
+            const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q], d2 = y2 - sx[2][q];
+            const double kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1 + d2 * d2, inv_ell);
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
-            if (c < ncb) acc[c] = fma(kv, sv[c][q], acc[c]);
+            for (int c = 0; c < NC; ++c) acc[c] = fma(kv, sv[c][q], acc[c]);
+          }
+        } else {
+#pragma unroll 4
+          for (int q = g; q < cnt; q += G) {
+            const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q];
+            const double kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1, inv_ell);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = fma(kv, sv[c][q], acc[c]);
+          }
         }
       }
       __syncthreads();
@@ -295,14 +215,142 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
     for (int c = 0; c < NC; ++c) red[c][t] = acc[c];
     __syncthreads();
     if (t < m) {
-      for (int c = 0; c < ncb; ++c) {
-        double sum = 0.0;
-        for (int gg = 0; gg < G; ++gg) sum += red[c][t + gg * m];
-        double* o = P.out + (rb + t) + (int64_t)(col0 + c) * P.ldo;
-        *o = P.beta ? (*o + sum) : sum;
+      // the diagonal shift of a self segment: sigma * x_p
+      double shift_x[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) shift_x[c] = 0.0;
+      for (int sg = P.seg0; sg < P.seg1; ++sg) {
+        const NearSeg S = segs[sg];
+        if (S.self) {
+          const int64_t off = P.row0 + rb + t - S.col0;
+          if (off >= 0 && off < S.cols) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              if (c < ncb) shift_x[c] += kf.shift * S.x[off + (int64_t)(col0 + c) * S.ldx];
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (c < ncb) {
+          double sum = 0.0;
+          for (int gg = 0; gg < G; ++gg) sum += red[c][t + gg * m];
+          sum += shift_x[c];
+          double* o = P.out + (rb + t) + (int64_t)(col0 + c) * P.ldo;
+          *o = P.beta ? (*o + sum) : sum;
+        }
       }
     }
     __syncthreads();
+  }
+}
+
+// Many columns (17..64): the (row, column) output pairs of 32 rows are spread over the 256
+// threads (at most 8 each, a compile-time count), the kernel tile of every 32-point source
+// chunk is evaluated once into shared memory, and the source rows of the chunk are staged.
+template <int PPT, int KIND>
+__device__ __forceinline__ void near_pairs(const NearProb& P, const NearSeg* __restrict__ segs,
+                                           int col0, int ncb, int rb, int nr, KernelFn kf,
+                                           const double* __restrict__ xs, int64_t ldx, int dim,
+                                           double (*Kt)[33], double (*Xt)[65], double (*rx)[32],
+                                           double (*cx)[32]) {
+  const int t = threadIdx.x;
+  const int npair = nr * ncb;
+  double acc[PPT];
+  int pr[PPT], pc[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int e = t + 256 * k;
+    acc[k] = 0.0;
+    pr[k] = (e < npair) ? e % nr : 0;
+    pc[k] = (e < npair) ? e / nr : 0;
+  }
+  for (int sg = P.seg0; sg < P.seg1; ++sg) {
+    const NearSeg S = segs[sg];
+    for (int q0 = 0; q0 < S.cols; q0 += 32) {
+      const int nq = min(32, S.cols - q0);
+      if (t < 32 && t < nq)
+        for (int a = 0; a < dim; ++a) cx[a][t] = xs[a * ldx + S.col0 + q0 + t];
+      for (int e = t; e < 32 * 64; e += 256) {
+        const int qq = e % 32, cc = e / 32;
+        double v = 0.0;
+        if (qq < nq && cc < ncb) v = S.x[(q0 + qq) + (int64_t)(col0 + cc) * S.ldx];
+        Xt[qq][cc] = v;
+      }
+      __syncthreads();
+      for (int e = t; e < 32 * 32; e += 256) {
+        const int rr = e & 31, qq = e >> 5;
+        double v = 0.0;
+        if (rr < nr && qq < nq) {
+          double r2 = 0.0;
+          for (int a = 0; a < dim; ++a) {
+            const double d = rx[a][rr] - cx[a][qq];
+            r2 += d * d;
+          }
+          v = kernel_r2_k<KIND>(r2, kf.inv_ell);
+          if (S.self && (P.row0 + rb + rr) == (S.col0 + q0 + qq)) v += kf.shift;
+        }
+        Kt[qq][rr] = v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int qq = 0; qq < 32; ++qq) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) acc[k] = fma(Kt[qq][pr[k]], Xt[qq][pc[k]], acc[k]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int e = t + 256 * k;
+    if (e < npair) {
+      double* o = P.out + (rb + pr[k]) + (int64_t)(col0 + pc[k]) * P.ldo;
+      *o = P.beta ? (*o + acc[k]) : acc[k];
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_near_pairs(const NearProb* __restrict__ probs,
+                                                    const NearSeg* __restrict__ segs,
+                                                    const int2* __restrict__ work, KernelFn kf,
+                                                    const double* __restrict__ xs, int64_t ldx,
+                                                    int dim) {
+  __shared__ double Kt[32][33];
+  __shared__ double Xt[32][65];
+  __shared__ double rx[3][32];
+  __shared__ double cx[3][32];
+  const int2 w = work[blockIdx.x];
+  const NearProb P = probs[w.x];
+  const int col0 = w.y;
+  const int ncb = min(64, P.ncol - col0);
+  for (int rb = 0; rb < P.rows; rb += 32) {
+    const int nr = min(32, P.rows - rb);
+    if (threadIdx.x < nr)
+      for (int a = 0; a < dim; ++a) rx[a][threadIdx.x] = xs[a * ldx + P.row0 + rb + threadIdx.x];
+    __syncthreads();
+    const int ppt = (nr * ncb + 255) / 256;
+    if (ppt <= 1) near_pairs<1, KIND>(P, segs, col0, ncb, rb, nr, kf, xs, ldx, dim, Kt, Xt, rx, cx);
+    else if (ppt <= 2) near_pairs<2, KIND>(P, segs, col0, ncb, rb, nr, kf, xs, ldx, dim, Kt, Xt, rx, cx);
+    else if (ppt <= 4) near_pairs<4, KIND>(P, segs, col0, ncb, rb, nr, kf, xs, ldx, dim, Kt, Xt, rx, cx);
+    else near_pairs<8, KIND>(P, segs, col0, ncb, rb, nr, kf, xs, ldx, dim, Kt, Xt, rx, cx);
+    __syncthreads();
+  }
+}
+
+// out = beta * out + sum of the parts (fixed order), one thread per output entry
+__global__ void k_near_reduce(const NearProb* __restrict__ probs, const int4* __restrict__ red,
+                              const double* __restrict__ scratch) {
+  const int4 r = red[blockIdx.x];
+  const NearProb P = probs[r.x];
+  const int64_t tot = (int64_t)P.rows * P.ncol;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int i = (int)(e % P.rows), c = (int)(e / P.rows);
+    double sum = 0.0;
+    for (int q = 0; q < r.z; ++q) sum += scratch[(int64_t)r.y + (int64_t)q * tot + e];
+    double* o = P.out + i + (int64_t)c * P.ldo;
+    *o = P.beta ? (*o + sum) : sum;
   }
 }
 
@@ -312,12 +360,58 @@ void NearBatch::upload(cudaStream_t s) {
   for (const auto& p : probs) mx = std::max(mx, p.ncol);
   // few columns: thread-per-row kernel (cb = -NC); otherwise shared-memory kernel tiles
   if (mx <= 16) cb = -(mx <= 1 ? 1 : (mx <= 2 ? 2 : (mx <= 4 ? 4 : (mx <= 8 ? 8 : 16))));
-  else cb = mx <= 32 ? 32 : 64;
+  else cb = 64;
   const int step = cb < 0 ? -cb : cb;
+  // split the segments of few-column problems when there are too few CTAs for the GPU
+  parts = 1;
+  part_probs.clear();
+  red.clear();
+  if (cb < 0 && !probs.empty()) {
+    int64_t ctas = 0, maxseg = 1;
+    for (const auto& p : probs) {
+      ctas += (p.ncol + step - 1) / step;
+      maxseg = std::max<int64_t>(maxseg, p.seg1 - p.seg0);
+    }
+    const int64_t want = 4 * 152;
+    parts = (int)std::min<int64_t>(std::max<int64_t>(1, (want + ctas - 1) / ctas), std::min<int64_t>(8, maxseg));
+  }
+  if (parts > 1) {
+    int64_t off = 0;
+    for (int p = 0; p < (int)probs.size(); ++p) {
+      const NearProb& P = probs[p];
+      const int ns = P.seg1 - P.seg0;
+      const int np = std::min(parts, std::max(ns, 1));
+      const int64_t tot = (int64_t)P.rows * P.ncol;
+      red.push_back(make_int4(p, (int)off, np, 0));
+      for (int q = 0; q < np; ++q) {
+        NearProb pp = P;
+        pp.seg0 = P.seg0 + (int)((int64_t)ns * q / np);
+        pp.seg1 = P.seg0 + (int)((int64_t)ns * (q + 1) / np);
+        pp.out = nullptr;          // patched to the scratch below
+        pp.ldo = P.rows;
+        pp.beta = 0;
+        pp.row0 = P.row0;
+        part_probs.push_back(pp);
+      }
+      off += tot * np;
+    }
+    SPD_REQUIRE(off < (1LL << 31), "near field: partial-sum scratch too large");
+    scratch.alloc(std::max<int64_t>(off, 1));
+    int64_t o2 = 0;
+    size_t k = 0;
+    for (size_t r = 0; r < red.size(); ++r) {
+      const NearProb& P = probs[red[r].x];
+      const int64_t tot = (int64_t)P.rows * P.ncol;
+      for (int q = 0; q < red[r].z; ++q, ++k) part_probs[k].out = scratch.p + o2 + (int64_t)q * tot;
+      o2 += tot * red[r].z;
+    }
+  }
   flops = 0.0;
   evals = 0.0;
+  const std::vector<NearProb>& wp = parts > 1 ? part_probs : probs;
+  for (int p = 0; p < (int)wp.size(); ++p)
+    for (int c0 = 0; c0 < wp[p].ncol; c0 += step) work.push_back(make_int2(p, c0));
   for (int p = 0; p < (int)probs.size(); ++p) {
-    for (int c0 = 0; c0 < probs[p].ncol; c0 += step) work.push_back(make_int2(p, c0));
     for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
       const double e = (double)probs[p].rows * segs[g].cols;
       evals += e;
@@ -327,6 +421,10 @@ void NearBatch::upload(cudaStream_t s) {
   d_probs.upload(probs, s);
   d_segs.upload(segs, s);
   d_work.upload(work, s);
+  if (parts > 1) {
+    d_part_probs.upload(part_probs, s);
+    d_red.upload(red, s);
+  }
 }
 
 void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
@@ -334,16 +432,35 @@ void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim
   if (work.empty()) return;
   ProfScope ps(tag, s, flops, 8.0 * evals);
   const unsigned g = (unsigned)work.size();
+  const NearProb* pr = parts > 1 ? d_part_probs.p : d_probs.p;
+  const NearSeg* sg = d_segs.p;
+  const int2* wk = d_work.p;
+#define SPD_NEAR_SMALL(NC)                                                                  \
+  switch (k.kind) {                                                                         \
+    case SPDHSS_K_EXP: k_near_small<NC, SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_GAUSS: k_near_small<NC, SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_MATERN32: k_near_small<NC, SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    default: k_near_small<NC, SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+  }
   switch (cb) {
-    case -1: k_near_small<1><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case -2: k_near_small<2><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case -4: k_near_small<4><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case -8: k_near_small<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case -16: k_near_small<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case 8: k_near<8><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case 16: k_near<16><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    case 32: k_near<32><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
-    default: k_near<64><<<g, 256, 0, s>>>(d_probs.p, d_segs.p, d_work.p, k, xs, ldx, dim); break;
+    case -1: SPD_NEAR_SMALL(1); break;
+    case -2: SPD_NEAR_SMALL(2); break;
+    case -4: SPD_NEAR_SMALL(4); break;
+    case -8: SPD_NEAR_SMALL(8); break;
+    case -16: SPD_NEAR_SMALL(16); break;
+    default:
+      switch (k.kind) {
+        case SPDHSS_K_EXP: k_near_pairs<SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+        case SPDHSS_K_GAUSS: k_near_pairs<SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+        case SPDHSS_K_MATERN32: k_near_pairs<SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+        default: k_near_pairs<SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+      }
+      break;
+  }
+#undef SPD_NEAR_SMALL
+  if (parts > 1) {
+    SPD_LAUNCHED();
+    k_near_reduce<<<(unsigned)red.size(), 128, 0, s>>>(d_probs.p, d_red.p, scratch.p);
   }
   SPD_LAUNCHED();
 }

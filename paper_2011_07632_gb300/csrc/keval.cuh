@@ -72,6 +72,14 @@ struct NearBatch {
   double flops = 0.0;       // 2 * (kernel entries) * columns: the block product
   double evals = 0.0;       // kernel entries of one launch
   const char* tag = "near";
+  // few-column products over too few problems to fill the GPU: every problem's segments
+  // are split into parts written as partial sums, then added in a fixed order
+  int parts = 1;
+  std::vector<NearProb> part_probs;   // one per (problem, part), output into the scratch
+  std::vector<int4> red;              // (problem, scratch offset, parts, 0)
+  DevBuf<NearProb> d_part_probs;
+  DevBuf<int4> d_red;
+  DevBuf<double> scratch;
   void prob(int64_t row0, int rows, double* out, int64_t ldo, int ncol, int beta) {
     NearProb p;
     p.row0 = row0; p.rows = rows; p.out = out; p.ldo = ldo; p.ncol = ncol; p.beta = beta;
