@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-at-scale", action="store_true")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving mode: this many Poisson-arriving mixed requests, served one at "
+                         "a time and then concurrently; prints a serving JSON line")
     ap.add_argument("--matvec-case", type=int, default=0,
                     help="profiling case: H2 of the Gaussian workload at this n, then 5 products "
                          "with 8 columns (prints timings, no benchmark line)")
@@ -406,8 +409,34 @@ def run_matvec_case(n):
     print(json.dumps({"case": "h2_matmul_8rhs", "n": n, "ms": e0.elapsed_time(e1) / 5, "h2": h.info()}))
 
 
+def run_serve(count):
+    """Poisson stream (200 req/s) of build+solve requests, n log-uniform in [1000, 16000], 2D
+    and 3D, kernels {exp, Gaussian ell=0.1, Matern-3/2 ell=0.1}, shift 1e-3, rank 50, 1..16
+    right-hand sides: one instance at a time versus 4 concurrent streams."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import serve
+    reqs = serve.synthetic_stream(count, rate=200.0, n_lo=1000, n_hi=16000, seed=1)
+    serve.Server(serve.GpuExecutor(1), slots=1).run(reqs[:2])          # warm-up
+    free = torch.cuda.mem_get_info()[0]
+    one, st1 = serve.Server(serve.GpuExecutor(1), slots=1).run(reqs)
+    mix, st4 = serve.Server(serve.GpuExecutor(4), slots=4, hbm_budget=int(0.6 * free)).run(reqs)
+    same = max(float(np.linalg.norm(xm - xo) / max(np.linalg.norm(xo), 1e-300))
+               for a, b in zip(one, mix) for xo, xm in zip(a.x, b.x))
+    iters = [int(np.max(r.iters[0])) for r in one if r.iters]
+    print(json.dumps({"metric": "served build+solve requests/s, p50/p99 latency",
+                      "workload": "poisson200_n1000-16000_mixed", "requests": count,
+                      "one_at_a_time": st1, "concurrent_4_streams": st4,
+                      "max_rel_diff_alone_vs_mix": same, "pcg_iters": iters,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def main():
     args = parse()
+    if args.serve:
+        run_serve(args.serve)
+        return
     if args.matvec_case:
         run_matvec_case(args.matvec_case)
         return

@@ -13,6 +13,47 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+cudaStream_t& current_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+
+// One memory pool per device, kept across calls (release threshold: never trim).
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  SPD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  SPD_CUDA(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = UINT64_MAX;
+  SPD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  g_pools[dev] = pool;
+  return pool;
+}
+
+void* pool_alloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  SPD_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s));
+  return p;
+}
+
+void pool_free(void* p, cudaStream_t s) {
+  if (cudaFreeAsync(p, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+  }
+}
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---- per-kernel-family timing with CUDA events on the launching stream ------------------
@@ -138,6 +179,7 @@ int64_t spdhss_profile_report(char* buf, int64_t len) {
 spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
                        int leaf_size, double tol, void* stream, h2_handle* out) {
   return guarded("h2_build", [&] {
+    StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     SPD_REQUIRE(points != nullptr, "points is NULL");
@@ -170,6 +212,7 @@ spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_d
 spdhss_status h2_matmul(h2_handle h, const double* X, double* Y, int nrhs, int64_t ld,
                         void* stream) {
   return guarded("h2_matmul", [&] {
+    StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(h && X && Y, "NULL argument");
     SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     SPD_REQUIRE(ld >= h->th.n, "ld must be >= n");
@@ -271,6 +314,7 @@ extern "C" {
 spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
                            uint64_t seed, void* stream, hss_handle* out) {
   return spd::guarded("spdhss_build", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     SPD_REQUIRE(h2 != nullptr, "NULL H2 handle");
@@ -286,6 +330,7 @@ spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double*
 spdhss_status hss_matmul(hss_handle hs, const double* X, double* Y, int nrhs, int64_t ld,
                          void* stream) {
   return spd::guarded("hss_matmul", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(hs && X && Y, "NULL argument");
     SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     SPD_REQUIRE(ld >= hs->h2->th.n, "ld must be >= n");
@@ -325,6 +370,7 @@ extern "C" {
 
 spdhss_status ulv_factor(hss_handle hs, void* stream, ulv_handle* out) {
   return spd::guarded("ulv_factor", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     SPD_REQUIRE(hs != nullptr, "NULL HSS handle");
@@ -337,6 +383,7 @@ spdhss_status ulv_factor(hss_handle hs, void* stream, ulv_handle* out) {
 spdhss_status ulv_solve(ulv_handle u, const double* B, double* X, int nrhs, int64_t ld,
                         void* stream) {
   return spd::guarded("ulv_solve", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(u && B && X, "NULL argument");
     SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     const int64_t n = u->hs->h2->th.n;
@@ -358,6 +405,7 @@ spdhss_status pcg_solve(h2_handle h2, ulv_handle u, const double* B, double* X, 
                         int64_t ld, double relres_tol, int maxit, int* iters_out,
                         double* relres_out, void* stream) {
   spdhss_status st = spd::guarded("pcg_solve", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(h2 && u && B && X, "NULL argument");
     SPD_REQUIRE(u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
     SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");

@@ -68,28 +68,42 @@ inline double qr_flops(int64_t m, int64_t n, int64_t k, bool pivot) {
     if (!(cond)) throw ::spd::Error(SPDHSS_EINVAL, (msg));      \
   } while (0)
 
-// Plain device allocation owned by its object (cudaMalloc / cudaFree).
+// The stream of the entry point running on this thread: device buffers are allocated and
+// freed in stream order on it (a library memory pool per device), so that freeing a
+// buffer neither synchronizes the device nor waits for other streams.
+cudaStream_t& current_stream();
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s) : prev(current_stream()) { current_stream() = s; }
+  ~StreamScope() { current_stream() = prev; }
+};
+void* pool_alloc(size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
+
+// Device allocation owned by its object, stream ordered on the stream current at allocation.
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t st = nullptr;
   DevBuf() = default;
   explicit DevBuf(size_t count) { alloc(count); }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), st(o.st) { o.p = nullptr; o.n = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { release(); p = o.p; n = o.n; st = o.st; o.p = nullptr; o.n = 0; }
     return *this;
   }
   ~DevBuf() { release(); }
   void alloc(size_t count) {
     release();
     n = count;
-    if (count) SPD_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    st = current_stream();
+    if (count) p = (T*)pool_alloc(count * sizeof(T), st);
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) pool_free(p, st);
     p = nullptr;
     n = 0;
   }

@@ -4,6 +4,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "dense.cuh"
 
@@ -597,12 +598,10 @@ static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_
 template <int C>
 static void trsm_blk_go(const TrsmProb* probs, const int2* work, int64_t nwork, size_t smem,
                         cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    SPD_CUDA(cudaFuncSetAttribute(k_trsm_blk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kTrsmMaxSmem));
-    configured = true;
-  }
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_trsm_blk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmMaxSmem);
+  });
   k_trsm_blk<C><<<(unsigned)nwork, 256, smem, s>>>(probs, work);
 }
 
@@ -831,11 +830,10 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
   cluster = std::max(1, std::min(cluster, 8));
   const size_t smem = (size_t)std::max(1, max_m) * sizeof(double);
   SPD_REQUIRE(smem <= 200 * 1024, "geqp3: matrix too tall for the shared-memory reflector");
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    SPD_CUDA(cudaFuncSetAttribute(k_geqp3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
-    configured = 200 * 1024;
-  }
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_geqp3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(b.size() * cluster), 1, 1);
   cfg.blockDim = dim3(256, 1, 1);

@@ -1,0 +1,85 @@
+"""Host logic of the serving loop (no GPU): admission order, slot and HBM-budget limits,
+latency accounting, failure isolation, percentiles."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2011_07632_gb300 import serve
+
+
+def _reqs(k, gap=0.002, n=1000):
+    return [serve.Request(rid=i, arrival=i * gap, points=np.zeros((n + 10 * i, 3)),
+                          rhs=[np.zeros((n + 10 * i, 1))]) for i in range(k)]
+
+
+def test_percentile_nearest_rank():
+    v = list(range(1, 101))
+    assert serve.percentile(v, 50) == 50
+    assert serve.percentile(v, 99) == 99
+    assert serve.percentile([3.0], 99) == 3.0
+
+
+def test_admission_respects_slots_and_budget():
+    live = {"n": 0, "max": 0, "bytes": 0, "max_bytes": 0}
+    lock = threading.Lock()
+    fp = lambda r: 100 + r.rid          # noqa: E731
+    budget = 450
+
+    def execute(req, slot):
+        with lock:
+            live["n"] += 1
+            live["bytes"] += fp(req)
+            live["max"] = max(live["max"], live["n"])
+            live["max_bytes"] = max(live["max_bytes"], live["bytes"])
+        time.sleep(0.01)
+        with lock:
+            live["n"] -= 1
+            live["bytes"] -= fp(req)
+        return [np.full((req.n, 1), req.rid)], [np.array([1])], [np.array([0.0])]
+
+    srv = serve.Server(execute, slots=3, hbm_budget=budget, footprint=fp)
+    res, st = srv.run(_reqs(20))
+    assert st["completed"] == 20 and st["failed"] == 0
+    assert live["max"] <= 3 and st["max_inflight"] <= 3
+    assert live["max_bytes"] <= budget and st["max_in_use_bytes"] <= budget
+    # first come, first served
+    adm = [r.admitted for r in sorted(res, key=lambda r: r.rid)]
+    assert adm == sorted(adm)
+    assert all(r.latency >= 0.0 and r.finished >= r.admitted >= r.arrival - 1e-3 for r in res)
+    assert all(r.x[0][0, 0] == r.rid for r in res)
+
+
+def test_failed_request_frees_its_slot_and_memory():
+    def execute(req, slot):
+        if req.rid == 2:
+            raise RuntimeError("NOT_SPD: injected on the host")
+        return [np.zeros((req.n, 1))], [np.array([1])], [np.array([0.0])]
+
+    srv = serve.Server(execute, slots=1, hbm_budget=10**12, footprint=lambda r: 10)
+    res, st = srv.run(_reqs(6))
+    assert st["completed"] == 5 and st["failed"] == 1
+    assert "NOT_SPD" in res[2].error
+    assert srv.trace[-1][1] == 0 and srv.trace[-1][2] == 0
+
+
+def test_oversized_request_is_rejected_not_blocking():
+    def execute(req, slot):
+        return [np.zeros((req.n, 1))], [np.array([1])], [np.array([0.0])]
+
+    srv = serve.Server(execute, slots=2, hbm_budget=150, footprint=lambda r: 1000 if r.rid == 1 else 100)
+    res, st = srv.run(_reqs(4))
+    assert res[1].error.startswith("rejected")
+    assert st["completed"] == 3
+
+
+def test_synthetic_stream_shape():
+    reqs = serve.synthetic_stream(12, rate=200.0, n_lo=1000, n_hi=4000, seed=1)
+    arr = [r.arrival for r in reqs]
+    assert arr == sorted(arr) and arr[0] == 0.0
+    assert {r.points.shape[1] for r in reqs} == {2, 3}
+    assert {r.kernel for r in reqs} == {"exp", "gauss", "matern32"}
+    assert all(1000 <= r.n <= 4000 for r in reqs)
+    assert all(1 <= r.rhs[0].shape[1] <= 16 for r in reqs)
+    assert serve.footprint_bytes(reqs[0]) > 0
