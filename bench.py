@@ -198,6 +198,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def roof_hbm(st):
+    """HBM roofline of a kernel family from its per-launch algorithmic bytes and time."""
+    if not st or st["ms"] <= 0:
+        return None
+    peak = 6801.7
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    gbs = st["bytes"] / (st["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "tflops": st["flops"] / (st["ms"] / 1e3) / 1e12}
+
+
 def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     """Components of the n = 200,000 Gaussian workload, each timed with CUDA events."""
     from paper_2011_07632_gb300 import inputs
@@ -227,6 +241,13 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     _, t_us = timed(lambda: [u.solve(B) for _ in range(reps)])
     k = c["pcg_probe_iters"]
     (x, it, rr), t_pcg = timed(lambda: api.pcg_solve(h, u, B, tol=c["relres"], maxit=k))
+    # mixed precision: FP32 copy of the H^2 generators, FP64 preconditioner and residuals
+    h.matmul_mixed(B)
+    native.lib().spdhss_profile(1)
+    _, t_mv32 = timed(lambda: [h.matmul_mixed(B) for _ in range(reps)])
+    prof32 = native.profile_report()
+    native.lib().spdhss_profile(0)
+    (x2, it2, rr2), t_pcg32 = timed(lambda: api.pcg_solve(h, u, B, tol=c["relres"], maxit=k, mixed=True))
     info = h.info()
     cp = prof.get("h2_coupling", {"ms": 0.0, "flops": 0.0, "launches": 1})
     ach = cp["flops"] / max(cp["launches"], 1) / (cp["ms"] / max(cp["launches"], 1) / 1e3) / 1e12
@@ -244,6 +265,13 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
         "roofline_h2_coupling": {"bound": "alu", "achieved": ach, "peak": fp64_peak,
                                  "unit": "TFLOP/s", "frac": ach / fp64_peak,
                                  "share_of_matmul": cp["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)},
+        "mixed": {
+            "h2_matmul_8rhs_fp32_ms": t_mv32 / reps,
+            "pcg_ms_per_iteration": t_pcg32 / max(int(it2.max()), 1),
+            "pcg_relres_after_probe": float(rr2.max()),
+            "roofline_h2_coupling_f32": roof_hbm(prof32.get("h2_coupling_f32")),
+            "kernels": {k2: round(v["ms"] / reps, 3) for k2, v in prof32.items()},
+        },
     }
     u.close(); hs.close(); h.close()
     del pts, B

@@ -185,6 +185,21 @@ spdhss_status pcg_solve(h2_handle h2, ulv_handle ulv, const double* B, double* X
                         int64_t ld, double relres_tol, int maxit, int* iters_out,
                         double* relres_out, void* stream);
 
+/* ---- mixed precision (FP32 products, FP64 factorizations and residuals) ---------------
+ * h2_matmul_mixed: Y = A X like h2_matmul, computed with an FP32 copy of the H^2 generators
+ * (made on the first mixed call and kept in the handle), FP32 near-field kernel entries and
+ * FP32 accumulation; X and Y are FP64.  Relative error ~1e-6.  nrhs in [1, 16].
+ * pcg_solve_mixed: pcg_solve whose products with A inside the iteration are the FP32
+ * product; the ULV preconditioner, the recurrences and the residuals stay FP64, the
+ * recursive residual is replaced by the FP64 true residual every 50 iterations, and
+ * convergence is declared on the FP64 true residual.  Arguments as pcg_solve, nrhs in
+ * [1, 16]. */
+spdhss_status h2_matmul_mixed(h2_handle h2, const double* X, double* Y, int nrhs, int64_t ld,
+                              void* stream);
+spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, double* X,
+                              int nrhs, int64_t ld, double relres_tol, int maxit, int* iters_out,
+                              double* relres_out, void* stream);
+
 /* ---- diagnostics ---------------------------------------------------------------------- */
 const char* spdhss_last_error(void);
 

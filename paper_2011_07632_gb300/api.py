@@ -61,6 +61,14 @@ class H2:
         N.check(N.lib().h2_matmul(self._h, _ptr(Xc), _ptr(Yc), Xc.shape[0], self.n, _stream(stream)))
         return Yc.t()
 
+    def matmul_mixed(self, X, stream=None) -> torch.Tensor:
+        """Y = A X with the FP32 copy of the H^2 matrix (h2_matmul_mixed); at most 16 columns."""
+        Xc = _colmajor(X)
+        Yc = torch.empty_like(Xc)
+        N.check(N.lib().h2_matmul_mixed(self._h, _ptr(Xc), _ptr(Yc), Xc.shape[0], self.n,
+                                        _stream(stream)))
+        return Yc.t()
+
     def info(self) -> dict:
         a = np.zeros(16, np.int64)
         N.check(N.lib().h2_info(self._h, _i64(a)))
@@ -190,8 +198,9 @@ class ULV:
 
 
 def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=None,
-              raise_on_no_convergence: bool = False):
+              raise_on_no_convergence: bool = False, mixed: bool = False):
     """PCG (Sec. 6.2): returns (X (n, nrhs), iterations per column, true relres per column).
+    mixed=True uses the FP32 product with A inside the iteration (pcg_solve_mixed).
 
     B may be a CUDA tensor (device path) or a CPU tensor / numpy array (host buffers: the
     library stages them through the device and X comes back on the host)."""
@@ -203,8 +212,9 @@ def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=
     Xc = torch.empty_like(Bc)
     it = (ctypes.c_int * nrhs)()
     rr = (ctypes.c_double * nrhs)()
-    st = N.lib().pcg_solve(h2._h, ulv._h, _ptr(Bc), _ptr(Xc), nrhs, h2.n, float(tol),
-                           int(maxit), it, rr, _stream(stream))
+    fn = N.lib().pcg_solve_mixed if mixed else N.lib().pcg_solve
+    st = fn(h2._h, ulv._h, _ptr(Bc), _ptr(Xc), nrhs, h2.n, float(tol), int(maxit), it, rr,
+            _stream(stream))
     if st != N.OK and not (st == N.NO_CONVERGENCE and not raise_on_no_convergence):
         N.check(st)
     return Xc.t(), np.array(list(it)), np.array(list(rr))

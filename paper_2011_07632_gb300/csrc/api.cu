@@ -363,7 +363,9 @@ spdhss_status hss_destroy(hss_handle hs) {
 namespace spd {
 void pcg_impl(const spdhss_h2_s* h2, spdhss_ulv_s* u, const double* B, double* X, int nrhs,
               int64_t ld, double tol, int maxit, int* iters_out, double* relres_out,
-              bool& converged, cudaStream_t s);
+              bool& converged, cudaStream_t s, int precision = 0, int refresh = 50);
+void h2_matmul_mixed_impl(spdhss_h2_s* h2, const double* X, double* Y, int nrhs, int64_t ld,
+                          cudaStream_t s);
 }
 
 extern "C" {
@@ -418,6 +420,39 @@ spdhss_status pcg_solve(h2_handle h2, ulv_handle u, const double* B, double* X, 
     if (!conv) throw spd::Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
   });
   return st;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+spdhss_status h2_matmul_mixed(h2_handle h, const double* X, double* Y, int nrhs, int64_t ld,
+                              void* stream) {
+  return spd::guarded("h2_matmul_mixed", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
+    SPD_REQUIRE(h && X && Y, "NULL argument");
+    SPD_REQUIRE(nrhs >= 1 && nrhs <= 16, "nrhs must be in [1, 16]");
+    SPD_REQUIRE(ld >= h->th.n, "ld must be >= n");
+    spd::h2_matmul_mixed_impl(h, X, Y, nrhs, ld, (cudaStream_t)stream);
+  });
+}
+
+spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle u, const double* B, double* X, int nrhs,
+                              int64_t ld, double relres_tol, int maxit, int* iters_out,
+                              double* relres_out, void* stream) {
+  return spd::guarded("pcg_solve_mixed", [&] {
+    spd::StreamScope ss((cudaStream_t)stream);
+    SPD_REQUIRE(h2 && u && B && X, "NULL argument");
+    SPD_REQUIRE(u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
+    SPD_REQUIRE(nrhs >= 1 && nrhs <= 16, "nrhs must be in [1, 16]");
+    SPD_REQUIRE(ld >= h2->th.n, "ld must be >= n");
+    SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
+    SPD_REQUIRE(maxit >= 1, "maxit must be >= 1");
+    bool conv = false;
+    spd::pcg_impl(h2, u, B, X, nrhs, ld, relres_tol, maxit, iters_out, relres_out, conv,
+                  (cudaStream_t)stream, 1, 50);
+    if (!conv) throw spd::Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
+  });
 }
 
 }  // extern "C"

@@ -170,6 +170,18 @@ __device__ __forceinline__ double kernel_r2_k(double r2, double inv_ell) {
   return 1.0 / sqrt(1.0 + r2 * (inv_ell * inv_ell));
 }
 
+// FP32 evaluation for the mixed-precision products.
+template <int KIND>
+__device__ __forceinline__ float kernel_r2_k(float r2, float inv_ell) {
+  if (KIND == SPDHSS_K_EXP) return expf(-sqrtf(r2) * inv_ell);
+  if (KIND == SPDHSS_K_GAUSS) return expf(-r2 * (inv_ell * inv_ell));
+  if (KIND == SPDHSS_K_MATERN32) {
+    const float t = 1.7320508f * sqrtf(r2) * inv_ell;
+    return (1.0f + t) * expf(-t);
+  }
+  return rsqrtf(1.0f + r2 * (inv_ell * inv_ell));
+}
+
 // Points are stored structure-of-arrays: coordinate a of point p at x[a * ldx + p].
 __device__ __forceinline__ double sqdist3(const double* __restrict__ x, int64_t ldx, int dim,
                                           int64_t p, double y0, double y1, double y2) {

@@ -17,24 +17,28 @@ namespace spd {
 // ---------------------------------------------------------------------------------------
 constexpr int GM = 64, GN = 64, GK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs,
-                                              const GemmSeg* __restrict__ segs,
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ probs,
+                                              const GemmSegT<T>* __restrict__ segs,
                                               const int4* __restrict__ tiles) {
   const int4 t = tiles[blockIdx.x];
-  const GemmProb P = probs[t.x];
+  const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
-  __shared__ double As[GK][GM + 1];
-  __shared__ double Bs[GK][GN + 1];
+  __shared__ T As[GK][GM + 1];
+  __shared__ T Bs[GK][GN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
   for (int s = P.seg0; s < P.seg1; ++s) {
-    const GemmSeg S = segs[s];
+    const GemmSegT<T> S = segs[s];
     for (int k0 = 0; k0 < S.K; k0 += GK) {
 #pragma unroll
       for (int r = 0; r < (GM * GK) / 256; ++r) {
@@ -42,7 +46,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
         int mm, kk;
         if (!S.tA) { mm = e % GM; kk = e / GM; } else { kk = e % GK; mm = e / GK; }
         const int gm = m0 + mm, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gm < P.M && gk < S.K)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
         int nn, kk;
         if (!S.tB) { kk = e % GK; nn = e / GK; } else { nn = e % GN; kk = e / GN; }
         const int gn = n0 + nn, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gn < P.N && gk < S.K)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < GK; ++kk) {
-        double a[4], b[4];
+        T a[4], b[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaT(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -82,9 +86,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= P.N) continue;
-      double* c = P.C + gm + (int64_t)gn * P.ldc;
-      double v = P.alpha * acc[i][j];
-      if (P.beta != 0.0) v += P.beta * (*c);
+      T* c = P.C + gm + (int64_t)gn * P.ldc;
+      T v = (T)P.alpha * acc[i][j];
+      if (P.beta != 0.0) v += (T)P.beta * (*c);
       *c = v;
     }
   }
@@ -92,23 +96,23 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb* __restrict__ probs
 
 // Skinny variant for N <= 32 columns: 64-row tiles, 256 threads = 64 rows x 4 column
 // groups of NB/4 columns each, K step 32.  No FMA is spent on padding columns.
-template <int NB>
-__global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ probs,
-                                                const GemmSeg* __restrict__ segs,
+template <class T, int NB>
+__global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__ probs,
+                                                const GemmSegT<T>* __restrict__ segs,
                                                 const int4* __restrict__ tiles) {
   constexpr int MB = 64, KB = 32, CPT = NB / 4;
   const int4 t = tiles[blockIdx.x];
-  const GemmProb P = probs[t.x];
+  const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
-  __shared__ double As[KB][MB + 1];
-  __shared__ double Bs[KB][NB + 1];
+  __shared__ T As[KB][MB + 1];
+  __shared__ T Bs[KB][NB + 1];
   const int tid = threadIdx.x;
   const int row = tid & 63, cg = tid >> 6;
-  double acc[CPT];
+  T acc[CPT];
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = 0.0;
+  for (int c = 0; c < CPT; ++c) acc[c] = 0;
   for (int sg = P.seg0; sg < P.seg1; ++sg) {
-    const GemmSeg S = segs[sg];
+    const GemmSegT<T> S = segs[sg];
     for (int k0 = 0; k0 < S.K; k0 += KB) {
 #pragma unroll
       for (int r = 0; r < (MB * KB) / 256; ++r) {
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
         int mm, kk;
         if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
         const int gm = m0 + mm, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gm < P.M && gk < S.K)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
         int nn, kk;
         if (!S.tB) { kk = e % KB; nn = e / KB; } else { nn = e % NB; kk = e / NB; }
         const int gn = n0 + nn, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gn < P.N && gk < S.K)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
@@ -133,9 +137,9 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
       __syncthreads();
 #pragma unroll 8
       for (int kk = 0; kk < KB; ++kk) {
-        const double a = As[kk][row];
+        const T a = As[kk][row];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = fma(a, Bs[kk][cg * CPT + c], acc[c]);
+        for (int c = 0; c < CPT; ++c) acc[c] = fmaT(a, Bs[kk][cg * CPT + c], acc[c]);
       }
       __syncthreads();
     }
@@ -146,9 +150,9 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
     for (int c = 0; c < CPT; ++c) {
       const int gn = n0 + cg * CPT + c;
       if (gn < P.N) {
-        double* cp = P.C + gm + (int64_t)gn * P.ldc;
-        double v = P.alpha * acc[c];
-        if (P.beta != 0.0) v += P.beta * (*cp);
+        T* cp = P.C + gm + (int64_t)gn * P.ldc;
+        T v = (T)P.alpha * acc[c];
+        if (P.beta != 0.0) v += (T)P.beta * (*cp);
         *cp = v;
       }
     }
@@ -158,24 +162,24 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProb* __restrict__ pro
 // Very skinny variant for N <= 4 columns (matrix-vector like): 64-row tiles, 256 threads =
 // 64 rows x 4 groups that split every 32-wide K chunk; the four partial sums are added in
 // a fixed order through shared memory.
-template <int NB>
-__global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ probs,
-                                                const GemmSeg* __restrict__ segs,
+template <class T, int NB>
+__global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__ probs,
+                                                const GemmSegT<T>* __restrict__ segs,
                                                 const int4* __restrict__ tiles) {
   constexpr int MB = 64, KB = 32;
   const int4 t = tiles[blockIdx.x];
-  const GemmProb P = probs[t.x];
+  const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
-  __shared__ double As[KB][MB + 1];
-  __shared__ double Bs[KB][NB];
-  __shared__ double red[4][NB][MB];
+  __shared__ T As[KB][MB + 1];
+  __shared__ T Bs[KB][NB];
+  __shared__ T red[4][NB][MB];
   const int tid = threadIdx.x;
   const int row = tid & 63, kg = tid >> 6;
-  double acc[NB];
+  T acc[NB];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NB; ++c) acc[c] = 0;
   for (int sg = P.seg0; sg < P.seg1; ++sg) {
-    const GemmSeg S = segs[sg];
+    const GemmSegT<T> S = segs[sg];
     for (int k0 = 0; k0 < S.K; k0 += KB) {
 #pragma unroll
       for (int r = 0; r < (MB * KB) / 256; ++r) {
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ pro
         int mm, kk;
         if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
         const int gm = m0 + mm, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gm < P.M && gk < S.K)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ pro
       if (tid < KB * NB) {
         const int kk = tid % KB, nn = tid / KB;
         const int gn = n0 + nn, gk = k0 + kk;
-        double v = 0.0;
+        T v = 0;
         if (gn < P.N && gk < S.K)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
@@ -200,9 +204,9 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ pro
 #pragma unroll
       for (int q = 0; q < KB / 4; ++q) {
         const int kk = kg * (KB / 4) + q;
-        const double a = As[kk][row];
+        const T a = As[kk][row];
 #pragma unroll
-        for (int c = 0; c < NB; ++c) acc[c] = fma(a, Bs[kk][c], acc[c]);
+        for (int c = 0; c < NB; ++c) acc[c] = fmaT(a, Bs[kk][c], acc[c]);
       }
       __syncthreads();
     }
@@ -217,10 +221,10 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProb* __restrict__ pro
       for (int c = 0; c < NB; ++c) {
         const int gn = n0 + c;
         if (gn < P.N) {
-          const double v0 = (red[0][c][row] + red[1][c][row]) + (red[2][c][row] + red[3][c][row]);
-          double* cp = P.C + gm + (int64_t)gn * P.ldc;
-          double v = P.alpha * v0;
-          if (P.beta != 0.0) v += P.beta * (*cp);
+          const T v0 = (red[0][c][row] + red[1][c][row]) + (red[2][c][row] + red[3][c][row]);
+          T* cp = P.C + gm + (int64_t)gn * P.ldc;
+          T v = (T)P.alpha * v0;
+          if (P.beta != 0.0) v += (T)P.beta * (*cp);
           *cp = v;
         }
       }
@@ -238,20 +242,22 @@ static int gemm_variant(int maxn) {
   return 0;
 }
 
-static void gemm_dispatch(int nb, int g, const GemmProb* pr, const GemmSeg* sg, const int4* tl,
-                          cudaStream_t s) {
+template <class T>
+static void gemm_dispatch(int nb, int g, const GemmProbT<T>* pr, const GemmSegT<T>* sg,
+                          const int4* tl, cudaStream_t s) {
   switch (nb) {
-    case 1: k_gemm_k<1><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 2: k_gemm_k<2><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 4: k_gemm_k<4><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 8: k_gemm_n<8><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 16: k_gemm_n<16><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 32: k_gemm_n<32><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    default: k_gemm<<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 1: k_gemm_k<T, 1><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 2: k_gemm_k<T, 2><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 4: k_gemm_k<T, 4><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 8: k_gemm_n<T, 8><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 16: k_gemm_n<T, 16><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 32: k_gemm_n<T, 32><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    default: k_gemm<T><<<g, 256, 0, s>>>(pr, sg, tl); break;
   }
 }
 
-void GemmBatch::upload(cudaStream_t s) {
+template <class T>
+void GemmBatchT<T>::upload(cudaStream_t s) {
   tiles.clear();
   flops = 0.0;
   bytes = 0.0;
@@ -265,26 +271,30 @@ void GemmBatch::upload(cudaStream_t s) {
     double kk = 0.0;
     for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
       kk += segs[g].K;
-      bytes += 8.0 * ((double)probs[p].M * segs[g].K + (double)segs[g].K * probs[p].N);
+      bytes += sizeof(T) * ((double)probs[p].M * segs[g].K + (double)segs[g].K * probs[p].N);
     }
     flops += 2.0 * probs[p].M * (double)probs[p].N * kk;
-    bytes += 8.0 * (double)probs[p].M * probs[p].N * (probs[p].beta != 0.0 ? 2.0 : 1.0);
+    bytes += sizeof(T) * (double)probs[p].M * probs[p].N * (probs[p].beta != 0.0 ? 2.0 : 1.0);
   }
   d_segs.upload(segs, s);
   d_probs.upload(probs, s);
   d_tiles.upload(tiles, s);
 }
 
-void GemmBatch::launch(cudaStream_t s) const {
+template <class T>
+void GemmBatchT<T>::launch(cudaStream_t s) const {
   const int64_t nt = (int64_t)tiles.size();
   if (nt == 0) return;
   ProfScope ps(tag, s, flops, bytes);
   for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
     const int g = (int)std::min<int64_t>(nt - b0, 2147483647LL);
-    gemm_dispatch(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s);
+    gemm_dispatch<T>(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s);
     SPD_LAUNCHED();
   }
 }
+
+template struct GemmBatchT<double>;
+template struct GemmBatchT<float>;
 
 // ---------------------------------------------------------------------------------------
 // Cholesky, one CTA per matrix, right-looking in global memory
@@ -1015,7 +1025,7 @@ std::vector<int4> gemm_tiles(const std::vector<GemmProb>& probs, int* nb_out) {
 void gemm_launch_raw(const GemmProb* d_probs, const GemmSeg* d_segs, const int4* d_tiles,
                      int64_t ntiles, int nb, cudaStream_t s) {
   if (ntiles <= 0) return;
-  gemm_dispatch(nb, (int)ntiles, d_probs, d_segs, d_tiles, s);
+  gemm_dispatch<double>(nb, (int)ntiles, d_probs, d_segs, d_tiles, s);
   SPD_LAUNCHED();
 }
 

@@ -8,41 +8,47 @@
 namespace spd {
 
 // ---- grouped, segmented GEMM:  C = alpha * sum_s op(A_s) op(B_s) + beta * C -----------
-struct GemmSeg {
-  const double* A;
-  const double* B;
+// T = double (the FP64 path) or float (the mixed-precision H^2 products).
+template <class T>
+struct GemmSegT {
+  const T* A;
+  const T* B;
   int64_t lda, ldb;
   int K;
   int tA, tB;   // 1: use the transpose
 };
-struct GemmProb {
-  double* C;
+template <class T>
+struct GemmProbT {
+  T* C;
   int64_t ldc;
   int M, N;
   int seg0, seg1;
   double alpha, beta;
 };
+using GemmSeg = GemmSegT<double>;
+using GemmProb = GemmProbT<double>;
 
 // Host-side builder of one grouped GEMM launch.
-struct GemmBatch {
-  std::vector<GemmSeg> segs;
-  std::vector<GemmProb> probs;
+template <class T>
+struct GemmBatchT {
+  std::vector<GemmSegT<T>> segs;
+  std::vector<GemmProbT<T>> probs;
   // Start a problem; add its segments with seg(); beta applies once.
-  void prob(double* C, int64_t ldc, int M, int N, double alpha, double beta) {
-    GemmProb p;
+  void prob(T* C, int64_t ldc, int M, int N, double alpha, double beta) {
+    GemmProbT<T> p;
     p.C = C; p.ldc = ldc; p.M = M; p.N = N; p.alpha = alpha; p.beta = beta;
     p.seg0 = p.seg1 = (int)segs.size();
     probs.push_back(p);
   }
-  void seg(const double* A, int64_t lda, int tA, const double* B, int64_t ldb, int tB, int K) {
-    GemmSeg s;
+  void seg(const T* A, int64_t lda, int tA, const T* B, int64_t ldb, int tB, int K) {
+    GemmSegT<T> s;
     s.A = A; s.B = B; s.lda = lda; s.ldb = ldb; s.K = K; s.tA = tA; s.tB = tB;
     segs.push_back(s);
     probs.back().seg1 = (int)segs.size();
   }
   // single-segment convenience
-  void add(double* C, int64_t ldc, int M, int N, const double* A, int64_t lda, int tA,
-           const double* B, int64_t ldb, int tB, int K, double alpha, double beta) {
+  void add(T* C, int64_t ldc, int M, int N, const T* A, int64_t lda, int tA,
+           const T* B, int64_t ldb, int tB, int K, double alpha, double beta) {
     prob(C, ldc, M, N, alpha, beta);
     seg(A, lda, tA, B, ldb, tB, K);
   }
@@ -56,10 +62,12 @@ struct GemmBatch {
   const char* tag = "gemm";
   int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
   double flops = 0.0, bytes = 0.0;   // algorithmic work of one launch
-  DevBuf<GemmSeg> d_segs;
-  DevBuf<GemmProb> d_probs;
+  DevBuf<GemmSegT<T>> d_segs;
+  DevBuf<GemmProbT<T>> d_probs;
   DevBuf<int4> d_tiles;
 };
+using GemmBatch = GemmBatchT<double>;
+using SGemmBatch = GemmBatchT<float>;
 
 // A batch of descriptors of one kind with its device copy.
 template <class P>

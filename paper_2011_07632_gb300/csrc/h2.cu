@@ -334,7 +334,9 @@ static int lca_level(const TreeHost& T, int64_t i, int64_t j) {
   return T.level_of_depth(T.depth_of(i));
 }
 
-void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s) {
+template <class F>
+static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int nslot,
+                            const F* Ub, const F* Cb, cudaStream_t s) {
   const TreeHost& T = h->th;
   const int64_t n = T.n, K = std::max<int64_t>(h->Ktot, 1);
   const int D = T.D;
@@ -345,10 +347,9 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
   p.ys.alloc((size_t)n * W);
   p.xhat.alloc((size_t)K * ncol);
   p.yhat.alloc((size_t)K * W);
-  const double* Ub = h->basis.p;
   auto U = [&](int64_t i) { return Ub + h->U_off[i]; };
   // upward
-  p.up_leaf = GemmBatch();
+  p.up_leaf = GemmBatchT<F>();
   for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i)
     if (h->rank(i) > 0)
       p.up_leaf.add(p.xhat.p + h->skel_off[i], K, h->rank(i), ncol, U(i), h->U_rows[i], 1,
@@ -356,14 +357,14 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
   p.up.clear();
   for (int t = D - 1; t >= 1; --t) {
     p.up.emplace_back();
-    GemmBatch& g = p.up.back();
+    GemmBatchT<F>& g = p.up.back();
     for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i)
       if (h->rank(i) > 0)
         g.add(p.xhat.p + h->skel_off[i], K, h->rank(i), ncol, U(i), h->U_rows[i], 1,
               p.xhat.p + h->skel_off[T.child_begin[i]], K, 0, h->U_rows[i], 1.0, 0.0);
   }
   // coupling
-  p.coupling = GemmBatch();
+  p.coupling = GemmBatchT<F>();
   for (int64_t i = 0; i < T.nn(); ++i) {
     if (h->rank(i) == 0) continue;
     const int lev = T.level_of_depth(T.depth_of(i));
@@ -379,7 +380,7 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
           opened = true;
         }
         const int tr = h->far_trans[e];
-        p.coupling.seg(h->coup.p + h->far_boff[e], tr ? h->rank(j) : h->rank(i), tr,
+        p.coupling.seg(Cb + h->far_boff[e], tr ? h->rank(j) : h->rank(i), tr,
                        p.xhat.p + h->skel_off[j], K, 0, h->rank(j));
       }
     }
@@ -389,7 +390,7 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
   p.down.clear();
   for (int t = 1; t <= D - 1; ++t) {
     p.down.emplace_back();
-    GemmBatch& g = p.down.back();
+    GemmBatchT<F>& g = p.down.back();
     for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i) {
       if (h->rank(i) == 0) continue;
       const int lev = T.level_of_depth(t);
@@ -401,14 +402,14 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
     }
   }
   // leaves
-  p.leaf_out = GemmBatch();
+  p.leaf_out = GemmBatchT<F>();
   for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
     p.leaf_out.prob(p.ys.p + T.begin[i], n, (int)T.size(i), W, 1.0, 0.0);
     if (h->rank(i) > 0)
       p.leaf_out.seg(U(i), h->U_rows[i], 0, p.yhat.p + h->skel_off[i], K, 0, h->rank(i));
   }
   // near field
-  p.near = NearBatch();
+  p.near = NearBatchT<F>();
   for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
     for (int sl = 0; sl < nslot; ++sl) {
       bool opened = false;
@@ -427,11 +428,13 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
       }
     }
   }
-  p.coupling.tag = nslot > 1 ? "h2_coupling_sample" : "h2_coupling";
-  p.near.tag = nslot > 1 ? "near_sample" : "near_h2";
-  p.up_leaf.tag = p.leaf_out.tag = "h2_basis";
-  for (auto& g : p.up) g.tag = "h2_basis";
-  for (auto& g : p.down) g.tag = "h2_basis";
+  const bool f32 = sizeof(F) == 4;
+  p.coupling.tag = nslot > 1 ? "h2_coupling_sample" : (f32 ? "h2_coupling_f32" : "h2_coupling");
+  p.near.tag = nslot > 1 ? "near_sample" : (f32 ? "near_h2_f32" : "near_h2");
+  const char* btag = f32 ? "h2_basis_f32" : "h2_basis";
+  p.up_leaf.tag = p.leaf_out.tag = btag;
+  for (auto& g : p.up) g.tag = btag;
+  for (auto& g : p.down) g.tag = btag;
   p.up_leaf.upload(s);
   for (auto& g : p.up) g.upload(s);
   p.coupling.upload(s);
@@ -441,7 +444,52 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
-void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s) {
+void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s) {
+  h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, h->coup.p, s);
+}
+
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+
+__global__ void k_f2d(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
+}
+
+void convert_d2f(const double* x, float* y, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_d2f<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16), 256, 0, s>>>(x, y, count);
+  SPD_LAUNCHED();
+}
+
+void convert_f2d(const float* x, double* y, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_f2d<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16), 256, 0, s>>>(x, y, count);
+  SPD_LAUNCHED();
+}
+
+H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
+  if (h->basis_f.n == 0) {
+    h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
+    h->coup_f.alloc(std::max<size_t>(h->coup.n, 1));
+    convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
+    convert_d2f(h->coup.p, h->coup_f.p, (int64_t)h->coup.n, s);
+  }
+  auto it = h->plans_f.find(ncol);
+  if (it == h->plans_f.end()) {
+    std::unique_ptr<H2PlanF> p(new H2PlanF());
+    h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, h->coup_f.p, s);
+    it = h->plans_f.emplace(ncol, std::move(p)).first;
+  }
+  return *it->second;
+}
+
+template <class T>
+static void h2_plan_run_t(const spdhss_h2_s* h, const H2PlanT<T>& p, cudaStream_t s) {
   p.up_leaf.launch(s);
   for (const auto& g : p.up) g.launch(s);
   SPD_CUDA(cudaMemsetAsync(p.yhat.p, 0, p.yhat.bytes(), s));
@@ -450,5 +498,8 @@ void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s) {
   p.leaf_out.launch(s);
   p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);
 }
+
+void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s) { h2_plan_run_t(h, p, s); }
+void h2_plan_run(const spdhss_h2_s* h, const H2PlanF& p, cudaStream_t s) { h2_plan_run_t(h, p, s); }
 
 }  // namespace spd

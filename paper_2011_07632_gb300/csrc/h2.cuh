@@ -14,17 +14,22 @@ namespace spd {
 // downward pass, leaf bases and near field.  With nslot > 1 the product is split by the
 // HSS level of the lowest common ancestor of every block (slot l - 2 for level l), which
 // the SPD-HSS sampling uses to form all Y^(k) of Eq. Yk in one pass.
-struct H2Plan {
+// T = double, or float for the mixed-precision product (FP32 copies of the generators,
+// FP32 kernel entries, FP32 accumulation).
+template <class T>
+struct H2PlanT {
   int ncol = 0;      // columns per slot
   int nslot = 1;
-  DevBuf<double> xs, ys, xhat, yhat;   // sorted-order input/output, skeleton-space vectors
-  GemmBatch up_leaf;
-  std::vector<GemmBatch> up;       // per depth D-1 .. 1
-  GemmBatch coupling;
-  std::vector<GemmBatch> down;     // per depth 1 .. D-1
-  GemmBatch leaf_out;
-  NearBatch near;
+  DevBuf<T> xs, ys, xhat, yhat;   // sorted-order input/output, skeleton-space vectors
+  GemmBatchT<T> up_leaf;
+  std::vector<GemmBatchT<T>> up;       // per depth D-1 .. 1
+  GemmBatchT<T> coupling;
+  std::vector<GemmBatchT<T>> down;     // per depth 1 .. D-1
+  GemmBatchT<T> leaf_out;
+  NearBatchT<T> near;
 };
+using H2Plan = H2PlanT<double>;
+using H2PlanF = H2PlanT<float>;
 
 }  // namespace spd
 
@@ -47,6 +52,9 @@ struct spdhss_h2_s {
   spd::DevBuf<double> coup;
   int max_rank = 0;
   std::map<int, std::unique_ptr<spd::H2Plan>> plans;   // by nrhs
+  // FP32 copies of the generators for the mixed-precision products (made on first use)
+  spd::DevBuf<float> basis_f, coup_f;
+  std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
 
   int rank(int64_t i) const { return (int)(skel_off[i + 1] - skel_off[i]); }
 };
@@ -57,6 +65,12 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
 // Y = A X on sorted-order data owned by the plan (plan.xs -> plan.ys)
 void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s);
 void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s);
+// the FP32 plan for ncol columns (generators converted on first use), cached in the handle
+H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s);
+void h2_plan_run(const spdhss_h2_s* h, const H2PlanF& p, cudaStream_t s);
+// element-wise conversions of n x ncol column-major blocks between FP64 and FP32
+void convert_d2f(const double* x, float* y, int64_t count, cudaStream_t s);
+void convert_f2d(const float* x, double* y, int64_t count, cudaStream_t s);
 // permutations between original and sorted order (ld of the original-order data given)
 void permute_to_sorted(const double* X, int64_t ldx, double* Xs, int64_t n, int ncol,
                        const int64_t* perm, cudaStream_t s);

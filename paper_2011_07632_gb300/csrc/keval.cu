@@ -1,5 +1,6 @@
 // Kernel-matrix evaluation kernels (see keval.cuh).
 #include <algorithm>
+#include <type_traits>
 
 #include "keval.cuh"
 
@@ -129,9 +130,9 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 // and a fixed-order sum in shared memory combines the groups.  Every kernel entry is
 // evaluated exactly once per column block, and no FMA is spent on padding.
 // ---------------------------------------------------------------------------------------
-template <int NC, int KIND>
-__global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__ probs,
-                                                    const NearSeg* __restrict__ segs,
+template <class T, int NC, int KIND>
+__global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restrict__ probs,
+                                                    const NearSegT<T>* __restrict__ segs,
                                                     const int2* __restrict__ work, KernelFn kf,
                                                     const double* __restrict__ xs, int64_t ldx,
                                                     int dim) {
@@ -139,15 +140,15 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
   constexpr int CH = NC >= 16 ? 192 : (NC >= 8 ? 256 : 512);
   constexpr int STAGE = CH * (3 + NC);
   constexpr int RED = NC * 256;
-  __shared__ double smem[STAGE > RED ? STAGE : RED];
-  double (*red)[256] = reinterpret_cast<double (*)[256]>(smem);
-  double (*sx)[CH] = reinterpret_cast<double (*)[CH]>(smem);
-  double (*sv)[CH] = reinterpret_cast<double (*)[CH]>(smem + 3 * CH);
+  __shared__ T smem[STAGE > RED ? STAGE : RED];
+  T (*red)[256] = reinterpret_cast<T (*)[256]>(smem);
+  T (*sx)[CH] = reinterpret_cast<T (*)[CH]>(smem);
+  T (*sv)[CH] = reinterpret_cast<T (*)[CH]>(smem + 3 * CH);
   const int2 w = work[blockIdx.x];
-  const NearProb P = probs[w.x];
+  const NearProbT<T> P = probs[w.x];
   const int col0 = w.y;
   const int ncb = min(NC, P.ncol - col0);
-  const double inv_ell = kf.inv_ell;
+  const T inv_ell = (T)kf.inv_ell;
   __shared__ int s_seg, s_q;   // chunk start: segment and offset inside it
   const int t = threadIdx.x;
   for (int rb = 0; rb < P.rows; rb += 256) {
@@ -155,15 +156,15 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
     const int G = max(1, 256 / m);
     const int p = t % m, g = t / m;
     const int64_t gp = P.row0 + rb + p;
-    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    T y0 = 0, y1 = 0, y2 = 0;
     if (g < G) {
-      y0 = xs[gp];
-      y1 = xs[ldx + gp];
-      if (dim == 3) y2 = xs[2 * ldx + gp];
+      y0 = (T)xs[gp];
+      y1 = (T)xs[ldx + gp];
+      if (dim == 3) y2 = (T)xs[2 * ldx + gp];
     }
-    double acc[NC];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = 0;
     if (t == 0) { s_seg = P.seg0; s_q = 0; }
     __syncthreads();
     while (s_seg < P.seg1) {
@@ -171,17 +172,17 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
       {
         int sg = s_seg, q = s_q;
         while (sg < P.seg1 && cnt < CH) {
-          const NearSeg S = segs[sg];
+          const NearSegT<T> S = segs[sg];
           const int take = min(S.cols - q, CH - cnt);
-          const double* xin = S.x + (int64_t)col0 * S.ldx;
+          const T* xin = S.x + (int64_t)col0 * S.ldx;
           for (int e = t; e < take; e += 256) {
             const int64_t gq = S.col0 + q + e;
-            sx[0][cnt + e] = xs[gq];
-            sx[1][cnt + e] = xs[ldx + gq];
-            sx[2][cnt + e] = (dim == 3) ? xs[2 * ldx + gq] : 0.0;
+            sx[0][cnt + e] = (T)xs[gq];
+            sx[1][cnt + e] = (T)xs[ldx + gq];
+            sx[2][cnt + e] = (dim == 3) ? (T)xs[2 * ldx + gq] : (T)0;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-              sv[c][cnt + e] = (c < ncb) ? xin[q + e + (int64_t)c * S.ldx] : 0.0;
+              sv[c][cnt + e] = (c < ncb) ? xin[q + e + (int64_t)c * S.ldx] : (T)0;
           }
           cnt += take;
           q += take;
@@ -194,18 +195,18 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
         if (dim == 3) {
 #pragma unroll 4
           for (int q = g; q < cnt; q += G) {
-            const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q], d2 = y2 - sx[2][q];
-            const double kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1 + d2 * d2, inv_ell);
+            const T d0 = y0 - sx[0][q], d1 = y1 - sx[1][q], d2 = y2 - sx[2][q];
+            const T kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1 + d2 * d2, inv_ell);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = fma(kv, sv[c][q], acc[c]);
+            for (int c = 0; c < NC; ++c) acc[c] = kv * sv[c][q] + acc[c];
           }
         } else {
 #pragma unroll 4
           for (int q = g; q < cnt; q += G) {
-            const double d0 = y0 - sx[0][q], d1 = y1 - sx[1][q];
-            const double kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1, inv_ell);
+            const T d0 = y0 - sx[0][q], d1 = y1 - sx[1][q];
+            const T kv = kernel_r2_k<KIND>(d0 * d0 + d1 * d1, inv_ell);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = fma(kv, sv[c][q], acc[c]);
+            for (int c = 0; c < NC; ++c) acc[c] = kv * sv[c][q] + acc[c];
           }
         }
       }
@@ -216,27 +217,27 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProb* __restrict__
     __syncthreads();
     if (t < m) {
       // the diagonal shift of a self segment: sigma * x_p
-      double shift_x[NC];
+      T shift_x[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) shift_x[c] = 0.0;
+      for (int c = 0; c < NC; ++c) shift_x[c] = 0;
       for (int sg = P.seg0; sg < P.seg1; ++sg) {
-        const NearSeg S = segs[sg];
+        const NearSegT<T> S = segs[sg];
         if (S.self) {
           const int64_t off = P.row0 + rb + t - S.col0;
           if (off >= 0 && off < S.cols) {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-              if (c < ncb) shift_x[c] += kf.shift * S.x[off + (int64_t)(col0 + c) * S.ldx];
+              if (c < ncb) shift_x[c] += (T)kf.shift * S.x[off + (int64_t)(col0 + c) * S.ldx];
           }
         }
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < ncb) {
-          double sum = 0.0;
+          T sum = 0;
           for (int gg = 0; gg < G; ++gg) sum += red[c][t + gg * m];
           sum += shift_x[c];
-          double* o = P.out + (rb + t) + (int64_t)(col0 + c) * P.ldo;
+          T* o = P.out + (rb + t) + (int64_t)(col0 + c) * P.ldo;
           *o = P.beta ? (*o + sum) : sum;
         }
       }
@@ -340,21 +341,23 @@ __global__ void __launch_bounds__(256) k_near_pairs(const NearProb* __restrict__
 }
 
 // out = beta * out + sum of the parts (fixed order), one thread per output entry
-__global__ void k_near_reduce(const NearProb* __restrict__ probs, const int4* __restrict__ red,
-                              const double* __restrict__ scratch) {
+template <class T>
+__global__ void k_near_reduce(const NearProbT<T>* __restrict__ probs, const int4* __restrict__ red,
+                              const T* __restrict__ scratch) {
   const int4 r = red[blockIdx.x];
-  const NearProb P = probs[r.x];
+  const NearProbT<T> P = probs[r.x];
   const int64_t tot = (int64_t)P.rows * P.ncol;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     const int i = (int)(e % P.rows), c = (int)(e / P.rows);
-    double sum = 0.0;
+    T sum = 0;
     for (int q = 0; q < r.z; ++q) sum += scratch[(int64_t)r.y + (int64_t)q * tot + e];
-    double* o = P.out + i + (int64_t)c * P.ldo;
+    T* o = P.out + i + (int64_t)c * P.ldo;
     *o = P.beta ? (*o + sum) : sum;
   }
 }
 
-void NearBatch::upload(cudaStream_t s) {
+template <class T>
+void NearBatchT<T>::upload(cudaStream_t s) {
   work.clear();
   int mx = 1;
   for (const auto& p : probs) mx = std::max(mx, p.ncol);
@@ -378,13 +381,13 @@ void NearBatch::upload(cudaStream_t s) {
   if (parts > 1) {
     int64_t off = 0;
     for (int p = 0; p < (int)probs.size(); ++p) {
-      const NearProb& P = probs[p];
+      const NearProbT<T>& P = probs[p];
       const int ns = P.seg1 - P.seg0;
       const int np = std::min(parts, std::max(ns, 1));
       const int64_t tot = (int64_t)P.rows * P.ncol;
       red.push_back(make_int4(p, (int)off, np, 0));
       for (int q = 0; q < np; ++q) {
-        NearProb pp = P;
+        NearProbT<T> pp = P;
         pp.seg0 = P.seg0 + (int)((int64_t)ns * q / np);
         pp.seg1 = P.seg0 + (int)((int64_t)ns * (q + 1) / np);
         pp.out = nullptr;          // patched to the scratch below
@@ -400,7 +403,7 @@ void NearBatch::upload(cudaStream_t s) {
     int64_t o2 = 0;
     size_t k = 0;
     for (size_t r = 0; r < red.size(); ++r) {
-      const NearProb& P = probs[red[r].x];
+      const NearProbT<T>& P = probs[red[r].x];
       const int64_t tot = (int64_t)P.rows * P.ncol;
       for (int q = 0; q < red[r].z; ++q, ++k) part_probs[k].out = scratch.p + o2 + (int64_t)q * tot;
       o2 += tot * red[r].z;
@@ -408,7 +411,7 @@ void NearBatch::upload(cudaStream_t s) {
   }
   flops = 0.0;
   evals = 0.0;
-  const std::vector<NearProb>& wp = parts > 1 ? part_probs : probs;
+  const std::vector<NearProbT<T>>& wp = parts > 1 ? part_probs : probs;
   for (int p = 0; p < (int)wp.size(); ++p)
     for (int c0 = 0; c0 < wp[p].ncol; c0 += step) work.push_back(make_int2(p, c0));
   for (int p = 0; p < (int)probs.size(); ++p) {
@@ -427,20 +430,21 @@ void NearBatch::upload(cudaStream_t s) {
   }
 }
 
-void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
-                       cudaStream_t s) const {
+template <class T>
+void NearBatchT<T>::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
+                           cudaStream_t s) const {
   if (work.empty()) return;
   ProfScope ps(tag, s, flops, 8.0 * evals);
   const unsigned g = (unsigned)work.size();
-  const NearProb* pr = parts > 1 ? d_part_probs.p : d_probs.p;
-  const NearSeg* sg = d_segs.p;
+  const NearProbT<T>* pr = parts > 1 ? d_part_probs.p : d_probs.p;
+  const NearSegT<T>* sg = d_segs.p;
   const int2* wk = d_work.p;
 #define SPD_NEAR_SMALL(NC)                                                                  \
   switch (k.kind) {                                                                         \
-    case SPDHSS_K_EXP: k_near_small<NC, SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
-    case SPDHSS_K_GAUSS: k_near_small<NC, SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
-    case SPDHSS_K_MATERN32: k_near_small<NC, SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
-    default: k_near_small<NC, SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_EXP: k_near_small<T, NC, SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_GAUSS: k_near_small<T, NC, SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_MATERN32: k_near_small<T, NC, SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    default: k_near_small<T, NC, SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
   }
   switch (cb) {
     case -1: SPD_NEAR_SMALL(1); break;
@@ -449,20 +453,27 @@ void NearBatch::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim
     case -8: SPD_NEAR_SMALL(8); break;
     case -16: SPD_NEAR_SMALL(16); break;
     default:
-      switch (k.kind) {
-        case SPDHSS_K_EXP: k_near_pairs<SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
-        case SPDHSS_K_GAUSS: k_near_pairs<SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
-        case SPDHSS_K_MATERN32: k_near_pairs<SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
-        default: k_near_pairs<SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+      if constexpr (std::is_same<T, double>::value) {
+        switch (k.kind) {
+          case SPDHSS_K_EXP: k_near_pairs<SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+          case SPDHSS_K_GAUSS: k_near_pairs<SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+          case SPDHSS_K_MATERN32: k_near_pairs<SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+          default: k_near_pairs<SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+        }
+      } else {
+        throw Error(SPDHSS_EINVAL, "mixed-precision near field supports at most 16 columns");
       }
       break;
   }
 #undef SPD_NEAR_SMALL
   if (parts > 1) {
     SPD_LAUNCHED();
-    k_near_reduce<<<(unsigned)red.size(), 128, 0, s>>>(d_probs.p, d_red.p, scratch.p);
+    k_near_reduce<T><<<(unsigned)red.size(), 128, 0, s>>>(d_probs.p, d_red.p, scratch.p);
   }
   SPD_LAUNCHED();
 }
+
+template struct NearBatchT<double>;
+template struct NearBatchT<float>;
 
 }  // namespace spd

@@ -45,49 +45,57 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 // out (rows x ncol, ld ldo), accumulated (beta = 1) or overwritten (beta = 0).
 // Segment: columns [col0, col0 + cols) of the sorted points with their input block x
 // (cols x ncol, ld ldx); self = 1 adds shift * x on the diagonal.
-struct NearProb {
+// T = double, or float for the mixed-precision products (kernel entries evaluated and
+// accumulated in FP32, few columns only).
+template <class T>
+struct NearProbT {
   int64_t row0;
   int rows;
-  double* out;
+  T* out;
   int64_t ldo;
   int ncol;
   int seg0, seg1;
   int beta;
 };
-struct NearSeg {
+template <class T>
+struct NearSegT {
   int64_t col0;
   int cols;
-  const double* x;
+  const T* x;
   int64_t ldx;
   int self;
 };
-struct NearBatch {
-  std::vector<NearProb> probs;
-  std::vector<NearSeg> segs;
+using NearProb = NearProbT<double>;
+using NearSeg = NearSegT<double>;
+
+template <class T>
+struct NearBatchT {
+  std::vector<NearProbT<T>> probs;
+  std::vector<NearSegT<T>> segs;
   std::vector<int2> work;   // (prob, first column)
-  DevBuf<NearProb> d_probs;
-  DevBuf<NearSeg> d_segs;
+  DevBuf<NearProbT<T>> d_probs;
+  DevBuf<NearSegT<T>> d_segs;
   DevBuf<int2> d_work;
-  int cb = 8;               // column block per CTA: 32/64 tile kernel, -NC few-column kernel
+  int cb = 8;               // column block per CTA: 64 pair-tile kernel, -NC few-column kernel
   double flops = 0.0;       // 2 * (kernel entries) * columns: the block product
   double evals = 0.0;       // kernel entries of one launch
   const char* tag = "near";
   // few-column products over too few problems to fill the GPU: every problem's segments
   // are split into parts written as partial sums, then added in a fixed order
   int parts = 1;
-  std::vector<NearProb> part_probs;   // one per (problem, part), output into the scratch
-  std::vector<int4> red;              // (problem, scratch offset, parts, 0)
-  DevBuf<NearProb> d_part_probs;
+  std::vector<NearProbT<T>> part_probs;   // one per (problem, part), output into the scratch
+  std::vector<int4> red;                  // (problem, scratch offset, parts, 0)
+  DevBuf<NearProbT<T>> d_part_probs;
   DevBuf<int4> d_red;
-  DevBuf<double> scratch;
-  void prob(int64_t row0, int rows, double* out, int64_t ldo, int ncol, int beta) {
-    NearProb p;
+  DevBuf<T> scratch;
+  void prob(int64_t row0, int rows, T* out, int64_t ldo, int ncol, int beta) {
+    NearProbT<T> p;
     p.row0 = row0; p.rows = rows; p.out = out; p.ldo = ldo; p.ncol = ncol; p.beta = beta;
     p.seg0 = p.seg1 = (int)segs.size();
     probs.push_back(p);
   }
-  void seg(int64_t col0, int cols, const double* x, int64_t ldx, int self) {
-    NearSeg g;
+  void seg(int64_t col0, int cols, const T* x, int64_t ldx, int self) {
+    NearSegT<T> g;
     g.col0 = col0; g.cols = cols; g.x = x; g.ldx = ldx; g.self = self;
     segs.push_back(g);
     probs.back().seg1 = (int)segs.size();
@@ -100,5 +108,7 @@ struct NearBatch {
     launch(k, xs, ldx, dim, s);
   }
 };
+using NearBatch = NearBatchT<double>;
+using NearBatchF = NearBatchT<float>;
 
 }  // namespace spd

@@ -86,9 +86,13 @@ __global__ void k_sub(const double* __restrict__ b, const double* __restrict__ a
   if (e < count) out[e] = b[e] - ax[e];
 }
 
+// precision = 0: FP64 throughout.  precision = 1: the product with A inside the iteration
+// uses the FP32 copy of the H^2 matrix (FP32 kernel entries and accumulation); the ULV
+// preconditioner, the recurrences and every residual check stay FP64, and every
+// `refresh` iterations the recursive residual is replaced by the FP64 true residual.
 void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* X, int nrhs,
               int64_t ld, double tol, int maxit, int* iters_out, double* relres_out,
-              bool& converged, cudaStream_t s) {
+              bool& converged, cudaStream_t s, int precision = 0, int refresh = 50) {
   spdhss_h2_s* h2 = const_cast<spdhss_h2_s*>(h2c);
   const int64_t n = h2->th.n;
   const int64_t nc = n * nrhs;
@@ -109,6 +113,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   UlvPlan& PU = ulv_plan(u, nrhs, s);
   double* p = PA.xs.p;
   double* q = PA.ys.p;
+  H2PlanF* PF = precision ? &h2_plan_f(h2, nrhs, s) : nullptr;
   double* z = PU.bw[0].p;
   DevBuf<double> bs(nc), x(nc), r(nc), part((size_t)DOT_BLOCKS * nrhs), sc((size_t)4 * nrhs);
   DevBuf<int> done(nrhs);
@@ -161,7 +166,13 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   };
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
-    h2_plan_run(h2, PA, s);                       // q = A p
+    if (PF) {                                     // q = A p in FP32
+      convert_d2f(p, PF->xs.p, nc, s);
+      h2_plan_run(h2, *PF, s);
+      convert_f2d(PF->ys.p, q, nc, s);
+    } else {
+      h2_plan_run(h2, PA, s);                     // q = A p
+    }
     dots(p, q, n, nrhs, part.p, pq, s);
     k_axpy_xr<<<gb, 256, 0, s>>>(x.p, r.p, p, q, n, nrhs, rz, pq, done.p);
     SPD_LAUNCHED();
@@ -197,6 +208,12 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     bool all = true;
     for (int c = 0; c < nrhs; ++c) all = all && hdone[c] == 1;
     if (all) break;
+    if (PF && refresh > 0 && it % refresh == 0) {
+      // refine: the recursive residual of the FP32 product drifts; replace it by b - A x
+      std::vector<double> trel;
+      true_residual(trel, false);
+      SPD_CUDA(cudaMemcpyAsync(r.p, PR.ys.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     SPD_CUDA(cudaMemcpyAsync(z, r.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ulv_solve_sorted(u, PU, s);                   // z = M^{-1} r
     dots(r.p, z, n, nrhs, part.p, rzn, s);
@@ -227,6 +244,18 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     permute_from_sorted(x.p, X, ld, n, nrhs, perm, s);
     SPD_CUDA(cudaStreamSynchronize(s));
   }
+}
+
+void h2_matmul_mixed_impl(spdhss_h2_s* h2, const double* X, double* Y, int nrhs, int64_t ld,
+                          cudaStream_t s) {
+  const int64_t n = h2->th.n;
+  H2PlanF& PF = h2_plan_f(h2, nrhs, s);
+  DevBuf<double> tmp((size_t)n * nrhs);
+  permute_to_sorted(X, ld, tmp.p, n, nrhs, h2->td.perm.p, s);
+  convert_d2f(tmp.p, PF.xs.p, n * nrhs, s);
+  h2_plan_run(h2, PF, s);
+  convert_f2d(PF.ys.p, tmp.p, n * nrhs, s);
+  permute_from_sorted(tmp.p, Y, ld, n, nrhs, h2->td.perm.p, s);
 }
 
 }  // namespace spd

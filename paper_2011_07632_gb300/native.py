@@ -50,6 +50,9 @@ _SIGS = {
     "ulv_solve": [_P, _P, _P, _I, _I64, _P],
     "ulv_destroy": [_P],
     "ulv_solve_noalloc": [_P, _P, _P, _I, _I64, _P],
+    "h2_matmul_mixed": [_P, _P, _P, _I, _I64, _P],
+    "pcg_solve_mixed": [_P, _P, _P, _P, _I, _I64, _D, _I, ctypes.POINTER(_I),
+                        ctypes.POINTER(_D), _P],
     "pcg_solve": [_P, _P, _P, _P, _I, _I64, _D, _I, ctypes.POINTER(_I),
                   ctypes.POINTER(_D), _P],
 }

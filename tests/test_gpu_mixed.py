@@ -1,0 +1,43 @@
+"""Mixed precision: FP32 H^2 products against the FP64 product and the exact kernel matrix;
+PCG with the FP32 product reaches the FP64 true-residual tolerance."""
+import numpy as np
+import pytest
+
+from oracle import kernels as OK
+from paper_2011_07632_gb300 import inputs
+
+from gpu_util import need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind,ell,dim,nrhs", [("exp", 1.0, 3, 1), ("gauss", 0.2, 3, 8),
+                                               ("matern32", 0.1, 2, 3), ("imq", 0.5, 3, 16)])
+def test_fp32_product_accuracy(kind, ell, dim, nrhs):
+    api = need_gpu()
+    n = 3000
+    X = inputs.uniform_cube(n, dim, 5)
+    h = api.H2(X, kind, ell, 1e-3, 64, 1e-8)
+    x = inputs.rhs(n, nrhs, 6)
+    y64 = h.matmul(x).cpu().numpy()
+    y32 = h.matmul_mixed(x).cpu().numpy()
+    A = OK.dense_matrix(OK.NAMES[kind], ell, 1e-3, X)
+    assert rel(y32, y64) < 2e-5
+    assert rel(y32, A @ x) < 2e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_mixed_pcg_reaches_fp64_tolerance(nrhs):
+    api = need_gpu()
+    n = 4096
+    X = inputs.uniform_cube(n, 3, 0)
+    h = api.H2(X, "exp", 1.0, 1e-2, 64, 1e-8)
+    u = api.ULV(api.HSS(h, 50, 10, omega=inputs.sketch(n, 60, 2)))
+    b = inputs.rhs(n, nrhs, 1)
+    x64, it64, rr64 = api.pcg_solve(h, u, b, tol=1e-6)
+    x32, it32, rr32 = api.pcg_solve(h, u, b, tol=1e-6, mixed=True, raise_on_no_convergence=True)
+    assert np.all(rr32 <= 1e-6)
+    assert np.all(it32 <= 2 * it64 + 10)
+    # the FP64 residual of the mixed solution, recomputed with the FP64 product
+    r = b - h.matmul(x32).cpu().numpy()
+    assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.01e-6)
