@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--matvec-case", type=int, default=0,
                     help="profiling case: H2 of the Gaussian workload at this n, then 5 products "
                          "with 8 columns (prints timings, no benchmark line)")
+    ap.add_argument("--mixed", action="store_true",
+                    help="with --matvec-case: also 5 FP32 products (mixed precision)")
     return ap.parse_args()
 
 
@@ -417,7 +419,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_matvec_case(n):
+def run_matvec_case(n, mixed=False):
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -434,7 +436,16 @@ def run_matvec_case(n):
         h.matmul(B)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"case": "h2_matmul_8rhs", "n": n, "ms": e0.elapsed_time(e1) / 5, "h2": h.info()}))
+    out = {"case": "h2_matmul_8rhs", "n": n, "ms": e0.elapsed_time(e1) / 5, "h2": h.info()}
+    if mixed:
+        h.matmul_mixed(B)
+        e0.record()
+        for _ in range(5):
+            h.matmul_mixed(B)
+        e1.record()
+        torch.cuda.synchronize()
+        out["fp32_ms"] = e0.elapsed_time(e1) / 5
+    print(json.dumps(out))
 
 
 def run_serve(count):
@@ -466,7 +477,7 @@ def main():
         run_serve(args.serve)
         return
     if args.matvec_case:
-        run_matvec_case(args.matvec_case)
+        run_matvec_case(args.matvec_case, args.mixed)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -365,7 +365,7 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   }
   // coupling
   p.coupling = GemmBatchT<F>();
-  for (int64_t i = 0; i < T.nn(); ++i) {
+  for (int64_t i = 0; Cb != nullptr && i < T.nn(); ++i) {
     if (h->rank(i) == 0) continue;
     const int lev = T.level_of_depth(T.depth_of(i));
     for (int sl = 0; sl < nslot; ++sl) {
@@ -472,17 +472,322 @@ void convert_f2d(const float* x, double* y, int64_t count, cudaStream_t s) {
   SPD_LAUNCHED();
 }
 
+// FP64 coupling block (owner orientation, possibly transposed) -> FP32 destination-major
+struct CopyD2F {
+  const double* src;
+  int64_t lds;
+  int trans;
+  float* dst;
+  int64_t ldd;
+  int m, n;
+};
+
+__global__ void k_copy_d2f(const CopyD2F* __restrict__ probs) {
+  const CopyD2F P = probs[blockIdx.y];
+  const int64_t tot = (int64_t)P.m * P.n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % P.m), j = (int)(e / P.m);
+    const double v = P.trans ? P.src[j + (int64_t)i * P.lds] : P.src[i + (int64_t)j * P.lds];
+    P.dst[i + (int64_t)j * P.ldd] = (float)v;
+  }
+}
+
+// CTA of 256 threads on rows [r0, r0 + 256) of node i's coupling matrix and a range of
+// its chunks.  With Mw warps of rows, the CTA holds G = 8 / Mw groups; in round t group g
+// takes chunk t * G + g.  Partial sums of the groups are added in group order, and the
+// parts of a node split over several CTAs are added in part order (deterministic).
+constexpr int kRowChunk = 64;
+constexpr int64_t kRowItemEntries = int64_t(1) << 20;   // coupling entries per CTA (target)
+
+__host__ __device__ constexpr int rowcoup_ncp(int nc) { return nc < 4 ? nc : 4 * ((nc + 3) / 4); }
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __restrict__ probs,
+                                                       const RowCoupChunk* __restrict__ chunks,
+                                                       const RowCoupWork* __restrict__ work,
+                                                       float* __restrict__ partial, int c0) {
+  constexpr int NCP = rowcoup_ncp(NC);
+  extern __shared__ __align__(16) float smem_rc[];
+  float* xs = smem_rc;                        // [G][kRowChunk][NCP]
+  const RowCoupWork W = work[blockIdx.x];
+  const RowCoupProb P = probs[W.p];
+  const int rows = min(P.M - W.r0, 256);
+  const int Mw = (rows + 31) / 32;
+  const int G = 8 / Mw;
+  const int RW = 32 * Mw;
+  const int tid = threadIdx.x;
+  const int g = tid / RW, rl = tid % RW;
+  const int r = W.r0 + rl;
+  const bool active = g < G && rl < rows;
+  float acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+  const int64_t M = P.M;
+  const int nch = W.ch1 - W.ch0;
+  const int rounds = (nch + G - 1) / G;
+  const int ncl = min(NC, P.ncol - c0);   // columns c0 .. c0 + ncl - 1 of this launch
+  for (int t = 0; t < rounds; ++t) {
+    // stage: element e -> (group gg, column c, row kk), kk fastest for coalesced reads
+    for (int e = tid; e < G * NC * kRowChunk; e += 256) {
+      const int gg = e / (NC * kRowChunk);
+      const int rem = e - gg * NC * kRowChunk;
+      const int c = rem / kRowChunk, kk = rem - c * kRowChunk;
+      const int ch = t * G + gg;
+      float v = 0.0f;
+      if (ch < nch) {
+        const RowCoupChunk C = chunks[W.ch0 + ch];
+        if (kk < C.K && c < ncl) v = C.x[(int64_t)(c0 + c) * C.ldx + kk];
+      }
+      xs[(gg * kRowChunk + kk) * NCP + c] = v;
+    }
+    __syncthreads();
+    const int ch = t * G + g;
+    if (active && ch < nch) {
+      const RowCoupChunk C = chunks[W.ch0 + ch];
+      const float* a = P.A + r + C.col * M;
+      const float* xg = xs + g * kRowChunk * NCP;
+      for (int kk0 = 0; kk0 < C.K; kk0 += 16) {
+        float b[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          b[u] = (kk0 + u < C.K) ? __ldg(a + (int64_t)(kk0 + u) * M) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float* xr = xg + (kk0 + u) * NCP;
+          if constexpr (NC >= 4) {
+#pragma unroll
+            for (int c4 = 0; c4 < NCP / 4; ++c4) {
+              const float4 v = reinterpret_cast<const float4*>(xr)[c4];
+              if (4 * c4 + 0 < NC) acc[4 * c4 + 0] = fmaf(b[u], v.x, acc[4 * c4 + 0]);
+              if (4 * c4 + 1 < NC) acc[4 * c4 + 1] = fmaf(b[u], v.y, acc[4 * c4 + 1]);
+              if (4 * c4 + 2 < NC) acc[4 * c4 + 2] = fmaf(b[u], v.z, acc[4 * c4 + 2]);
+              if (4 * c4 + 3 < NC) acc[4 * c4 + 3] = fmaf(b[u], v.w, acc[4 * c4 + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = fmaf(b[u], xr[c], acc[c]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // group partial sums through shared memory: red[g][c][rl]
+  float* red = smem_rc;
+  if (G > 1) {
+    if (active)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) red[(g * NC + c) * RW + rl] = acc[c];
+    __syncthreads();
+    if (g == 0 && active) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float v = red[c * RW + rl];
+        for (int gg = 1; gg < G; ++gg) v += red[(gg * NC + c) * RW + rl];
+        acc[c] = v;
+      }
+    }
+  }
+  if (g == 0 && active) {
+    if (W.part < 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < ncl) P.C[r + (int64_t)(c0 + c) * P.ldc] = acc[c];
+    } else {
+      float* pt = partial + W.part * (NC * 256);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pt[c * 256 + rl] = acc[c];
+    }
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_coupling_rows_reduce(const RowCoupProb* __restrict__ probs,
+                                                              const RowCoupRed* __restrict__ red,
+                                                              const float* __restrict__ partial,
+                                                              int c0) {
+  const RowCoupRed R = red[blockIdx.x];
+  const RowCoupProb P = probs[R.p];
+  const int rl = threadIdx.x;
+  if (rl >= min(P.M - R.r0, 256)) return;
+  const int ncl = min(NC, P.ncol - c0);
+  for (int c = 0; c < ncl; ++c) {
+    float v = 0.0f;
+    for (int q = 0; q < R.nparts; ++q) v += partial[(R.part0 + q) * (NC * 256) + c * 256 + rl];
+    P.C[R.r0 + rl + (int64_t)(c0 + c) * P.ldc] = v;
+  }
+}
+
+static int rowcoup_nc(int ncol) {
+  return ncol <= 1 ? 1 : (ncol <= 2 ? 2 : (ncol <= 4 ? 4 : (ncol <= 8 ? 8 : 16)));
+}
+
+void RowCoupBatch::upload(cudaStream_t s) {
+  work.clear();
+  red.clear();
+  flops = bytes = 0.0;
+  int64_t nparts = 0;
+  for (int p = 0; p < (int)probs.size(); ++p) {
+    const RowCoupProb& P = probs[p];
+    int64_t kt = 0;
+    for (int g = P.ch0; g < P.ch1; ++g) kt += chunks[g].K;
+    flops += 2.0 * P.M * (double)kt * P.ncol;
+    bytes += 4.0 * P.M * (double)kt;
+    for (int r0 = 0; r0 < P.M; r0 += 256) {
+      const int rows = std::min(P.M - r0, 256);
+      // cut the chunk range into parts of about kRowItemEntries entries
+      std::vector<std::pair<int, int>> parts;
+      int start = P.ch0;
+      int64_t acc = 0;
+      for (int g = P.ch0; g < P.ch1; ++g) {
+        acc += (int64_t)rows * chunks[g].K;
+        if (acc >= kRowItemEntries && g + 1 < P.ch1) {
+          parts.emplace_back(start, g + 1);
+          start = g + 1;
+          acc = 0;
+        }
+      }
+      parts.emplace_back(start, P.ch1);
+      if (parts.size() == 1) {
+        work.push_back(RowCoupWork{p, r0, parts[0].first, parts[0].second, -1});
+      } else {
+        red.push_back(RowCoupRed{p, r0, nparts, (int)parts.size()});
+        for (auto& pr : parts) work.push_back(RowCoupWork{p, r0, pr.first, pr.second, nparts++});
+      }
+    }
+  }
+  // the largest items first, so that the long ones do not form the tail
+  std::stable_sort(work.begin(), work.end(), [&](const RowCoupWork& x, const RowCoupWork& y) {
+    auto sz = [&](const RowCoupWork& w) {
+      int64_t k = 0;
+      for (int g = w.ch0; g < w.ch1; ++g) k += chunks[g].K;
+      return k * std::min(probs[w.p].M - w.r0, 256);
+    };
+    return sz(x) > sz(y);
+  });
+  d_probs.upload(probs, s);
+  d_chunks.upload(chunks, s);
+  d_work.upload(work, s);
+  d_red.upload(red, s);
+  partial.alloc(std::max<int64_t>(nparts, 1) * rowcoup_nc(ncol) * 256);
+}
+
+template <int NC>
+static void rowcoup_go(const RowCoupBatch& b, cudaStream_t s) {
+  constexpr int NCP = rowcoup_ncp(NC);
+  const size_t smem = (size_t)8 * kRowChunk * NCP * sizeof(float);
+  // the reduction reuses the staging buffer: G * NC * RW <= 256 * NC floats
+  static_assert(8 * kRowChunk * NCP >= 256 * NC, "reduction buffer");
+  if (smem > 48 * 1024)
+    SPD_CUDA(cudaFuncSetAttribute(k_coupling_rows<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  for (int c0 = 0; c0 < b.ncol; c0 += NC) {
+    k_coupling_rows<NC><<<(unsigned)b.work.size(), 256, smem, s>>>(
+        b.d_probs.p, b.d_chunks.p, b.d_work.p, b.partial.p, c0);
+    SPD_LAUNCHED();
+    if (!b.red.empty()) {
+      k_coupling_rows_reduce<NC><<<(unsigned)b.red.size(), 256, 0, s>>>(b.d_probs.p, b.d_red.p,
+                                                                        b.partial.p, c0);
+      SPD_LAUNCHED();
+    }
+  }
+}
+
+void RowCoupBatch::launch(cudaStream_t s) const {
+  if (work.empty()) return;
+  ProfScope ps("h2_coupling_f32", s, flops, bytes);
+  switch (rowcoup_nc(ncol)) {
+    case 1: rowcoup_go<1>(*this, s); break;
+    case 2: rowcoup_go<2>(*this, s); break;
+    case 4: rowcoup_go<4>(*this, s); break;
+    case 8: rowcoup_go<8>(*this, s); break;
+    default: rowcoup_go<16>(*this, s); break;
+  }
+}
+
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
+  const TreeHost& T = h->th;
   if (h->basis_f.n == 0) {
     h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
-    h->coup_f.alloc(std::max<size_t>(h->coup.n, 1));
     convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
-    convert_d2f(h->coup.p, h->coup_f.p, (int64_t)h->coup.n, s);
+    // destination-major FP32 couplings
+    const int64_t NN = T.nn();
+    h->coup_fd_off.assign(NN + 1, 0);
+    for (int64_t i = 0; i < NN; ++i) {
+      int64_t kt = 0;
+      if (h->rank(i) > 0)
+        for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) kt += h->rank(T.far_idx[e]);
+      h->coup_fd_off[i + 1] = h->coup_fd_off[i] + (int64_t)h->rank(i) * kt;
+    }
+    h->coup_fd.alloc(std::max<int64_t>(h->coup_fd_off[NN], 1));
+    std::vector<CopyD2F> cps;
+    int64_t maxe = 1;
+    for (int64_t i = 0; i < NN; ++i) {
+      const int ki = h->rank(i);
+      if (ki == 0) continue;
+      int64_t col = 0;
+      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+        const int64_t j = T.far_idx[e];
+        const int kj = h->rank(j);
+        if (kj == 0) continue;
+        CopyD2F c;
+        c.src = h->coup.p + h->far_boff[e];
+        c.trans = h->far_trans[e];
+        c.lds = c.trans ? kj : ki;
+        c.dst = h->coup_fd.p + h->coup_fd_off[i] + col * ki;
+        c.ldd = ki;
+        c.m = ki;
+        c.n = kj;
+        cps.push_back(c);
+        maxe = std::max<int64_t>(maxe, (int64_t)ki * kj);
+        col += kj;
+      }
+    }
+    for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
+      std::vector<CopyD2F> part(cps.begin() + b0, cps.begin() + std::min(cps.size(), b0 + 65535));
+      DevBuf<CopyD2F> dp;
+      dp.upload(part, s);
+      const int gx = (int)std::min<int64_t>(ceil_div(maxe, 256), 16);
+      k_copy_d2f<<<dim3(gx, (unsigned)part.size()), 256, 0, s>>>(dp.p);
+      SPD_LAUNCHED();
+      SPD_CUDA(cudaStreamSynchronize(s));
+    }
   }
   auto it = h->plans_f.find(ncol);
   if (it == h->plans_f.end()) {
     std::unique_ptr<H2PlanF> p(new H2PlanF());
-    h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, h->coup_f.p, s);
+    h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, nullptr, s);
+    // coupling: one streaming problem per destination node
+    const int64_t K = std::max<int64_t>(h->Ktot, 1);
+    RowCoupBatch& rb = p->rowcoup;
+    rb.ncol = ncol;
+    for (int64_t i = 0; i < T.nn(); ++i) {
+      const int ki = h->rank(i);
+      if (ki == 0 || T.far_off[i] == T.far_off[i + 1]) continue;
+      RowCoupProb pr;
+      pr.C = p->yhat.p + h->skel_off[i];
+      pr.ldc = K;
+      pr.M = ki;
+      pr.ncol = ncol;
+      pr.A = h->coup_fd.p + h->coup_fd_off[i];
+      pr.ch0 = (int)rb.chunks.size();
+      int64_t col = 0;
+      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+        const int64_t j = T.far_idx[e];
+        const int kj = h->rank(j);
+        for (int k0 = 0; k0 < kj; k0 += kRowChunk)
+          rb.chunks.push_back(RowCoupChunk{p->xhat.p + h->skel_off[j] + k0, K, col + k0,
+                                           std::min(kRowChunk, kj - k0)});
+        col += kj;
+      }
+      pr.ch1 = (int)rb.chunks.size();
+      rb.probs.push_back(pr);
+    }
+    rb.upload(s);
+    p->use_rowcoup = true;
+    p->coupling = GemmBatchT<float>();
+    SPD_CUDA(cudaStreamSynchronize(s));
     it = h->plans_f.emplace(ncol, std::move(p)).first;
   }
   return *it->second;
@@ -493,7 +798,8 @@ static void h2_plan_run_t(const spdhss_h2_s* h, const H2PlanT<T>& p, cudaStream_
   p.up_leaf.launch(s);
   for (const auto& g : p.up) g.launch(s);
   SPD_CUDA(cudaMemsetAsync(p.yhat.p, 0, p.yhat.bytes(), s));
-  p.coupling.launch(s);
+  if (p.use_rowcoup) p.rowcoup.launch(s);
+  else p.coupling.launch(s);
   for (const auto& g : p.down) g.launch(s);
   p.leaf_out.launch(s);
   p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);

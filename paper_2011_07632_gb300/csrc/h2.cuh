@@ -10,6 +10,52 @@
 
 namespace spd {
 
+// FP32 couplings in destination-major form: node i owns one column-major k_i x (sum of its
+// far partners' ranks) matrix [B_ij1 B_ij2 ...], so the coupling step of the FP32 product
+// streams every entry exactly once and coalesced.  The columns are cut into chunks of at
+// most 64 that stay within one partner; the CTA of a node stages the x^_j pieces of a few
+// chunks in shared memory and each thread accumulates one row over its chunks.
+struct RowCoupProb {
+  float* C;          // y^_i (k_i x ncol, ld ldc)
+  int64_t ldc;
+  int M;             // k_i
+  int ncol;
+  const float* A;    // k_i x (sum k_j), ld k_i
+  int ch0, ch1;      // chunk range
+};
+struct RowCoupChunk {
+  const float* x;    // x^_j rows [kk0, kk0 + K) (ld ldx)
+  int64_t ldx;
+  int64_t col;       // first column of the chunk in A
+  int K;             // <= 64
+};
+// one CTA: rows [r0, r0 + 256) of problem p over chunks [ch0, ch1); part >= 0 writes a
+// partial tile (summed later in part order) instead of the output
+struct RowCoupWork {
+  int p, r0, ch0, ch1;
+  int64_t part;
+};
+struct RowCoupRed {
+  int p, r0;
+  int64_t part0;
+  int nparts;
+};
+struct RowCoupBatch {
+  std::vector<RowCoupProb> probs;
+  std::vector<RowCoupChunk> chunks;
+  std::vector<RowCoupWork> work;
+  std::vector<RowCoupRed> red;
+  DevBuf<RowCoupProb> d_probs;
+  DevBuf<RowCoupChunk> d_chunks;
+  DevBuf<RowCoupWork> d_work;
+  DevBuf<RowCoupRed> d_red;
+  DevBuf<float> partial;          // nparts x NC x 256
+  int ncol = 1;
+  double flops = 0.0, bytes = 0.0;
+  void upload(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+};
+
 // One H^2 product plan for a fixed number of columns: upward pass, Type-3 couplings,
 // downward pass, leaf bases and near field.  With nslot > 1 the product is split by the
 // HSS level of the lowest common ancestor of every block (slot l - 2 for level l), which
@@ -18,6 +64,8 @@ namespace spd {
 // FP32 kernel entries, FP32 accumulation).
 template <class T>
 struct H2PlanT {
+  RowCoupBatch rowcoup;   // FP32 plans: the coupling step (replaces `coupling`)
+  bool use_rowcoup = false;
   int ncol = 0;      // columns per slot
   int nslot = 1;
   DevBuf<T> xs, ys, xhat, yhat;   // sorted-order input/output, skeleton-space vectors
@@ -53,7 +101,9 @@ struct spdhss_h2_s {
   int max_rank = 0;
   std::map<int, std::unique_ptr<spd::H2Plan>> plans;   // by nrhs
   // FP32 copies of the generators for the mixed-precision products (made on first use)
-  spd::DevBuf<float> basis_f, coup_f;
+  spd::DevBuf<float> basis_f;
+  spd::DevBuf<float> coup_fd;                 // destination-major FP32 couplings
+  std::vector<int64_t> coup_fd_off;           // per node: offset of its coupling matrix
   std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
 
   int rank(int64_t i) const { return (int)(skel_off[i + 1] - skel_off[i]); }

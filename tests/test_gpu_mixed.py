@@ -41,3 +41,28 @@ def test_mixed_pcg_reaches_fp64_tolerance(nrhs):
     # the FP64 residual of the mixed solution, recomputed with the FP64 product
     r = b - h.matmul(x32).cpu().numpy()
     assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.01e-6)
+
+
+@pytest.mark.parametrize("nrhs", [3, 8, 16])
+def test_fp32_product_split_rows(nrhs):
+    """A size where high-rank nodes carry row tiles of more than 2^20 coupling entries (the
+    FP32 coupling step then splits them over several CTAs and adds the parts in order)."""
+    api = need_gpu()
+    n = 60000
+    X = inputs.uniform_cube(n, 3, 11)
+    h = api.H2(X, "gauss", 0.1, 1e-4, 128, 1e-8)
+    tr = h.export_tree()
+    off, _ = h.export_skeletons()
+    k = np.diff(off)
+    big = 0
+    for i in range(len(k)):
+        kt = sum(int(k[j]) for j in tr["far_idx"][tr["far_off"][i]:tr["far_off"][i + 1]])
+        big = max(big, min(int(k[i]), 256) * kt)
+    assert big > (1 << 20)
+    x = inputs.rhs(n, nrhs, 12)
+    y64 = h.matmul(x).cpu().numpy()
+    y32 = h.matmul_mixed(x).cpu().numpy()
+    # FP32 rounding against sums with ~1000 significant terms of both signs per row
+    assert rel(y32, y64) < 1e-4
+    # deterministic: a second product is bit-identical
+    assert np.array_equal(h.matmul_mixed(x).cpu().numpy(), y32)
