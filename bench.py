@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: this many Poisson-arriving mixed requests, served one at "
                          "a time and then concurrently; prints a serving JSON line")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="batched level sweep: this many independent instances built and solved "
+                         "with merged launches, then one at a time; prints a batching JSON line")
     ap.add_argument("--matvec-case", type=int, default=0,
                     help="profiling case: H2 of the Gaussian workload at this n, then 5 products "
                          "with 8 columns (prints timings, no benchmark line)")
@@ -471,8 +474,103 @@ def run_serve(count):
                       "dtype": "f64", "data": "synthetic"}))
 
 
+def batch_instances(count, seed=3):
+    """Independent instances: n = floor(exp(U[ln 2000, ln 32000])), 2D and 3D alternating,
+    kernels cycled over {exp, Gaussian ell=0.1, Matern-3/2 ell=0.1}, shift 1e-3, leaf 64,
+    H^2 tol 1e-8, rank 50, one N(0,1) right-hand side each."""
+    from paper_2011_07632_gb300 import inputs
+    sizes = inputs.log_uniform_sizes(count, 2000, 32000, seed)
+    kinds = [("exp", 1.0), ("gauss", 0.1), ("matern32", 0.1)]
+    out = []
+    for k in range(count):
+        kind, ell = kinds[k % 3]
+        dim = 2 if k % 2 == 0 else 3
+        n = int(sizes[k])
+        out.append(dict(points=inputs.uniform_cube(n, dim, 1000 + k), kernel=kind, ell=ell,
+                        shift=1e-3, leaf_size=64, tol=1e-8, rank=50, oversample=10, seed=k,
+                        rhs=inputs.rhs(n, 1, 5000 + k)))
+    return out
+
+
+def run_batch(count):
+    """Batched level sweep (spdhss_build_batched + pcg_solve_batched) against the same
+    instances built and solved one at a time on the same stream."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, native
+    insts = batch_instances(count)
+    dev = [dict(i, points=torch.from_numpy(i["points"]).cuda(),
+                rhs=torch.from_numpy(np.ascontiguousarray(i["rhs"])).cuda()) for i in insts]
+    torch.cuda.synchronize()
+
+    def batched(ins):
+        t0 = time.perf_counter()
+        built, st, stats = api.build_batched(ins)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        X, its, rrs, st2 = api.pcg_solve_batched([b[0] for b in built], [b[2] for b in built],
+                                                 [i["rhs"] for i in ins], tol=1e-6)
+        torch.cuda.synchronize()
+        return built, st, stats, X, its, st2, t1 - t0, time.perf_counter() - t1
+
+    def single(ins):
+        xs, its, tb, ts = [], [], 0.0, 0.0
+        for i in ins:
+            t0 = time.perf_counter()
+            h = api.H2(i["points"], i["kernel"], i["ell"], i["shift"], i["leaf_size"], i["tol"])
+            hs = api.HSS(h, i["rank"], i["oversample"], seed=i["seed"])
+            u = api.ULV(hs)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x, it, rr = api.pcg_solve(h, u, i["rhs"], tol=1e-6)
+            xs.append(x.cpu().numpy())
+            ts += time.perf_counter() - t1
+            tb += t1 - t0
+            its.append(int(it[0]))
+            u.close(); hs.close(); h.close()
+        torch.cuda.synchronize()
+        return xs, its, tb, ts
+
+    batched(dev[:4])                     # warm-up
+    single(dev[:2])
+    c0 = native.launch_count()
+    t0 = time.perf_counter()
+    built, st, stats, X, its_b, st2, tb_b, ts_b = batched(dev)
+    t_b = time.perf_counter() - t0
+    c1 = native.launch_count()
+    xb = [x.cpu().numpy() for x in X]
+    del built, X
+    torch.cuda.synchronize()
+    c2 = native.launch_count()
+    t0 = time.perf_counter()
+    xs, its_s, tb_s, ts_s = single(dev)
+    t_s = time.perf_counter() - t0
+    c3 = native.launch_count()
+    diff = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(xb, xs))
+    ib = [int(v[0]) for v in its_b]
+    print(json.dumps({
+        "metric": "SPD-HSS build+PCG solves/s over independent instances",
+        "workload": f"batch{count}_n2000-32000_mixed", "instances": count,
+        "batched": {"wall_s": t_b, "instances_per_s": count / t_b, "build_s": tb_b,
+                    "solve_s": ts_b, "gpu_launches": c1 - c0,
+                    "build_merged_launches": stats[0], "build_hand_overs": stats[1],
+                    "status_ok": sum(v == native.OK for v in st),
+                    "converged": sum(v == native.OK for v in st2)},
+        "one_at_a_time": {"wall_s": t_s, "instances_per_s": count / t_s, "build_s": tb_s,
+                          "solve_s": ts_s, "gpu_launches": c3 - c2},
+        "pcg_iters": {"batched_max": max(ib), "single_max": max(its_s),
+                      "max_abs_diff": max(abs(a - b) for a, b in zip(ib, its_s))},
+        "max_rel_diff_batched_vs_single": diff,
+        "n_total": int(sum(i["points"].shape[0] for i in insts)),
+        "dtype": "f64", "data": "synthetic"}))
+
+
 def main():
     args = parse()
+    if args.batch:
+        run_batch(args.batch)
+        return
     if args.serve:
         run_serve(args.serve)
         return

@@ -200,6 +200,44 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
                               int nrhs, int64_t ld, double relres_tol, int maxit, int* iters_out,
                               double* relres_out, void* stream);
 
+/* ---- batched level sweep over independent instances -----------------------------------
+ * The construction of Alg. 5.3 (with the H^2 build before it and the ULV factorization
+ * after it) proceeds level by level with the same steps for every matrix; for many
+ * independent matrices these calls run them together: one host thread per instance
+ * prepares that instance's descriptors, and every batched kernel launch (grouped GEMM,
+ * kernel tiles, proxy matrices, near field, Cholesky, TRSM, pivoted QR, reflectors,
+ * copies) takes the nodes of all instances at the same step, so the GPU sees one launch
+ * per step instead of one per step and instance.  Instances at different steps (other
+ * depths, other iteration counts) form separate launches; an instance that fails leaves
+ * the sweep without stopping the others.  Results agree with the one-instance calls up to
+ * floating-point summation order (kernel variants are chosen for the merged launch).
+ * All work runs on `stream`.  Arrays are HOST arrays of `count` entries.
+ *
+ * spdhss_build_batched: for instance i, h2_build(points[i], n[i], dim[i], kernel[i],
+ *   leaf_size[i], tol[i]) -> spdhss_build(rank[i], oversample[i], omega NULL, seed[i]) ->
+ *   ulv_factor.  points[i]: n[i] x dim[i] column-major, HOST or DEVICE.  Outputs: HOST
+ *   arrays of handles (NULL entry where that instance failed) and status[i] per instance
+ *   (may be NULL).  Returns OK when every instance succeeded, else the first failing
+ *   instance's status (spdhss_last_error names it).  The caller destroys the handles.
+ * pcg_solve_batched: pcg_solve for every instance (B[i], X[i]: n_i x nrhs[i], ld[i];
+ *   iters_out[i] / relres_out[i]: HOST arrays of nrhs[i] entries or NULL), the iterations
+ *   of all instances in lockstep (an instance leaves when it has converged).  status[i]
+ *   per instance (NO_CONVERGENCE for one that missed the tolerance). */
+spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
+                                   const int* dim, const spdhss_kernel_desc* kernel,
+                                   const int* leaf_size, const double* tol, const int* rank,
+                                   const int* oversample, const uint64_t* seed, void* stream,
+                                   h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
+                                   spdhss_status* status);
+spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                const double* const* B, double* const* X, const int* nrhs,
+                                const int64_t* ld, double relres_tol, int maxit,
+                                int* const* iters_out, double* const* relres_out, void* stream,
+                                spdhss_status* status);
+/* Launches issued by the last batched call of the calling thread: merged[0] = launches of
+ * the batched kernels after merging, merged[1] = the hand-overs they replaced. */
+void spdhss_batched_stats(int64_t* merged);
+
 /* ---- diagnostics ---------------------------------------------------------------------- */
 const char* spdhss_last_error(void);
 

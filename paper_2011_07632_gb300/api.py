@@ -218,3 +218,88 @@ def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=
     if st != N.OK and not (st == N.NO_CONVERGENCE and not raise_on_no_convergence):
         N.check(st)
     return Xc.t(), np.array(list(it)), np.array(list(rr))
+
+
+def _wrap(cls, handle, **attrs):
+    """A Python handle object around a library handle made by a batched call."""
+    o = cls.__new__(cls)
+    for k, v in attrs.items():
+        setattr(o, k, v)
+    o._h = ctypes.c_void_p(handle) if handle else None
+    return o
+
+
+def build_batched(instances, stream=None):
+    """Batched level sweep (spdhss_build_batched): H^2 -> SPD-HSS -> ULV for independent
+    instances, with the batched kernel launches of all instances merged step by step.
+
+    instances: list of dicts with keys points ((n, dim) array or tensor), kernel, ell,
+    shift, leaf_size, tol, rank, oversample (default 10), seed (default 0).
+    Returns (list of (H2, HSS, ULV) or None per instance, per-instance status codes,
+    (merged launches, hand-overs))."""
+    m = len(instances)
+    pts, keep = [], []
+    for inst in instances:
+        p = inst["points"]
+        if isinstance(p, np.ndarray):
+            p = torch.from_numpy(np.ascontiguousarray(p, dtype=np.float64))
+        p = p.to(torch.float64).contiguous()
+        keep.append(p)
+        pts.append(p)
+    ptr = (ctypes.c_void_p * m)(*[p.data_ptr() for p in pts])
+    n = np.array([p.shape[0] for p in pts], np.int64)
+    dim = (ctypes.c_int * m)(*[int(p.shape[1]) for p in pts])
+    kd = (N.KernelDesc * m)(*[N.KernelDesc(N.KERNELS[i["kernel"]], float(i["ell"]),
+                                            float(i["shift"])) for i in instances])
+    leaf = (ctypes.c_int * m)(*[int(i["leaf_size"]) for i in instances])
+    tol = (ctypes.c_double * m)(*[float(i["tol"]) for i in instances])
+    rank = (ctypes.c_int * m)(*[int(i["rank"]) for i in instances])
+    over = (ctypes.c_int * m)(*[int(i.get("oversample", 10)) for i in instances])
+    seed = (ctypes.c_uint64 * m)(*[int(i.get("seed", 0)) for i in instances])
+    h2o, hso, ulo = (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)()
+    st = (ctypes.c_int * m)()
+    rc = N.lib().spdhss_build_batched(m, ptr, _i64(n), dim, kd, leaf, tol, rank, over, seed,
+                                      _stream(stream), h2o, hso, ulo, st)
+    if rc != N.OK and all(v == N.OK for v in st):
+        N.check(rc)
+    out = []
+    for k, inst in enumerate(instances):
+        if st[k] != N.OK:
+            out.append(None)
+            continue
+        h = _wrap(H2, h2o[k], n=int(n[k]), dim=int(dim[k]), kernel=inst["kernel"],
+                  ell=float(inst["ell"]), shift=float(inst["shift"]),
+                  leaf_size=int(inst["leaf_size"]), tol=float(inst["tol"]))
+        hs = _wrap(HSS, hso[k], h2=h, rank=int(inst["rank"]),
+                   oversample=int(inst.get("oversample", 10)))
+        u = _wrap(ULV, ulo[k], hss=hs)
+        out.append((h, hs, u))
+    stats = np.zeros(2, np.int64)
+    N.lib().spdhss_batched_stats(_i64(stats))
+    return out, [int(v) for v in st], (int(stats[0]), int(stats[1]))
+
+
+def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, stream=None):
+    """pcg_solve for every instance with the iterations in lockstep (pcg_solve_batched).
+    Bs: device tensors or arrays (n_i, nrhs_i).  Returns (list of X (n_i, nrhs_i) device
+    tensors, list of iteration arrays, list of relres arrays, per-instance status codes)."""
+    m = len(h2s)
+    Bc = [_colmajor(b) for b in Bs]
+    Xc = [torch.empty_like(b) for b in Bc]
+    nrhs = [b.shape[0] for b in Bc]
+    its = [(ctypes.c_int * k)() for k in nrhs]
+    rrs = [(ctypes.c_double * k)() for k in nrhs]
+    P = ctypes.c_void_p * m
+    ld = np.array([h.n for h in h2s], np.int64)
+    st = (ctypes.c_int * m)()
+    rc = N.lib().pcg_solve_batched(
+        m, P(*[h._h.value for h in h2s]), P(*[u._h.value for u in ulvs]),
+        P(*[b.data_ptr() for b in Bc]), P(*[x.data_ptr() for x in Xc]),
+        (ctypes.c_int * m)(*nrhs), _i64(ld), float(tol), int(maxit),
+        P(*[ctypes.addressof(a) for a in its]), P(*[ctypes.addressof(a) for a in rrs]),
+        _stream(stream), st)
+    if any(v not in (N.OK, N.NO_CONVERGENCE) for v in st) or (
+            rc != N.OK and all(v == N.OK for v in st)):
+        N.check(rc)
+    return ([x.t() for x in Xc], [np.array(list(a)) for a in its],
+            [np.array(list(a)) for a in rrs], [int(v) for v in st])

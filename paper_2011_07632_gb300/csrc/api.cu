@@ -4,6 +4,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include "h2.cuh"
 
@@ -176,36 +177,48 @@ int64_t spdhss_profile_report(char* buf, int64_t len) {
   return (int64_t)out.size() + 1;
 }
 
+}  // extern "C"
+
+namespace spd {
+// the body of h2_build (also run per instance by spdhss_build_batched)
+static std::unique_ptr<spdhss_h2_s> h2_build_one(const double* points, int64_t n, int dim,
+                                                 spdhss_kernel_desc kernel, int leaf_size,
+                                                 double tol, cudaStream_t s) {
+  SPD_REQUIRE(points != nullptr, "points is NULL");
+  SPD_REQUIRE(n >= 1 && n < (1LL << 40), "n out of range");
+  SPD_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+  SPD_REQUIRE(leaf_size >= 1, "leaf_size must be >= 1");
+  SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
+  SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 3, "unknown kernel kind");
+  SPD_REQUIRE(kernel.ell > 0.0, "kernel length scale must be > 0");
+  SPD_REQUIRE(kernel.shift >= 0.0, "shift must be >= 0");
+  std::unique_ptr<spdhss_h2_s> h(new spdhss_h2_s());
+  h->kfn.kind = kernel.kind;
+  h->kfn.inv_ell = 1.0 / kernel.ell;
+  h->kfn.shift = kernel.shift;
+  h->tol = tol;
+  const double* dp = points;
+  DevBuf<double> staged;
+  if (!is_device_pointer(points)) {
+    staged.alloc((size_t)n * dim);
+    SPD_CUDA(cudaMemcpyAsync(staged.p, points, (size_t)n * dim * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    dp = staged.p;
+  }
+  h2_build_impl(h.get(), dp, n, dim, leaf_size, s);
+  return h;
+}
+}  // namespace spd
+
+extern "C" {
+
 spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
                        int leaf_size, double tol, void* stream, h2_handle* out) {
   return guarded("h2_build", [&] {
     StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
-    SPD_REQUIRE(points != nullptr, "points is NULL");
-    SPD_REQUIRE(n >= 1 && n < (1LL << 40), "n out of range");
-    SPD_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
-    SPD_REQUIRE(leaf_size >= 1, "leaf_size must be >= 1");
-    SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
-    SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 3, "unknown kernel kind");
-    SPD_REQUIRE(kernel.ell > 0.0, "kernel length scale must be > 0");
-    SPD_REQUIRE(kernel.shift >= 0.0, "shift must be >= 0");
-    cudaStream_t s = (cudaStream_t)stream;
-    std::unique_ptr<spdhss_h2_s> h(new spdhss_h2_s());
-    h->kfn.kind = kernel.kind;
-    h->kfn.inv_ell = 1.0 / kernel.ell;
-    h->kfn.shift = kernel.shift;
-    h->tol = tol;
-    const double* dp = points;
-    DevBuf<double> staged;
-    if (!is_device_pointer(points)) {
-      staged.alloc((size_t)n * dim);
-      SPD_CUDA(cudaMemcpyAsync(staged.p, points, (size_t)n * dim * sizeof(double),
-                               cudaMemcpyHostToDevice, s));
-      dp = staged.p;
-    }
-    h2_build_impl(h.get(), dp, n, dim, leaf_size, s);
-    *out = h.release();
+    *out = h2_build_one(points, n, dim, kernel, leaf_size, tol, (cudaStream_t)stream).release();
   });
 }
 
@@ -453,6 +466,136 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle u, const double* B, doubl
                   (cudaStream_t)stream, 1, 50);
     if (!conv) throw spd::Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
   });
+}
+
+}  // extern "C"
+
+// ---- batched level sweep ---------------------------------------------------------------
+
+namespace spd {
+
+static thread_local int64_t g_batched_stats[2] = {0, 0};
+
+// Runs f(i) for every instance on a host thread of its own, all on stream s, with the
+// batched launches of all instances merged (merge.cuh).  Collects each instance's status
+// and error message.
+template <class F>
+static void run_batched(int count, cudaStream_t s, std::vector<spdhss_status>& st,
+                        std::vector<std::string>& msg, F f) {
+  Merger M(s, count);
+  st.assign(count, SPDHSS_OK);
+  msg.assign(count, std::string());
+  int dev = 0;
+  SPD_CUDA(cudaGetDevice(&dev));
+  std::vector<std::thread> th;
+  th.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    th.emplace_back([&, i] {
+      MergeCtx& c = merge_ctx();
+      st[i] = guarded("instance", [&] {
+        SPD_CUDA(cudaSetDevice(dev));
+        c.m = &M;
+        c.instance = i;
+        c.bypass = false;
+        StreamScope ss(s);
+        f(i);
+      });
+      if (st[i] != SPDHSS_OK) msg[i] = g_last_error;
+      c.m = nullptr;
+      M.leave();
+    });
+  }
+  for (auto& t : th) t.join();
+  g_batched_stats[0] = M.launches();
+  g_batched_stats[1] = M.submissions();
+}
+
+static spdhss_status batched_result(const char* where, const std::vector<spdhss_status>& st,
+                                    const std::vector<std::string>& msg, spdhss_status* status) {
+  if (status)
+    for (size_t i = 0; i < st.size(); ++i) status[i] = st[i];
+  for (size_t i = 0; i < st.size(); ++i)
+    if (st[i] != SPDHSS_OK) {
+      set_last_error(std::string(where) + ": instance " + std::to_string(i) + ": " + msg[i]);
+      return st[i];
+    }
+  return SPDHSS_OK;
+}
+
+}  // namespace spd
+
+extern "C" {
+
+spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
+                                   const int* dim, const spdhss_kernel_desc* kernel,
+                                   const int* leaf_size, const double* tol, const int* rank,
+                                   const int* oversample, const uint64_t* seed, void* stream,
+                                   h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
+                                   spdhss_status* status) {
+  std::vector<spdhss_status> st;
+  std::vector<std::string> msg;
+  cudaStream_t s = (cudaStream_t)stream;
+  const spdhss_status outer = guarded("spdhss_build_batched", [&] {
+    SPD_REQUIRE(count >= 1, "count must be >= 1");
+    SPD_REQUIRE(points && n && dim && kernel && leaf_size && tol && rank && oversample && seed,
+                "NULL argument");
+    SPD_REQUIRE(h2_out && hss_out && ulv_out, "NULL output array");
+    for (int i = 0; i < count; ++i) {
+      h2_out[i] = nullptr;
+      hss_out[i] = nullptr;
+      ulv_out[i] = nullptr;
+    }
+    run_batched(count, s, st, msg, [&](int i) {
+      SPD_REQUIRE(rank[i] >= 1, "rank must be >= 1");
+      SPD_REQUIRE(oversample[i] >= 0, "oversample must be >= 0");
+      std::unique_ptr<spdhss_h2_s> h =
+          h2_build_one(points[i], n[i], dim[i], kernel[i], leaf_size[i], tol[i], s);
+      std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
+      spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], nullptr, seed[i], s);
+      std::unique_ptr<spdhss_ulv_s> u(new spdhss_ulv_s());
+      ulv_factor_impl(u.get(), hs.get(), s);
+      ulv_out[i] = u.release();
+      hss_out[i] = hs.release();
+      h2_out[i] = h.release();
+    });
+  });
+  if (outer != SPDHSS_OK) return outer;
+  return batched_result("spdhss_build_batched", st, msg, status);
+}
+
+spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                const double* const* B, double* const* X, const int* nrhs,
+                                const int64_t* ld, double relres_tol, int maxit,
+                                int* const* iters_out, double* const* relres_out, void* stream,
+                                spdhss_status* status) {
+  std::vector<spdhss_status> st;
+  std::vector<std::string> msg;
+  cudaStream_t s = (cudaStream_t)stream;
+  const spdhss_status outer = guarded("pcg_solve_batched", [&] {
+    SPD_REQUIRE(count >= 1, "count must be >= 1");
+    SPD_REQUIRE(h2 && ulv && B && X && nrhs && ld, "NULL argument");
+    SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
+    SPD_REQUIRE(maxit >= 1, "maxit must be >= 1");
+    run_batched(count, s, st, msg, [&](int i) {
+      SPD_REQUIRE(h2[i] && ulv[i] && B[i] && X[i], "NULL argument");
+      SPD_REQUIRE(ulv[i]->hs->h2 == h2[i], "the ULV factorization belongs to another H2 matrix");
+      SPD_REQUIRE(nrhs[i] >= 1, "nrhs must be >= 1");
+      SPD_REQUIRE(ld[i] >= h2[i]->th.n, "ld must be >= n");
+      bool conv = false;
+      pcg_impl(h2[i], ulv[i], B[i], X[i], nrhs[i], ld[i], relres_tol, maxit,
+               iters_out ? iters_out[i] : nullptr, relres_out ? relres_out[i] : nullptr, conv, s);
+      if (!conv) throw Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
+    });
+  });
+  if (outer != SPDHSS_OK) return outer;
+  return batched_result("pcg_solve_batched", st, msg, status);
+}
+
+void spdhss_batched_stats(int64_t* merged) {
+  if (merged) {
+    merged[0] = g_batched_stats[0];
+    merged[1] = g_batched_stats[1];
+  }
 }
 
 }  // extern "C"

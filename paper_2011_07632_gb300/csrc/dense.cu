@@ -281,8 +281,41 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
   d_tiles.upload(tiles, s);
 }
 
+// grouped GEMMs of several instances: segments re-based, one upload, one launch
+template <class T>
+struct DeferredGemm : Deferred {
+  std::vector<GemmSegT<T>> segs;
+  std::vector<GemmProbT<T>> probs;
+  const char* tag = "gemm";
+  void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
+    GemmBatchT<T> m;
+    m.tag = tag;
+    for (Deferred* d : group) {
+      const auto* x = static_cast<const DeferredGemm<T>*>(d);
+      const int off = (int)m.segs.size();
+      m.segs.insert(m.segs.end(), x->segs.begin(), x->segs.end());
+      for (GemmProbT<T> p : x->probs) {
+        p.seg0 += off;
+        p.seg1 += off;
+        m.probs.push_back(p);
+      }
+    }
+    m.upload(s);
+    m.launch(s);
+  }
+};
+
 template <class T>
 void GemmBatchT<T>::launch(cudaStream_t s) const {
+  if (merging()) {
+    if (probs.empty()) { merge_skip(); return; }
+    std::unique_ptr<DeferredGemm<T>> d(new DeferredGemm<T>());
+    d->segs = segs;
+    d->probs = probs;
+    d->tag = tag;
+    merge_ctx().m->submit(sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", std::move(d));
+    return;
+  }
   const int64_t nt = (int64_t)tiles.size();
   if (nt == 0) return;
   ProfScope ps(tag, s, flops, bytes);
@@ -314,7 +347,7 @@ __global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ pro
       const double d = A[j + j * ld];
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = 1;
-        if (atomicCAS(info, 0, P.tag + 1) == 0) info[1] = j;
+        if (atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = j;
       }
       s_d = sqrt(d);
     }
@@ -363,7 +396,7 @@ __global__ void __launch_bounds__(256) k_potrf_blk(const PotrfProb* __restrict__
         if (lane == 0) {
           const double d = dk[j][j];
           if (!(d > 0.0) || !isfinite(d)) {
-            if (!s_fail && atomicCAS(info, 0, P.tag + 1) == 0) info[1] = k0 + j;
+            if (!s_fail && atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = k0 + j;
             s_fail = 1;
             dk[j][j] = 1.0;
           } else {
@@ -443,7 +476,21 @@ __global__ void __launch_bounds__(256) k_potrf_blk(const PotrfProb* __restrict__
 }
 
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    std::vector<PotrfProb> h = b.h;
+    for (auto& p : h)
+      if (!p.info) p.info = d_info;
+    const char* tag = b.tag;
+    defer_launch("potrf", h, [tag](std::vector<PotrfProb>& all, cudaStream_t st) {
+      Batch<PotrfProb> m;
+      m.h = std::move(all);
+      m.tag = tag;
+      m.upload(st);
+      potrf_launch(m, nullptr, st);
+    });
+    return;
+  }
   double f = 0.0;
   for (const auto& p : b.h) f += (double)p.n * p.n * p.n / 3.0;
   ProfScope ps(b.tag ? b.tag : "potrf", s, f);
@@ -637,7 +684,18 @@ void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
 }
 
 void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    const char* tag = b.tag;
+    defer_launch("trsm", b.h, [tag](std::vector<TrsmProb>& all, cudaStream_t st) {
+      Batch<TrsmProb> m;
+      m.h = std::move(all);
+      m.tag = tag;
+      m.upload(st);
+      trsm_launch(m, st);
+    });
+    return;
+  }
   double f = 0.0;
   for (const auto& p : b.h) f += (double)p.n * p.n * p.ncol;
   if (b.nwork >= 0) {
@@ -835,8 +893,38 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
   cl.sync();
 }
 
+// pivoted QRs of several instances: the largest cluster and row count of the group
+struct DeferredQr : Deferred {
+  std::vector<QrProb> h;
+  int pivot = 1, cluster = 1, max_m = 1;
+  const char* tag = nullptr;
+  void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
+    Batch<QrProb> m;
+    m.tag = tag;
+    int cl = 1, mm = 1;
+    for (Deferred* d : group) {
+      const auto* x = static_cast<const DeferredQr*>(d);
+      m.h.insert(m.h.end(), x->h.begin(), x->h.end());
+      cl = std::max(cl, x->cluster);
+      mm = std::max(mm, x->max_m);
+    }
+    m.upload(s);
+    geqp3_launch(m, pivot, cl, mm, s);
+  }
+};
+
 int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s) {
-  if (b.empty()) return -1;
+  if (b.empty()) { merge_skip(); return -1; }
+  if (merging()) {
+    std::unique_ptr<DeferredQr> d(new DeferredQr());
+    d->h = b.h;
+    d->pivot = pivot;
+    d->cluster = cluster;
+    d->max_m = max_m;
+    d->tag = b.tag;
+    merge_ctx().m->submit(pivot ? "geqp3" : "geqrf", std::move(d));
+    return -1;
+  }
   cluster = std::max(1, std::min(cluster, 8));
   const size_t smem = (size_t)std::max(1, max_m) * sizeof(double);
   SPD_REQUIRE(smem <= 200 * 1024, "geqp3: matrix too tall for the shared-memory reflector");
@@ -906,7 +994,19 @@ void householder_prepare(Batch<HhApplyProb>& b, cudaStream_t s) {
 }
 
 void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    const char* tag = b.tag;
+    defer_launch(trans ? "householder_t" : "householder_n", b.h,
+                 [tag, trans](std::vector<HhApplyProb>& all, cudaStream_t st) {
+                   Batch<HhApplyProb> m;
+                   m.h = std::move(all);
+                   m.tag = tag;
+                   m.upload(st);
+                   householder_launch(m, trans, st);
+                 });
+    return;
+  }
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
     ProfScope ps(b.tag ? b.tag : "householder", s);
@@ -953,7 +1053,18 @@ __global__ void __launch_bounds__(256) k_form_q(const FormQProb* __restrict__ pr
 }
 
 void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    const char* tag = b.tag;
+    defer_launch("form_q", b.h, [tag](std::vector<FormQProb>& all, cudaStream_t st) {
+      Batch<FormQProb> m;
+      m.h = std::move(all);
+      m.tag = tag;
+      m.upload(st);
+      form_q_launch(m, st);
+    });
+    return;
+  }
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
     for (int c = 0; c < b.h[p].kcols; ++c) work.push_back(make_int2(p, c));
@@ -980,6 +1091,7 @@ __global__ void k_copy(const CopyProb* __restrict__ probs, int ident) {
     const int i = (int)(e % P.m), j = (int)(e / P.m);
     double v;
     if (ident) v = (i == j) ? 1.0 : 0.0;
+    else if (!P.src) v = 0.0;
     else v = P.alpha * (P.trans ? P.src[j + (int64_t)i * P.lds] : P.src[i + (int64_t)j * P.lds]);
     double* d = P.dst + i + (int64_t)j * P.ldd;
     if (P.accumulate) *d += v; else *d = v;
@@ -987,7 +1099,19 @@ __global__ void k_copy(const CopyProb* __restrict__ probs, int ident) {
 }
 
 static void copy_common(const Batch<CopyProb>& b, int ident, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    const char* tag = b.tag;
+    defer_launch(ident ? "identity" : "copy", b.h,
+                 [tag, ident](std::vector<CopyProb>& all, cudaStream_t st) {
+                   Batch<CopyProb> m;
+                   m.h = std::move(all);
+                   m.tag = tag;
+                   m.upload(st);
+                   copy_common(m, ident, st);
+                 });
+    return;
+  }
   ProfScope ps(b.tag ? b.tag : "copy", s);
   int64_t mx = 1;
   for (const auto& p : b.h) mx = std::max<int64_t>(mx, (int64_t)p.m * p.n);
@@ -1001,6 +1125,22 @@ static void copy_common(const Batch<CopyProb>& b, int ident, cudaStream_t s) {
 
 void copy_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 0, s); }
 void identity_launch(const Batch<CopyProb>& b, cudaStream_t s) { copy_common(b, 1, s); }
+
+void copy_vec(double* dst, const double* src, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  if (merging()) {
+    Batch<CopyProb> b;
+    CopyProb c;
+    c.src = src; c.lds = count; c.dst = dst; c.ldd = count;
+    c.m = (int)count; c.n = 1; c.trans = 0; c.accumulate = 0; c.alpha = 1.0;
+    SPD_REQUIRE(count < (int64_t(1) << 31), "copy_vec: vector too long to merge");
+    b.h.push_back(c);
+    copy_launch(b, s);
+    return;
+  }
+  if (src) SPD_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else SPD_CUDA(cudaMemsetAsync(dst, 0, count * sizeof(double), s));
+}
 
 }  // namespace spd
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "merge.cuh"
 
 namespace spd {
 
@@ -92,6 +93,7 @@ struct PotrfProb {
   int64_t lda;
   int n;
   int tag;   // reported in the failure record
+  int* info = nullptr;   // failure record of this matrix (null: the launch's d_info)
 };
 // info[0] receives tag+1 of a failing matrix (0 if all succeed); info[1] the failing column.
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s);
@@ -163,13 +165,16 @@ struct CopyProb {
   double* dst;
   int64_t ldd;
   int m, n;
-  int trans;        // 1: dst(i,j) = src(j,i)
+  int trans;        // 1: dst(i,j) = src(j,i)   (src null: zeros)
   int accumulate;   // 1: dst += ...
   double alpha;
 };
 void copy_launch(const Batch<CopyProb>& b, cudaStream_t s);
 // dst(0:m, 0:m) = I for every entry (src unused)
 void identity_launch(const Batch<CopyProb>& b, cudaStream_t s);
+// dst[0:count) = src[0:count) (src null: zeros), device vectors; merged like the batched
+// copies when the calling thread runs an instance of a batched sweep
+void copy_vec(double* dst, const double* src, int64_t count, cudaStream_t s);
 
 // one-shot helpers: upload and launch (descriptors freed when the call returns)
 template <class P, class F>

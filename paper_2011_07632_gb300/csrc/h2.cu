@@ -7,6 +7,7 @@
 // matrix and the first k pivots are the skeleton.  Couplings B_ij = K(X_skel_i, X_skel_j)
 // for the Type-3 pairs (Sec. 5.2.2) are stored once per unordered pair.
 #include <algorithm>
+#include <type_traits>
 
 #include "h2.cuh"
 
@@ -96,6 +97,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
   std::vector<double*> Uptr(NN, nullptr);
 
   for (int t = D; t >= 1; --t) {
+    merge_stage(1, D - t);   // batched sweeps align the levels by height above the leaves
     const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
     // candidate rows
     for (int64_t k = 0; k < nn; ++k) {
@@ -251,6 +253,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
   }
 
   // global skeleton arrays (node-major) and bases
+  merge_stage(2, 0);
   h->skel_off.assign(NN + 1, 0);
   h->skel_idx.clear();
   h->U_rows.assign(NN, 0);
@@ -268,11 +271,18 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
   int64_t btot = 0;
   for (int64_t i = 0; i < NN; ++i) { h->U_off[i] = btot; btot += (int64_t)mrows[i] * rank[i]; }
   h->basis.alloc(std::max<int64_t>(btot, 1));
-  for (int64_t i = 0; i < NN; ++i)
-    if ((int64_t)mrows[i] * rank[i] > 0)
-      SPD_CUDA(cudaMemcpyAsync(h->basis.p + h->U_off[i], Uptr[i],
-                               (size_t)mrows[i] * rank[i] * sizeof(double),
-                               cudaMemcpyDeviceToDevice, s));
+  {
+    Batch<CopyProb> cb;
+    for (int64_t i = 0; i < NN; ++i)
+      if ((int64_t)mrows[i] * rank[i] > 0) {
+        CopyProb c;
+        c.src = Uptr[i]; c.lds = mrows[i]; c.dst = h->basis.p + h->U_off[i]; c.ldd = mrows[i];
+        c.m = mrows[i]; c.n = rank[i]; c.trans = 0; c.accumulate = 0; c.alpha = 1.0;
+        cb.push(c);
+      }
+    cb.upload(s);
+    copy_launch(cb, s);
+  }
   SPD_CUDA(cudaStreamSynchronize(s));
   upool.clear();
   const int64_t K = h->Ktot;
@@ -797,7 +807,8 @@ template <class T>
 static void h2_plan_run_t(const spdhss_h2_s* h, const H2PlanT<T>& p, cudaStream_t s) {
   p.up_leaf.launch(s);
   for (const auto& g : p.up) g.launch(s);
-  SPD_CUDA(cudaMemsetAsync(p.yhat.p, 0, p.yhat.bytes(), s));
+  if constexpr (std::is_same<T, double>::value) copy_vec(p.yhat.p, nullptr, (int64_t)p.yhat.n, s);
+  else SPD_CUDA(cudaMemsetAsync(p.yhat.p, 0, p.yhat.bytes(), s));
   if (p.use_rowcoup) p.rowcoup.launch(s);
   else p.coupling.launch(s);
   for (const auto& g : p.down) g.launch(s);

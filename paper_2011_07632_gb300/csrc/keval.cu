@@ -10,10 +10,12 @@ namespace spd {
 // dense tiles, 32 x 32 per CTA
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_tiles(const TileProb* __restrict__ probs,
-                                               const int4* __restrict__ work, KernelFn kf,
-                                               int dim) {
+                                               const int4* __restrict__ work, KernelFn kf_,
+                                               int dim_) {
   const int4 w = work[blockIdx.x];
   const TileProb P = probs[w.x];
+  const KernelFn kf = P.dim ? P.kf : kf_;
+  const int dim = P.dim ? P.dim : dim_;
   const int i0 = w.y, j0 = w.z;
   for (int e = threadIdx.x; e < 32 * 32; e += 256) {
     const int i = i0 + (e & 31), j = j0 + (e >> 5);
@@ -31,7 +33,19 @@ __global__ void __launch_bounds__(256) k_tiles(const TileProb* __restrict__ prob
 }
 
 void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStream_t s) {
-  if (b.empty()) return;
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    std::vector<TileProb> h = b.h;
+    for (auto& p : h)
+      if (!p.dim) { p.kf = k; p.dim = dim; }
+    defer_launch("tile", h, [](std::vector<TileProb>& all, cudaStream_t st) {
+      Batch<TileProb> m;
+      m.h = std::move(all);
+      m.upload(st);
+      tile_launch(m, KernelFn{}, 0, st);
+    });
+    return;
+  }
   std::vector<int4> work;
   for (int p = 0; p < (int)b.size(); ++p)
     for (int i0 = 0; i0 < b.h[p].rows; i0 += 32)
@@ -79,10 +93,12 @@ __device__ __forceinline__ void proxy_point(const ProxyProb& P, int dim, int r, 
 }
 
 __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ probs,
-                                               const int4* __restrict__ work, KernelFn kf,
-                                               int dim) {
+                                               const int4* __restrict__ work, KernelFn kf_,
+                                               int dim_) {
   const int4 w = work[blockIdx.x];
   const ProxyProb P = probs[w.x];
+  const KernelFn kf = P.dim ? P.kf : kf_;
+  const int dim = P.dim ? P.dim : dim_;
   const int np = proxy_count(dim);
   const int i0 = w.y, j0 = w.z;
   __shared__ double sy[3][64];
@@ -107,11 +123,22 @@ __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ pro
 }
 
 void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s) {
-  if (b.empty()) return;
-  const int np = proxy_count(dim);
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    std::vector<ProxyProb> h = b.h;
+    for (auto& p : h)
+      if (!p.dim) { p.kf = k; p.dim = dim; }
+    defer_launch("proxy", h, [](std::vector<ProxyProb>& all, cudaStream_t st) {
+      Batch<ProxyProb> m;
+      m.h = std::move(all);
+      m.upload(st);
+      proxy_launch(m, KernelFn{}, 0, st);
+    });
+    return;
+  }
   std::vector<int4> work;
   for (int p = 0; p < (int)b.size(); ++p)
-    for (int i0 = 0; i0 < np; i0 += 64)
+    for (int i0 = 0, np = proxy_count(b.h[p].dim ? b.h[p].dim : dim); i0 < np; i0 += 64)
       for (int j0 = 0; j0 < b.h[p].cols; j0 += 32) work.push_back(make_int4(p, i0, j0, 0));
   if (work.empty()) return;
   DevBuf<int4> dw;
@@ -133,9 +160,9 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 template <class T, int NC, int KIND>
 __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restrict__ probs,
                                                     const NearSegT<T>* __restrict__ segs,
-                                                    const int2* __restrict__ work, KernelFn kf,
-                                                    const double* __restrict__ xs, int64_t ldx,
-                                                    int dim) {
+                                                    const int2* __restrict__ work, KernelFn kf_,
+                                                    const double* __restrict__ xs_, int64_t ldx_,
+                                                    int dim_) {
   // source points staged per chunk; the staging area is reused for the final reduction
   constexpr int CH = NC >= 16 ? 192 : (NC >= 8 ? 256 : 512);
   constexpr int STAGE = CH * (3 + NC);
@@ -146,6 +173,12 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restri
   T (*sv)[CH] = reinterpret_cast<T (*)[CH]>(smem + 3 * CH);
   const int2 w = work[blockIdx.x];
   const NearProbT<T> P = probs[w.x];
+  const bool own = P.xs != nullptr;
+  const double* __restrict__ xs = own ? P.xs : xs_;
+  const int64_t ldx = own ? P.ldx : ldx_;
+  const int dim = own ? P.dim : dim_;
+  KernelFn kf = kf_;
+  if (own) { kf.inv_ell = P.inv_ell; kf.shift = P.shift; }
   const int col0 = w.y;
   const int ncb = min(NC, P.ncol - col0);
   const T inv_ell = (T)kf.inv_ell;
@@ -315,15 +348,21 @@ __device__ __forceinline__ void near_pairs(const NearProb& P, const NearSeg* __r
 template <int KIND>
 __global__ void __launch_bounds__(256) k_near_pairs(const NearProb* __restrict__ probs,
                                                     const NearSeg* __restrict__ segs,
-                                                    const int2* __restrict__ work, KernelFn kf,
-                                                    const double* __restrict__ xs, int64_t ldx,
-                                                    int dim) {
+                                                    const int2* __restrict__ work, KernelFn kf_,
+                                                    const double* __restrict__ xs_, int64_t ldx_,
+                                                    int dim_) {
   __shared__ double Kt[32][33];
   __shared__ double Xt[32][65];
   __shared__ double rx[3][32];
   __shared__ double cx[3][32];
   const int2 w = work[blockIdx.x];
   const NearProb P = probs[w.x];
+  const bool own = P.xs != nullptr;
+  const double* __restrict__ xs = own ? P.xs : xs_;
+  const int64_t ldx = own ? P.ldx : ldx_;
+  const int dim = own ? P.dim : dim_;
+  KernelFn kf = kf_;
+  if (own) { kf.inv_ell = P.inv_ell; kf.shift = P.shift; }
   const int col0 = w.y;
   const int ncb = min(64, P.ncol - col0);
   for (int rb = 0; rb < P.rows; rb += 32) {
@@ -430,9 +469,50 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   }
 }
 
+// near-field problems of several instances (same kernel kind): every problem carries its
+// own points and kernel parameters
+template <class T>
+struct DeferredNear : Deferred {
+  std::vector<NearProbT<T>> probs;
+  std::vector<NearSegT<T>> segs;
+  const char* tag = "near";
+  int kind = 0;
+  void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
+    NearBatchT<T> m;
+    m.tag = tag;
+    for (Deferred* d : group) {
+      const auto* x = static_cast<const DeferredNear<T>*>(d);
+      const int off = (int)m.segs.size();
+      m.segs.insert(m.segs.end(), x->segs.begin(), x->segs.end());
+      for (NearProbT<T> p : x->probs) {
+        p.seg0 += off;
+        p.seg1 += off;
+        m.probs.push_back(p);
+      }
+    }
+    KernelFn k{};
+    k.kind = kind;
+    m.upload(s);
+    m.launch(k, nullptr, 0, 0, s);
+  }
+};
+
 template <class T>
 void NearBatchT<T>::launch(const KernelFn& k, const double* xs, int64_t ldx, int dim,
                            cudaStream_t s) const {
+  if (merging()) {
+    if (probs.empty()) { merge_skip(); return; }
+    std::unique_ptr<DeferredNear<T>> d(new DeferredNear<T>());
+    d->probs = probs;
+    for (auto& p : d->probs)
+      if (!p.xs) { p.xs = xs; p.ldx = ldx; p.dim = dim; p.inv_ell = k.inv_ell; p.shift = k.shift; }
+    d->segs = segs;
+    d->tag = tag;
+    d->kind = k.kind;
+    merge_ctx().m->submit(std::string(sizeof(T) == 8 ? "near_f64_" : "near_f32_") +
+                              std::to_string(k.kind), std::move(d));
+    return;
+  }
   if (work.empty()) return;
   ProfScope ps(tag, s, flops, 8.0 * evals);
   const unsigned g = (unsigned)work.size();

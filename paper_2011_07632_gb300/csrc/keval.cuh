@@ -4,6 +4,7 @@
 #pragma once
 
 #include "dense.cuh"
+#include "merge.cuh"
 
 namespace spd {
 
@@ -18,6 +19,8 @@ struct TileProb {
   double* out;
   int64_t ldo;
   double diag_add;   // added where r0 + i == c0 + j and xr == xc (self block)
+  KernelFn kf{};     // kernel and dimension of this problem (dim 0: the launch's)
+  int dim = 0;
 };
 void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStream_t s);
 
@@ -38,6 +41,8 @@ struct ProxyProb {
   int cols;
   double* out;     // proxy_count(dim) x cols, column-major
   int64_t ldo;
+  KernelFn kf{};   // kernel and dimension of this problem (dim 0: the launch's)
+  int dim = 0;
 };
 void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s);
 
@@ -56,6 +61,12 @@ struct NearProbT {
   int ncol;
   int seg0, seg1;
   int beta;
+  // points, dimension and kernel parameters of this problem (xs null: the launch's); set
+  // when the problems of several instances share one launch
+  const double* xs = nullptr;
+  int64_t ldx = 0;
+  int dim = 0;
+  double inv_ell = 0.0, shift = 0.0;
 };
 template <class T>
 struct NearSegT {

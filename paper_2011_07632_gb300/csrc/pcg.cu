@@ -45,8 +45,74 @@ __global__ void k_dot_final(const double* __restrict__ part, int nb, double* __r
   out[c] = t;
 }
 
+// the same dot products for the vectors of several instances in one launch: work item =
+// (problem, column); the partition of every column and the summation order are those of
+// k_dot_partial / k_dot_final
+struct DotProb {
+  const double* a;
+  const double* b;
+  int64_t n;
+  int ncol;
+  double* part;
+  double* out;
+};
+
+__global__ void __launch_bounds__(256) k_dot_partial_b(const DotProb* __restrict__ probs,
+                                                       const int2* __restrict__ work) {
+  const int2 w = work[blockIdx.y];
+  const DotProb P = probs[w.x];
+  const int c = w.y;
+  const double* x = P.a + (int64_t)c * P.n;
+  const double* y = P.b + (int64_t)c * P.n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < 8; ++w2) t += ws[w2];
+    P.part[c * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dot_final_b(const DotProb* __restrict__ probs, const int2* __restrict__ work,
+                              int nwork) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nwork) return;
+  const int2 w = work[k];
+  const DotProb P = probs[w.x];
+  double t = 0.0;
+  for (int b = 0; b < DOT_BLOCKS; ++b) t += P.part[w.y * DOT_BLOCKS + b];
+  P.out[w.y] = t;
+}
+
+static void dots_merged(std::vector<DotProb>& all, cudaStream_t s) {
+  std::vector<int2> work;
+  for (int p = 0; p < (int)all.size(); ++p)
+    for (int c = 0; c < all[p].ncol; ++c) work.push_back(make_int2(p, c));
+  if (work.empty()) return;
+  DevBuf<DotProb> dp;
+  DevBuf<int2> dw;
+  dp.upload(all, s);
+  dw.upload(work, s);
+  for (size_t w0 = 0; w0 < work.size(); w0 += 65535) {
+    const unsigned gy = (unsigned)std::min<size_t>(65535, work.size() - w0);
+    k_dot_partial_b<<<dim3(DOT_BLOCKS, gy), 256, 0, s>>>(dp.p, dw.p + w0);
+    SPD_LAUNCHED();
+  }
+  k_dot_final_b<<<ceil_div((int64_t)work.size(), 128), 128, 0, s>>>(dp.p, dw.p, (int)work.size());
+  SPD_LAUNCHED();
+}
+
 static void dots(const double* a, const double* b, int64_t n, int ncol, double* part, double* out,
                  cudaStream_t s) {
+  if (defer_launch("dots", std::vector<DotProb>{DotProb{a, b, n, ncol, part, out}}, dots_merged))
+    return;
   k_dot_partial<<<dim3(DOT_BLOCKS, ncol), 256, 0, s>>>(a, b, n, part);
   SPD_LAUNCHED();
   k_dot_final<<<ceil_div(ncol, 128), 128, 0, s>>>(part, DOT_BLOCKS, out, ncol);
@@ -84,6 +150,84 @@ __global__ void k_sub(const double* __restrict__ b, const double* __restrict__ a
                       double* __restrict__ out, int64_t count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < count) out[e] = b[e] - ax[e];
+}
+
+// The vector updates of several instances in one launch (blockIdx.y = instance).
+struct VecProb {
+  int op;                // 0: x, r update (k_axpy_xr); 1: p update (k_update_p); 2: out = b - ax
+  double* x;             // x | p | out
+  double* r;             // r | - | -
+  const double* p;       // p | z | b
+  const double* q;       // q | - | ax
+  int64_t n;
+  int ncol;
+  const double* s1;      // rz | rzn
+  const double* s2;      // pq | rz
+  const int* done;
+};
+
+__global__ void __launch_bounds__(256) k_vec_b(const VecProb* __restrict__ probs) {
+  const VecProb P = probs[blockIdx.y];
+  const int64_t tot = P.n * P.ncol;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (P.op == 2) {
+      P.x[e] = P.p[e] - P.q[e];
+      continue;
+    }
+    const int c = (int)(e / P.n);
+    if (P.done[c] == 1) continue;
+    if (P.op == 0) {
+      const double alpha = P.s2[c] != 0.0 ? P.s1[c] / P.s2[c] : 0.0;
+      P.x[e] += alpha * P.p[e];
+      P.r[e] -= alpha * P.q[e];
+    } else {
+      const double beta = (P.done[c] == 0 && P.s2[c] != 0.0) ? P.s1[c] / P.s2[c] : 0.0;
+      P.x[e] = P.p[e] + beta * P.x[e];
+    }
+  }
+}
+
+static void vec_merged(std::vector<VecProb>& all, cudaStream_t s) {
+  int64_t mx = 1;
+  for (const auto& p : all) mx = std::max<int64_t>(mx, p.n * p.ncol);
+  DevBuf<VecProb> dp;
+  dp.upload(all, s);
+  const unsigned gx = (unsigned)std::min<int64_t>(ceil_div(mx, 256), 128);
+  for (size_t y0 = 0; y0 < all.size(); y0 += 65535) {
+    const unsigned gy = (unsigned)std::min<size_t>(65535, all.size() - y0);
+    k_vec_b<<<dim3(gx, gy), 256, 0, s>>>(dp.p + y0);
+    SPD_LAUNCHED();
+  }
+}
+
+static void axpy_xr(double* x, double* r, const double* p, const double* q, int64_t n, int ncol,
+                    const double* rz, const double* pq, const int* done, cudaStream_t s) {
+  if (defer_launch("vec_axpy", std::vector<VecProb>{VecProb{0, x, r, p, q, n, ncol, rz, pq, done}},
+                   vec_merged))
+    return;
+  k_axpy_xr<<<ceil_div(n * ncol, 256), 256, 0, s>>>(x, r, p, q, n, ncol, rz, pq, done);
+  SPD_LAUNCHED();
+}
+
+static void update_p(double* p, const double* z, int64_t n, int ncol, const double* rzn,
+                     const double* rz, const int* done, cudaStream_t s) {
+  if (defer_launch("vec_update",
+                   std::vector<VecProb>{VecProb{1, p, nullptr, z, nullptr, n, ncol, rzn, rz, done}},
+                   vec_merged))
+    return;
+  k_update_p<<<ceil_div(n * ncol, 256), 256, 0, s>>>(p, z, n, ncol, rzn, rz, done);
+  SPD_LAUNCHED();
+}
+
+static void sub(const double* b, const double* ax, double* out, int64_t count, cudaStream_t s) {
+  if (defer_launch("vec_sub",
+                   std::vector<VecProb>{VecProb{2, out, nullptr, b, ax, count, 1, nullptr, nullptr,
+                                                nullptr}},
+                   vec_merged))
+    return;
+  k_sub<<<ceil_div(count, 256), 256, 0, s>>>(b, ax, out, count);
+  SPD_LAUNCHED();
 }
 
 // precision = 0: FP64 throughout.  precision = 1: the product with A inside the iteration
@@ -131,10 +275,10 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   } else {
     permute_to_sorted(B, ld, bs.p, n, nrhs, perm, s);
   }
-  const unsigned gb = (unsigned)ceil_div(nc, 256);
   x.zero(s);
   done.zero(s);
-  SPD_CUDA(cudaMemcpyAsync(r.p, bs.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  merge_stage(10, 0);
+  copy_vec(r.p, bs.p, nc, s);
   std::vector<double> bn(nrhs);
   dots(bs.p, bs.p, n, nrhs, part.p, rr, s);
   {
@@ -146,16 +290,15 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   std::vector<int> hdone(nrhs, 0), hit(nrhs, 0);
   for (int c = 0; c < nrhs; ++c) hdone[c] = 0;
   // z = M^{-1} r, p = z, rz = r.z
-  SPD_CUDA(cudaMemcpyAsync(z, r.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  copy_vec(z, r.p, nc, s);
   ulv_solve_sorted(u, PU, s);
-  SPD_CUDA(cudaMemcpyAsync(p, z, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  copy_vec(p, z, nc, s);
   dots(r.p, z, n, nrhs, part.p, rz, s);
   std::vector<double> hrr(nrhs);
   auto true_residual = [&](std::vector<double>& rel, bool replace_active) {
-    SPD_CUDA(cudaMemcpyAsync(PR.xs.p, x.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    copy_vec(PR.xs.p, x.p, nc, s);
     h2_plan_run(h2, PR, s);
-    k_sub<<<gb, 256, 0, s>>>(bs.p, PR.ys.p, PR.ys.p, nc);
-    SPD_LAUNCHED();
+    sub(bs.p, PR.ys.p, PR.ys.p, nc, s);
     dots(PR.ys.p, PR.ys.p, n, nrhs, part.p, rr, s);
     std::vector<double> h(nrhs);
     SPD_CUDA(cudaMemcpyAsync(h.data(), rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -166,6 +309,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   };
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
+    merge_stage(10, it);
     if (PF) {                                     // q = A p in FP32
       convert_d2f(p, PF->xs.p, nc, s);
       h2_plan_run(h2, *PF, s);
@@ -174,8 +318,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       h2_plan_run(h2, PA, s);                     // q = A p
     }
     dots(p, q, n, nrhs, part.p, pq, s);
-    k_axpy_xr<<<gb, 256, 0, s>>>(x.p, r.p, p, q, n, nrhs, rz, pq, done.p);
-    SPD_LAUNCHED();
+    axpy_xr(x.p, r.p, p, q, n, nrhs, rz, pq, done.p, s);
     dots(r.p, r.p, n, nrhs, part.p, rr, s);
     SPD_CUDA(cudaMemcpyAsync(hrr.data(), rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     SPD_CUDA(cudaStreamSynchronize(s));
@@ -196,8 +339,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
         if (trel[c] <= tol) { hdone[c] = 1; changed = true; }
         else {
           // residual replacement: r = b - A x, and the next direction restarts (beta = 0)
-          SPD_CUDA(cudaMemcpyAsync(r.p + (int64_t)c * n, PR.ys.p + (int64_t)c * n, n * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, s));
+          copy_vec(r.p + (int64_t)c * n, PR.ys.p + (int64_t)c * n, n, s);
           hdone[c] = 2;
           changed = true;
         }
@@ -212,14 +354,13 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       // refine: the recursive residual of the FP32 product drifts; replace it by b - A x
       std::vector<double> trel;
       true_residual(trel, false);
-      SPD_CUDA(cudaMemcpyAsync(r.p, PR.ys.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      copy_vec(r.p, PR.ys.p, nc, s);
     }
-    SPD_CUDA(cudaMemcpyAsync(z, r.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    copy_vec(z, r.p, nc, s);
     ulv_solve_sorted(u, PU, s);                   // z = M^{-1} r
     dots(r.p, z, n, nrhs, part.p, rzn, s);
-    k_update_p<<<gb, 256, 0, s>>>(p, z, n, nrhs, rzn, rz, done.p);
-    SPD_LAUNCHED();
-    SPD_CUDA(cudaMemcpyAsync(rz, rzn, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    update_p(p, z, n, nrhs, rzn, rz, done.p, s);
+    copy_vec(rz, rzn, nrhs, s);
     bool restarted = false;
     for (int c = 0; c < nrhs; ++c)
       if (hdone[c] == 2) { hdone[c] = 0; restarted = true; }
@@ -227,6 +368,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       SPD_CUDA(cudaMemcpyAsync(done.p, hdone.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
   }
   std::vector<double> trel;
+  merge_stage(11, 0);
   true_residual(trel, false);
   converged = true;
   for (int c = 0; c < nrhs; ++c) {

@@ -127,6 +127,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
   }
 
   // ---- sampling: Y^(k), k = 1 .. L-1, in sorted order: ys column block (k-1)*s ----------
+  merge_stage(3, 0);
   const int nslot = L - 1;
   H2Plan plan;
   h2_plan_build(h2, plan, sc, nslot, s);
@@ -159,6 +160,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
   const double* UH = h2->basis.p;
 
   for (int k = 1; k <= L - 1; ++k) {
+    merge_stage(4, k);
     const int t = D + 1 - k;
     const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
     const bool leaf = (k == 1);
@@ -567,6 +569,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
   }
 
   // ---- compact the generators and the sibling blocks ---------------------------------
+  merge_stage(5, 0);
   hs->hoff.assign(NN + 1, 0);
   for (int i = 0; i < NN; ++i) hs->hoff[i + 1] = hs->hoff[i] + rk[i];
   hs->Rtot = hs->hoff[NN];

@@ -83,6 +83,7 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
   auto Up = [&](int64_t i) { return u->Ubuf.p + u->Uoff[i]; };
 
   for (int k = 1; k <= L - 1; ++k) {
+    merge_stage(6, k);
     const int t = D + 1 - k;
     const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
     // (1) D_i and W_i
@@ -262,6 +263,7 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
     }
   }
   // root block from the level L-1 reduced blocks
+  merge_stage(7, 0);
   {
     int mr = 0;
     for (int64_t c = T.child_begin[0]; c < T.child_end[0]; ++c) mr += u->r[c];

@@ -55,6 +55,14 @@ _SIGS = {
                         ctypes.POINTER(_D), _P],
     "pcg_solve": [_P, _P, _P, _P, _I, _I64, _D, _I, ctypes.POINTER(_I),
                   ctypes.POINTER(_D), _P],
+    "spdhss_build_batched": [_I, ctypes.POINTER(_P), _PI64, ctypes.POINTER(_I),
+                             ctypes.POINTER(KernelDesc), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                             ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(ctypes.c_uint64), _P, ctypes.POINTER(_P),
+                             ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I)],
+    "pcg_solve_batched": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                          ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
+                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
 }
 
 
@@ -79,6 +87,8 @@ def lib():
         L.spdhss_version.argtypes = []
         L.spdhss_profile.restype = None
         L.spdhss_profile.argtypes = [ctypes.c_int]
+        L.spdhss_batched_stats.restype = None
+        L.spdhss_batched_stats.argtypes = [_PI64]
         L.spdhss_profile_report.restype = ctypes.c_int64
         L.spdhss_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
         _lib = L
@@ -104,4 +114,4 @@ def profile_report() -> dict:
 
 def exported_symbols() -> list:
     return list(_SIGS) + ["spdhss_last_error", "spdhss_launch_count", "spdhss_version",
-                          "spdhss_profile", "spdhss_profile_report"]
+                          "spdhss_profile", "spdhss_profile_report", "spdhss_batched_stats"]
