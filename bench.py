@@ -548,6 +548,14 @@ def run_batch(count):
     t_s = time.perf_counter() - t0
     c3 = native.launch_count()
     diff = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(xb, xs))
+    # device time of the batched kernels (library CUDA events), one more batched pass
+    native.lib().spdhss_profile(1)
+    res = batched(dev)
+    prof = native.profile_report()
+    native.lib().spdhss_profile(0)
+    del res
+    busy = sum(v["ms"] for v in prof.values()) / 1e3
+    top = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]
     ib = [int(v[0]) for v in its_b]
     print(json.dumps({
         "metric": "SPD-HSS build+PCG solves/s over independent instances",
@@ -562,6 +570,8 @@ def run_batch(count):
         "pcg_iters": {"batched_max": max(ib), "single_max": max(its_s),
                       "max_abs_diff": max(abs(a - b) for a, b in zip(ib, its_s))},
         "max_rel_diff_batched_vs_single": diff,
+        "batched_kernel_s": busy,
+        "batched_top_kernels_ms": {k: round(v["ms"], 1) for k, v in top},
         "n_total": int(sum(i["points"].shape[0] for i in insts)),
         "dtype": "f64", "data": "synthetic"}))
 
