@@ -893,6 +893,214 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
   cl.sync();
 }
 
+// ---------------------------------------------------------------------------------------
+// The same factorization with every column resident in shared memory: a cluster of C CTAs
+// shares one matrix, CTA q holding the columns c with c % C == q for the whole
+// factorization (position swaps only permute a replicated position <-> column map).  Per
+// step: each CTA proposes its best remaining column, the cluster agrees on the pivot
+// (largest norm, lowest position), the owner forms the reflector in its shared memory, the
+// other CTAs copy it over DSMEM, and every CTA updates and re-measures its own columns.
+// Every reduction has the shape and order of k_geqp3, so the results are bit-identical.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kQrSmemBudget = 200 * 1024;
+
+struct QrSmemLayout {
+  int nown, ldm;
+  size_t cols, norms, pos2col, col2pos, v, total;
+};
+__host__ __device__ inline QrSmemLayout qr_smem_layout(int m, int n, int C) {
+  QrSmemLayout L;
+  L.nown = (n + C - 1) / C;
+  L.ldm = m + (m & 1);
+  L.cols = 0;
+  L.norms = L.cols + (size_t)L.nown * L.ldm * sizeof(double);
+  L.pos2col = L.norms + (size_t)L.nown * sizeof(double);
+  L.col2pos = L.pos2col + (size_t)n * sizeof(int);
+  L.v = (L.col2pos + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
+  L.total = L.v + (size_t)L.ldm * sizeof(double);
+  return L;
+}
+
+__global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ probs, int mmax,
+                                                    int nmax) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
+  const QrProb P = probs[blockIdx.x / C];
+  extern __shared__ __align__(16) unsigned char smem_qr[];
+  const QrSmemLayout Ly = qr_smem_layout(mmax, nmax, C);
+  double* cols = reinterpret_cast<double*>(smem_qr + Ly.cols);
+  double* norms = reinterpret_cast<double*>(smem_qr + Ly.norms);
+  int* pos2col = reinterpret_cast<int*>(smem_qr + Ly.pos2col);
+  int* col2pos = reinterpret_cast<int*>(smem_qr + Ly.col2pos);
+  double* s_v = reinterpret_cast<double*>(smem_qr + Ly.v);   // the reflector, m - j entries
+  __shared__ double s_wv[8];
+  __shared__ double s_cv[2];
+  __shared__ int s_cp[2];
+  __shared__ double s_first, s_tau;
+  __shared__ int s_stop, s_piv;
+  const int m = P.m, n = P.n;
+  const int kmax = min(P.kmax, min(m, n));
+  const int64_t ld = P.lda;
+  const int ldm = Ly.ldm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nown = (q < n) ? (n - q + C - 1) / C : 0;   // owned columns c = q + t * C
+
+  for (int t = warp; t < nown; t += nw) {
+    const double* src = P.A + (int64_t)(q + t * C) * ld;
+    double* dst = cols + (int64_t)t * ldm;
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double a = src[i];
+      dst[i] = a;
+      s += a * a;
+    }
+    s = warp_sum(s);
+    if (lane == 0) norms[t] = sqrt(s);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { pos2col[i] = i; col2pos[i] = i; }
+  cl.sync();
+
+  int j = 0;
+  for (; j < kmax; ++j) {
+    // this CTA's candidate: largest norm among its columns at positions >= j, lowest position
+    if (warp == 0) {
+      double bv = -1.0;
+      int bp = n;
+      for (int t = lane; t < nown; t += 32) {
+        const int p = col2pos[q + t * C];
+        if (p >= j) argmax_merge(bv, bp, norms[t], p);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
+        argmax_merge(bv, bp, v2, p2);
+      }
+      if (lane == 0) { s_cv[j & 1] = bv; s_cp[j & 1] = bp; }
+    }
+    cl.sync();
+    if (warp == 0) {
+      // the candidates of the C CTAs, one per lane (the merge order does not matter: the
+      // order (largest value, then lowest position) is total)
+      double gv = -1.0;
+      int gp = n;
+      if (lane < C) {
+        gv = *cl.map_shared_rank(&s_cv[j & 1], lane);
+        gp = *cl.map_shared_rank(&s_cp[j & 1], lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, gv, o);
+        const int p2 = __shfl_xor_sync(0xffffffffu, gp, o);
+        argmax_merge(gv, gp, v2, p2);
+      }
+      if (lane == 0) {
+        if (j == 0) s_first = gv;
+        s_stop = (gv <= 0.0) || (gv <= P.rtol * s_first) || (gp >= n);
+        if (!s_stop) {
+          // positions j and gp exchange their columns
+          const int cj = pos2col[j], cp = pos2col[gp];
+          pos2col[j] = cp; pos2col[gp] = cj;
+          col2pos[cp] = j; col2pos[cj] = gp;
+          s_piv = cp;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int cp = s_piv;
+    const int owner = cp % C;
+    if (q == owner) {
+      double* x = cols + (int64_t)(cp / C) * ldm;
+      double s = 0.0;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) { const double a = x[i]; s += a * a; }
+      s = warp_sum(s);
+      if (lane == 0) s_wv[warp] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += s_wv[w];
+        const double normx = sqrt(tot);
+        const double alpha = x[j];
+        double tau = 0.0, beta = alpha, scale = 0.0;
+        if (normx > 0.0) {
+          beta = alpha >= 0.0 ? -normx : normx;
+          scale = 1.0 / (alpha - beta);
+          tau = (beta - alpha) / beta;
+        }
+        s_tau = tau;
+        s_wv[0] = scale;
+        P.tau[j] = tau;
+        x[j] = beta;
+      }
+      __syncthreads();
+      const double scale = s_wv[0];
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= scale;
+    }
+    cl.sync();
+    // the reflector v (v_0 = 1) and tau from the owner's shared memory
+    const int len = m - j;
+    {
+      const double* xo = cl.map_shared_rank(cols + (int64_t)(cp / C) * ldm, owner);
+      for (int i = threadIdx.x; i < len; i += blockDim.x) s_v[i] = (i == 0) ? 1.0 : xo[j + i];
+      if (threadIdx.x == 0) s_wv[1] = *cl.map_shared_rank(&s_tau, owner);
+    }
+    __syncthreads();
+    const double tau = s_wv[1];
+    for (int t = warp; t < nown; t += nw) {
+      if (col2pos[q + t * C] <= j) continue;
+      double* col = cols + (int64_t)t * ldm + j;
+      if (tau != 0.0) {
+        double w = 0.0;
+        for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
+        w = warp_sum(w) * tau;
+        double s = 0.0;
+        for (int i = lane; i < len; i += 32) {
+          const double a = col[i] - w * s_v[i];
+          col[i] = a;
+          if (i > 0) s += a * a;
+        }
+        s = warp_sum(s);
+        if (lane == 0) norms[t] = sqrt(s);
+      } else {
+        double s = 0.0;
+        for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
+        s = warp_sum(s);
+        if (lane == 0) norms[t] = sqrt(s);
+      }
+    }
+    __syncthreads();
+  }
+  // columns to their final positions, the position -> column map, the rank
+  for (int t = warp; t < nown; t += nw) {
+    const int c = q + t * C;
+    const int p = col2pos[c];
+    double* dst = P.A + (int64_t)p * ld;
+    const double* src = cols + (int64_t)t * ldm;
+    for (int i = lane; i < m; i += 32) dst[i] = src[i];
+    if (lane == 0) {
+      P.piv[p] = c;
+      P.norms[p] = norms[t];
+    }
+  }
+  if (q == 0 && threadIdx.x == 0) *P.rank = j;
+  // keep every CTA of the cluster alive until peers are done reading its shared memory
+  cl.sync();
+}
+
+// Cluster size for the shared-memory variant, 0 to use k_geqp3.  A cluster spends C SMs
+// and two cluster barriers per step on one matrix: that pays when the batch has too few
+// matrices to fill the GPU one CTA each (measured on the H^2 ID: 3D leaves and the level
+// above at n = 4096 gain 1.4x, batches of 500+ full-rank leaves lose 2-3x); a matrix that
+// fits one CTA's shared memory always gains.
+static int geqp3_smem_cluster(int mmax, int nmax, size_t nprob) {
+  for (int C = 1; C <= 8; C *= 2)
+    if (qr_smem_layout(mmax, nmax, C).total <= kQrSmemBudget)
+      return (C == 1 || nprob <= 2 * 152) ? C : 0;
+  return 0;
+}
+
 // pivoted QRs of several instances: the largest cluster and row count of the group
 struct DeferredQr : Deferred {
   std::vector<QrProb> h;
@@ -924,6 +1132,35 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
     d->tag = b.tag;
     merge_ctx().m->submit(pivot ? "geqp3" : "geqrf", std::move(d));
     return -1;
+  }
+  if (pivot) {
+    int mmax = 1, nmax = 1;
+    for (const auto& p : b.h) { mmax = std::max(mmax, p.m); nmax = std::max(nmax, p.n); }
+    const int C = geqp3_smem_cluster(mmax, nmax, b.size());
+    if (C > 0) {
+      const size_t sm = qr_smem_layout(mmax, nmax, C).total;
+      static std::once_flag once_s;
+      std::call_once(once_s, [] {
+        cudaFuncSetAttribute(k_geqp3_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kQrSmemBudget);
+      });
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(b.size() * C), 1, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.dynamicSmemBytes = sm;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ProfScope ps(b.tag ? b.tag : "geqp3", s);
+      SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem, (const QrProb*)b.d.p, mmax, nmax));
+      SPD_LAUNCHED();
+      return ps.slot;
+    }
   }
   cluster = std::max(1, std::min(cluster, 8));
   const size_t smem = (size_t)std::max(1, max_m) * sizeof(double);
