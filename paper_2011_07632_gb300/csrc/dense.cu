@@ -162,14 +162,27 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
 // Very skinny variant for N <= 4 columns (matrix-vector like): 64-row tiles, 256 threads =
 // 64 rows x 4 groups that split every 32-wide K chunk; the four partial sums are added in
 // a fixed order through shared memory.
+// A tile with t.w > 0 covers only the K range kparts[t.w - 1] = (k_lo, k_hi, slot) of the
+// problem's concatenated segments and writes its unscaled partial sums to partial slot
+// `slot`; k_gemm_kreduce adds the slots of a tile in order and applies alpha and beta.
 template <class T, int NB>
 __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__ probs,
                                                 const GemmSegT<T>* __restrict__ segs,
-                                                const int4* __restrict__ tiles) {
+                                                const int4* __restrict__ tiles,
+                                                const int4* __restrict__ kparts,
+                                                T* __restrict__ partial) {
   constexpr int MB = 64, KB = 32;
   const int4 t = tiles[blockIdx.x];
   const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
+  int klo = 0, khi = 0x7fffffff;
+  T* pout = nullptr;
+  if (t.w > 0) {
+    const int4 kp = kparts[t.w - 1];
+    klo = kp.x;
+    khi = kp.y;
+    pout = partial + (int64_t)kp.z * (NB * MB);
+  }
   __shared__ T As[KB][MB + 1];
   __shared__ T Bs[KB][NB];
   __shared__ T red[4][NB][MB];
@@ -178,9 +191,12 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
   T acc[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c) acc[c] = 0;
+  int kbase = 0;   // offset of the segment in the concatenated K range
   for (int sg = P.seg0; sg < P.seg1; ++sg) {
     const GemmSegT<T> S = segs[sg];
-    for (int k0 = 0; k0 < S.K; k0 += KB) {
+    const int ks = max(0, klo - kbase), ke = min(S.K, khi - kbase);
+    kbase += S.K;
+    for (int k0 = ks; k0 < ke; k0 += KB) {
 #pragma unroll
       for (int r = 0; r < (MB * KB) / 256; ++r) {
         const int e = tid + 256 * r;
@@ -188,7 +204,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
         if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
         const int gm = m0 + mm, gk = k0 + kk;
         T v = 0;
-        if (gm < P.M && gk < S.K)
+        if (gm < P.M && gk < ke)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
       }
@@ -196,7 +212,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
         const int kk = tid % KB, nn = tid / KB;
         const int gn = n0 + nn, gk = k0 + kk;
         T v = 0;
-        if (gn < P.N && gk < S.K)
+        if (gn < P.N && gk < ke)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
       }
@@ -214,7 +230,11 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
 #pragma unroll
   for (int c = 0; c < NB; ++c) red[kg][c][row] = acc[c];
   __syncthreads();
-  if (kg == 0) {
+  if (kg == 0 && pout) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      pout[c * MB + row] = (red[0][c][row] + red[1][c][row]) + (red[2][c][row] + red[3][c][row]);
+  } else if (kg == 0) {
     const int gm = m0 + row;
     if (gm < P.M) {
 #pragma unroll
@@ -232,6 +252,30 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
   }
 }
 
+// the K parts of a split tile: out = alpha * (sum of the slots in order) + beta * out
+template <class T, int NB>
+__global__ void __launch_bounds__(64) k_gemm_kreduce(const GemmProbT<T>* __restrict__ probs,
+                                                     const int4* __restrict__ reds,
+                                                     const int* __restrict__ nparts,
+                                                     const T* __restrict__ partial) {
+  constexpr int MB = 64;
+  const int4 r = reds[blockIdx.x];   // (problem, m0, n0, first slot)
+  const int np = nparts[blockIdx.x];
+  const GemmProbT<T> P = probs[r.x];
+  const int row = threadIdx.x, gm = r.y + row;
+  if (gm >= P.M) return;
+  for (int c = 0; c < NB; ++c) {
+    const int gn = r.z + c;
+    if (gn >= P.N) break;
+    T v0 = partial[(int64_t)r.w * (NB * MB) + c * MB + row];
+    for (int q = 1; q < np; ++q) v0 += partial[(int64_t)(r.w + q) * (NB * MB) + c * MB + row];
+    T* cp = P.C + gm + (int64_t)gn * P.ldc;
+    T v = (T)P.alpha * v0;
+    if (P.beta != 0.0) v += (T)P.beta * (*cp);
+    *cp = v;
+  }
+}
+
 static int gemm_variant(int maxn) {
   if (maxn <= 1) return 1;
   if (maxn <= 2) return 2;
@@ -244,11 +288,12 @@ static int gemm_variant(int maxn) {
 
 template <class T>
 static void gemm_dispatch(int nb, int g, const GemmProbT<T>* pr, const GemmSegT<T>* sg,
-                          const int4* tl, cudaStream_t s) {
+                          const int4* tl, cudaStream_t s, const int4* kp = nullptr,
+                          T* partial = nullptr) {
   switch (nb) {
-    case 1: k_gemm_k<T, 1><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 2: k_gemm_k<T, 2><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 4: k_gemm_k<T, 4><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 1: k_gemm_k<T, 1><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
+    case 2: k_gemm_k<T, 2><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
+    case 4: k_gemm_k<T, 4><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
     case 8: k_gemm_n<T, 8><<<g, 256, 0, s>>>(pr, sg, tl); break;
     case 16: k_gemm_n<T, 16><<<g, 256, 0, s>>>(pr, sg, tl); break;
     case 32: k_gemm_n<T, 32><<<g, 256, 0, s>>>(pr, sg, tl); break;
@@ -275,6 +320,35 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
     }
     flops += 2.0 * probs[p].M * (double)probs[p].N * kk;
     bytes += sizeof(T) * (double)probs[p].M * probs[p].N * (probs[p].beta != 0.0 ? 2.0 : 1.0);
+  }
+  // matrix-vector-like products on too few tiles to fill the GPU: split the K range of each
+  // tile over several CTAs (partial sums, added in order by k_gemm_kreduce)
+  kparts.clear();
+  reds.clear();
+  rednp.clear();
+  if (nb >= 1 && nb <= 4 && !tiles.empty() && (int64_t)tiles.size() < 2 * 152) {
+    const int want = (int)std::min<int64_t>(16, ceil_div(4 * 152, (int64_t)tiles.size()));
+    std::vector<int4> nt;
+    int slot = 0;
+    for (const int4& t : tiles) {
+      int K = 0;
+      for (int g = probs[t.x].seg0; g < probs[t.x].seg1; ++g) K += segs[g].K;
+      const int kp = std::min(want, (K + 127) / 128);
+      if (kp <= 1) { nt.push_back(t); continue; }
+      reds.push_back(make_int4(t.x, t.y, t.z, slot));
+      rednp.push_back(kp);
+      for (int q = 0; q < kp; ++q) {
+        const int lo = (int)((int64_t)K * q / kp), hi = (int)((int64_t)K * (q + 1) / kp);
+        kparts.push_back(make_int4(lo, hi, slot + q, 0));
+        nt.push_back(make_int4(t.x, t.y, t.z, (int)kparts.size()));
+      }
+      slot += kp;
+    }
+    tiles.swap(nt);
+    d_kparts.upload(kparts, s);
+    d_reds.upload(reds, s);
+    d_rednp.upload(rednp, s);
+    d_partial.alloc(std::max(slot, 1) * (size_t)nb * 64);
   }
   d_segs.upload(segs, s);
   d_probs.upload(probs, s);
@@ -321,7 +395,16 @@ void GemmBatchT<T>::launch(cudaStream_t s) const {
   ProfScope ps(tag, s, flops, bytes);
   for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
     const int g = (int)std::min<int64_t>(nt - b0, 2147483647LL);
-    gemm_dispatch<T>(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s);
+    gemm_dispatch<T>(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s, d_kparts.p, d_partial.p);
+    SPD_LAUNCHED();
+  }
+  if (!reds.empty()) {
+    const unsigned g = (unsigned)reds.size();
+    switch (nb) {
+      case 1: k_gemm_kreduce<T, 1><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
+      case 2: k_gemm_kreduce<T, 2><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
+      default: k_gemm_kreduce<T, 4><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
+    }
     SPD_LAUNCHED();
   }
 }
@@ -347,7 +430,7 @@ __global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ pro
       const double d = A[j + j * ld];
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = 1;
-        if (atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = j;
+        if (atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = P.col0 + j;
       }
       s_d = sqrt(d);
     }
@@ -396,7 +479,7 @@ __global__ void __launch_bounds__(256) k_potrf_blk(const PotrfProb* __restrict__
         if (lane == 0) {
           const double d = dk[j][j];
           if (!(d > 0.0) || !isfinite(d)) {
-            if (!s_fail && atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = k0 + j;
+            if (!s_fail && atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = P.col0 + k0 + j;
             s_fail = 1;
             dk[j][j] = 1.0;
           } else {
@@ -475,7 +558,117 @@ __global__ void __launch_bounds__(256) k_potrf_blk(const PotrfProb* __restrict__
     for (int i = lane; i < c; i += 32) A[i + (int64_t)c * ld] = 0.0;
 }
 
+// Matrices larger than kPotrfBig are factored by blocks of kPotrfNB columns over several
+// launches, each covering all of them: Cholesky of the diagonal block (one CTA each), its
+// triangular inverse (TRSM on the identity, one warp per column), the panel
+// L_ik = A_ik L_kk^{-T} and the trailing update of the lower triangle as grouped GEMMs over
+// many CTAs.  One CTA would run the whole O(n^3) factorization at the FP64 rate of a single
+// SM.
+constexpr int kPotrfBig = 128, kPotrfNB = 64;
+
+static void potrf_one_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s);
+
+static void potrf_blocked(const std::vector<PotrfProb>& big, int* d_info, const char* tag,
+                          cudaStream_t s) {
+  const int NB = kPotrfNB;
+  const size_t np = big.size();
+  std::vector<int64_t> soff(np + 1, 0);
+  int nmax = 0;
+  for (size_t q = 0; q < np; ++q) {
+    soff[q + 1] = soff[q] + (int64_t)NB * NB + (int64_t)big[q].n * NB;
+    nmax = std::max(nmax, big[q].n);
+  }
+  DevBuf<double> scratch(std::max<int64_t>(soff[np], 1));
+  for (int k0 = 0; k0 < nmax; k0 += NB) {
+    Batch<PotrfProb> pd;
+    Batch<CopyProb> idb, back;
+    Batch<TrsmProb> tb;
+    GemmBatch panel, trail;
+    pd.tag = tag;
+    for (size_t q = 0; q < np; ++q) {
+      const PotrfProb& P = big[q];
+      if (P.n <= k0) continue;
+      const int kb = std::min(NB, P.n - k0);
+      const int64_t ld = P.lda;
+      double* Akk = P.A + k0 + (int64_t)k0 * ld;
+      PotrfProb d = P;
+      d.A = Akk;
+      d.n = kb;
+      d.info = P.info ? P.info : d_info;
+      d.col0 = P.col0 + k0;
+      pd.push(d);
+      const int r0 = k0 + kb, R = P.n - r0;
+      if (R <= 0) continue;
+      double* W = scratch.p + soff[q];            // kb x kb: L_kk^{-1}
+      double* S = W + (int64_t)NB * NB;           // R x kb: the new panel
+      CopyProb c;
+      c.src = nullptr; c.lds = kb; c.dst = W; c.ldd = kb; c.m = kb; c.n = kb;
+      c.trans = 0; c.accumulate = 0; c.alpha = 1.0;
+      idb.push(c);
+      TrsmProb t;
+      t.T = Akk; t.ldt = ld; t.B = W; t.ldb = kb; t.n = kb; t.ncol = kb; t.lower = 1; t.trans = 0;
+      tb.push(t);
+      double* Ap = P.A + r0 + (int64_t)k0 * ld;
+      panel.add(S, R, R, kb, Ap, ld, 0, W, kb, 1, kb, 1.0, 0.0);
+      for (int j0 = r0; j0 < P.n; j0 += NB) {
+        const int jw = std::min(NB, P.n - j0);
+        trail.add(P.A + j0 + (int64_t)j0 * ld, ld, P.n - j0, jw, S + (j0 - r0), R, 0,
+                  S + (j0 - r0), R, 1, kb, -1.0, 1.0);
+      }
+      CopyProb cb;
+      cb.src = S; cb.lds = R; cb.dst = Ap; cb.ldd = ld; cb.m = R; cb.n = kb;
+      cb.trans = 0; cb.accumulate = 0; cb.alpha = 1.0;
+      back.push(cb);
+    }
+    pd.upload(s);
+    potrf_one_launch(pd, d_info, s);
+    if (idb.empty()) continue;
+    idb.upload(s);
+    identity_launch(idb, s);
+    tb.tag = "trsm_potrf_inv";
+    tb.upload(s);
+    trsm_launch(tb, s);
+    panel.tag = trail.tag = "gemm_potrf";
+    panel.run(s);
+    trail.run(s);
+    back.upload(s);
+    copy_launch(back, s);
+  }
+  // zeros above the diagonal blocks
+  Batch<CopyProb> z;
+  for (const auto& P : big)
+    for (int j0 = NB; j0 < P.n; j0 += NB) {
+      CopyProb c;
+      c.src = nullptr; c.lds = j0; c.dst = P.A + (int64_t)j0 * P.lda; c.ldd = P.lda;
+      c.m = j0; c.n = std::min(NB, P.n - j0); c.trans = 0; c.accumulate = 0; c.alpha = 1.0;
+      z.push(c);
+    }
+  z.upload(s);
+  copy_launch(z, s);
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
+  if (!merging() && !b.empty()) {
+    int nmax = 0;
+    for (const auto& p : b.h) nmax = std::max(nmax, p.n);
+    if (nmax > kPotrfBig) {
+      Batch<PotrfProb> small;
+      std::vector<PotrfProb> big;
+      small.tag = b.tag;
+      for (const auto& p : b.h) (p.n > kPotrfBig ? big.push_back(p) : small.push(p));
+      if (!small.empty()) {
+        small.upload(s);
+        potrf_one_launch(small, d_info, s);
+      }
+      potrf_blocked(big, d_info, b.tag ? b.tag : "potrf", s);
+      return;
+    }
+  }
+  potrf_one_launch(b, d_info, s);
+}
+
+static void potrf_one_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
   if (b.empty()) { merge_skip(); return; }
   if (merging()) {
     std::vector<PotrfProb> h = b.h;
@@ -1217,6 +1410,85 @@ __global__ void __launch_bounds__(256) k_hh_apply(const HhApplyProb* __restrict_
   }
 }
 
+// The same product with the column held in registers: lane l owns rows l + 32 e (e < EPT,
+// m <= 32 EPT), so each reflector costs one round of independent loads of v (issued one
+// reflector ahead) and one warp reduction, instead of two passes over the column in memory.
+template <int EPT>
+__global__ void __launch_bounds__(256) k_hh_apply_r(const HhApplyProb* __restrict__ probs,
+                                                    const int2* __restrict__ work, int64_t nwork,
+                                                    int trans) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nwork) return;
+  const int lane = threadIdx.x & 31;
+  const int2 it = work[w];
+  const HhApplyProb P = probs[it.x];
+  const int k = *P.k;
+  double* b = P.B + (int64_t)it.y * P.ldb;
+  double x[EPT], vn[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = lane + 32 * e;
+    x[e] = (i < P.m) ? b[i] : 0.0;
+  }
+  auto load_v = [&](int t, double* vv, double& tau) {
+    const int j = trans ? t : k - 1 - t;
+    const double* v = P.V + (int64_t)j * P.ldv;
+    tau = P.tau[j];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = lane + 32 * e;
+      vv[e] = (i > j && i < P.m) ? v[i] : (i == j ? 1.0 : 0.0);
+    }
+  };
+  double taun = 0.0;
+  if (k > 0) load_v(0, vn, taun);
+  for (int t = 0; t < k; ++t) {
+    double vv[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) vv[e] = vn[e];
+    const double tau = taun;
+    if (t + 1 < k) load_v(t + 1, vn, taun);
+    if (tau == 0.0) continue;
+    double s = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) s = fma(vv[e], x[e], s);
+    s = warp_sum(s) * tau;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) x[e] -= s * vv[e];
+  }
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = lane + 32 * e;
+    if (i < P.m) b[i] = x[e];
+  }
+}
+
+// registers per lane for the rows of the tallest matrix (0: too tall, generic kernel)
+static int hh_ept(const Batch<HhApplyProb>& b) {
+  int mx = 1;
+  for (const auto& p : b.h) mx = std::max(mx, p.m);
+  const int e = (mx + 31) / 32;
+  return e <= 1 ? 1 : (e <= 2 ? 2 : (e <= 4 ? 4 : (e <= 8 ? 8 : (e <= 16 ? 16 : 0))));
+}
+
+// FP64 issue is 2 FMA per clock per SM on this part: with few columns the warps are spread
+// one or two per CTA so that they land on different SMs.
+static void hh_go(const HhApplyProb* probs, const int2* work, int64_t nw, int ept, int trans,
+                  cudaStream_t s) {
+  const int wpb = nw >= 8 * 152 ? 8 : (nw >= 2 * 152 ? 2 : 1);   // warps per CTA
+  const unsigned g = (unsigned)ceil_div(nw, wpb);
+  const int bs = 32 * wpb;
+  switch (ept) {
+    case 1: k_hh_apply_r<1><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
+    case 2: k_hh_apply_r<2><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
+    case 4: k_hh_apply_r<4><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
+    case 8: k_hh_apply_r<8><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
+    case 16: k_hh_apply_r<16><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
+    default: k_hh_apply<<<(unsigned)ceil_div(nw, 8), 256, 0, s>>>(probs, work, nw, trans); break;
+  }
+  SPD_LAUNCHED();
+}
+
 static std::vector<int2> hh_work(const Batch<HhApplyProb>& b) {
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
@@ -1228,6 +1500,7 @@ void householder_prepare(Batch<HhApplyProb>& b, cudaStream_t s) {
   std::vector<int2> w = hh_work(b);
   b.work.upload(w, s);
   b.nwork = (int64_t)w.size();
+  b.variant = hh_ept(b);
 }
 
 void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) {
@@ -1247,8 +1520,7 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
     ProfScope ps(b.tag ? b.tag : "householder", s);
-    k_hh_apply<<<ceil_div(b.nwork, 8), 256, 0, s>>>(b.d.p, b.work.p, b.nwork, trans);
-    SPD_LAUNCHED();
+    hh_go(b.d.p, b.work.p, b.nwork, b.variant, trans, s);
     return;
   }
   std::vector<int2> work = hh_work(b);
@@ -1258,8 +1530,7 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   const int64_t nw = (int64_t)work.size();
   {
     ProfScope ps(b.tag ? b.tag : "householder", s);
-    k_hh_apply<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw, trans);
-    SPD_LAUNCHED();
+    hh_go(b.d.p, dw.p, nw, hh_ept(b), trans, s);
   }
   SPD_CUDA(cudaStreamSynchronize(s));
 }

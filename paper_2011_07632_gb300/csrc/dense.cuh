@@ -58,7 +58,7 @@ struct GemmBatchT {
   void upload(cudaStream_t s);
   void launch(cudaStream_t s) const;
   void run(cudaStream_t s) { upload(s); launch(s); }
-  void clear() { segs.clear(); probs.clear(); tiles.clear(); }
+  void clear() { segs.clear(); probs.clear(); tiles.clear(); kparts.clear(); reds.clear(); rednp.clear(); }
   std::vector<int4> tiles;   // (prob, m0, n0, 0)
   const char* tag = "gemm";
   int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
@@ -66,6 +66,13 @@ struct GemmBatchT {
   DevBuf<GemmSegT<T>> d_segs;
   DevBuf<GemmProbT<T>> d_probs;
   DevBuf<int4> d_tiles;
+  // K-split tiles of the few-column kernel: (k_lo, k_hi, slot) per split tile, and per
+  // split output tile (problem, m0, n0, first slot) with its number of parts
+  std::vector<int4> kparts, reds;
+  std::vector<int> rednp;
+  DevBuf<int4> d_kparts, d_reds;
+  DevBuf<int> d_rednp;
+  DevBuf<T> d_partial;
 };
 using GemmBatch = GemmBatchT<double>;
 using SGemmBatch = GemmBatchT<float>;
@@ -94,6 +101,7 @@ struct PotrfProb {
   int n;
   int tag;   // reported in the failure record
   int* info = nullptr;   // failure record of this matrix (null: the launch's d_info)
+  int col0 = 0;          // added to the failing column in the record (a diagonal block)
 };
 // info[0] receives tag+1 of a failing matrix (0 if all succeed); info[1] the failing column.
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s);

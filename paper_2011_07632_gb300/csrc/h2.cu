@@ -454,9 +454,6 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 
-void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s) {
-  h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, h->coup.p, s);
-}
 
 __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -482,24 +479,26 @@ void convert_f2d(const float* x, double* y, int64_t count, cudaStream_t s) {
   SPD_LAUNCHED();
 }
 
-// FP64 coupling block (owner orientation, possibly transposed) -> FP32 destination-major
-struct CopyD2F {
+// FP64 coupling block (owner orientation, possibly transposed) -> destination-major copy
+template <class TD>
+struct CopyDM {
   const double* src;
   int64_t lds;
   int trans;
-  float* dst;
+  TD* dst;
   int64_t ldd;
   int m, n;
 };
 
-__global__ void k_copy_d2f(const CopyD2F* __restrict__ probs) {
-  const CopyD2F P = probs[blockIdx.y];
+template <class TD>
+__global__ void k_copy_dm(const CopyDM<TD>* __restrict__ probs) {
+  const CopyDM<TD> P = probs[blockIdx.y];
   const int64_t tot = (int64_t)P.m * P.n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % P.m), j = (int)(e / P.m);
     const double v = P.trans ? P.src[j + (int64_t)i * P.lds] : P.src[i + (int64_t)j * P.lds];
-    P.dst[i + (int64_t)j * P.ldd] = (float)v;
+    P.dst[i + (int64_t)j * P.ldd] = (TD)v;
   }
 }
 
@@ -508,20 +507,27 @@ __global__ void k_copy_d2f(const CopyD2F* __restrict__ probs) {
 // takes chunk t * G + g.  Partial sums of the groups are added in group order, and the
 // parts of a node split over several CTAs are added in part order (deterministic).
 constexpr int kRowChunk = 64;
-constexpr int64_t kRowItemEntries = int64_t(1) << 20;   // coupling entries per CTA (target)
+// coupling entries per CTA: about total / (152 SMs x 16), within [4096, 2^20], so that small
+// products still spread over many CTAs and large ones keep long streams
+constexpr int64_t kRowItemMax = int64_t(1) << 20;
+constexpr int64_t kRowItemMin = 4096;
 
 __host__ __device__ constexpr int rowcoup_ncp(int nc) { return nc < 4 ? nc : 4 * ((nc + 3) / 4); }
 
-template <int NC>
-__global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __restrict__ probs,
-                                                       const RowCoupChunk* __restrict__ chunks,
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProbT<T>* __restrict__ probs,
+                                                       const RowCoupChunkT<T>* __restrict__ chunks,
                                                        const RowCoupWork* __restrict__ work,
-                                                       float* __restrict__ partial, int c0) {
+                                                       T* __restrict__ partial, int c0) {
   constexpr int NCP = rowcoup_ncp(NC);
-  extern __shared__ __align__(16) float smem_rc[];
-  float* xs = smem_rc;                        // [G][kRowChunk][NCP]
+  extern __shared__ __align__(16) unsigned char smem_rc_raw[];
+  T* smem_rc = reinterpret_cast<T*>(smem_rc_raw);
+  T* xs = smem_rc;                            // [G][kRowChunk][NCP]
   const RowCoupWork W = work[blockIdx.x];
-  const RowCoupProb P = probs[W.p];
+  const RowCoupProbT<T> P = probs[W.p];
   const int rows = min(P.M - W.r0, 256);
   const int Mw = (rows + 31) / 32;
   const int G = 8 / Mw;
@@ -530,9 +536,9 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __rest
   const int g = tid / RW, rl = tid % RW;
   const int r = W.r0 + rl;
   const bool active = g < G && rl < rows;
-  float acc[NC];
+  T acc[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
   const int64_t M = P.M;
   const int nch = W.ch1 - W.ch0;
   const int rounds = (nch + G - 1) / G;
@@ -544,9 +550,9 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __rest
       const int rem = e - gg * NC * kRowChunk;
       const int c = rem / kRowChunk, kk = rem - c * kRowChunk;
       const int ch = t * G + gg;
-      float v = 0.0f;
+      T v = T(0);
       if (ch < nch) {
-        const RowCoupChunk C = chunks[W.ch0 + ch];
+        const RowCoupChunkT<T> C = chunks[W.ch0 + ch];
         if (kk < C.K && c < ncl) v = C.x[(int64_t)(c0 + c) * C.ldx + kk];
       }
       xs[(gg * kRowChunk + kk) * NCP + c] = v;
@@ -554,37 +560,44 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __rest
     __syncthreads();
     const int ch = t * G + g;
     if (active && ch < nch) {
-      const RowCoupChunk C = chunks[W.ch0 + ch];
-      const float* a = P.A + r + C.col * M;
-      const float* xg = xs + g * kRowChunk * NCP;
-      for (int kk0 = 0; kk0 < C.K; kk0 += 16) {
-        float b[16];
+      const RowCoupChunkT<T> C = chunks[W.ch0 + ch];
+      const T* a = P.A + r + C.col * M;
+      const T* xg = xs + g * kRowChunk * NCP;
+      int kk0 = 0;
+      for (; kk0 + 16 <= C.K; kk0 += 16) {
+        T b[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          b[u] = (kk0 + u < C.K) ? __ldg(a + (int64_t)(kk0 + u) * M) : 0.0f;
+        for (int u = 0; u < 16; ++u) b[u] = __ldg(a + (int64_t)(kk0 + u) * M);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const float* xr = xg + (kk0 + u) * NCP;
-          if constexpr (NC >= 4) {
+          const T* xr = xg + (kk0 + u) * NCP;
+          if constexpr (NC >= 4 && sizeof(T) == 4) {
 #pragma unroll
             for (int c4 = 0; c4 < NCP / 4; ++c4) {
               const float4 v = reinterpret_cast<const float4*>(xr)[c4];
-              if (4 * c4 + 0 < NC) acc[4 * c4 + 0] = fmaf(b[u], v.x, acc[4 * c4 + 0]);
-              if (4 * c4 + 1 < NC) acc[4 * c4 + 1] = fmaf(b[u], v.y, acc[4 * c4 + 1]);
-              if (4 * c4 + 2 < NC) acc[4 * c4 + 2] = fmaf(b[u], v.z, acc[4 * c4 + 2]);
-              if (4 * c4 + 3 < NC) acc[4 * c4 + 3] = fmaf(b[u], v.w, acc[4 * c4 + 3]);
+              if (4 * c4 + 0 < NC) acc[4 * c4 + 0] = fma_t(b[u], v.x, acc[4 * c4 + 0]);
+              if (4 * c4 + 1 < NC) acc[4 * c4 + 1] = fma_t(b[u], v.y, acc[4 * c4 + 1]);
+              if (4 * c4 + 2 < NC) acc[4 * c4 + 2] = fma_t(b[u], v.z, acc[4 * c4 + 2]);
+              if (4 * c4 + 3 < NC) acc[4 * c4 + 3] = fma_t(b[u], v.w, acc[4 * c4 + 3]);
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = fmaf(b[u], xr[c], acc[c]);
+            for (int c = 0; c < NC; ++c) acc[c] = fma_t(b[u], xr[c], acc[c]);
           }
         }
+      }
+      // the rest of the chunk, without padding FMAs
+      for (; kk0 < C.K; ++kk0) {
+        const T bu = __ldg(a + (int64_t)kk0 * M);
+        const T* xr = xg + kk0 * NCP;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma_t(bu, xr[c], acc[c]);
       }
     }
     __syncthreads();
   }
   // group partial sums through shared memory: red[g][c][rl]
-  float* red = smem_rc;
+  T* red = smem_rc;
   if (G > 1) {
     if (active)
 #pragma unroll
@@ -593,7 +606,7 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __rest
     if (g == 0 && active) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        float v = red[c * RW + rl];
+        T v = red[c * RW + rl];
         for (int gg = 1; gg < G; ++gg) v += red[(gg * NC + c) * RW + rl];
         acc[c] = v;
       }
@@ -605,25 +618,25 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProb* __rest
       for (int c = 0; c < NC; ++c)
         if (c < ncl) P.C[r + (int64_t)(c0 + c) * P.ldc] = acc[c];
     } else {
-      float* pt = partial + W.part * (NC * 256);
+      T* pt = partial + W.part * (NC * 256);
 #pragma unroll
       for (int c = 0; c < NC; ++c) pt[c * 256 + rl] = acc[c];
     }
   }
 }
 
-template <int NC>
-__global__ void __launch_bounds__(256) k_coupling_rows_reduce(const RowCoupProb* __restrict__ probs,
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_coupling_rows_reduce(const RowCoupProbT<T>* __restrict__ probs,
                                                               const RowCoupRed* __restrict__ red,
-                                                              const float* __restrict__ partial,
+                                                              const T* __restrict__ partial,
                                                               int c0) {
   const RowCoupRed R = red[blockIdx.x];
-  const RowCoupProb P = probs[R.p];
+  const RowCoupProbT<T> P = probs[R.p];
   const int rl = threadIdx.x;
   if (rl >= min(P.M - R.r0, 256)) return;
   const int ncl = min(NC, P.ncol - c0);
   for (int c = 0; c < ncl; ++c) {
-    float v = 0.0f;
+    T v = T(0);
     for (int q = 0; q < R.nparts; ++q) v += partial[(R.part0 + q) * (NC * 256) + c * 256 + rl];
     P.C[R.r0 + rl + (int64_t)(c0 + c) * P.ldc] = v;
   }
@@ -633,26 +646,30 @@ static int rowcoup_nc(int ncol) {
   return ncol <= 1 ? 1 : (ncol <= 2 ? 2 : (ncol <= 4 ? 4 : (ncol <= 8 ? 8 : 16)));
 }
 
-void RowCoupBatch::upload(cudaStream_t s) {
+template <class T>
+void RowCoupBatchT<T>::upload(cudaStream_t s) {
   work.clear();
   red.clear();
   flops = bytes = 0.0;
-  int64_t nparts = 0;
+  int64_t nparts = 0, total = 0;
+  for (const auto& P : probs)
+    for (int g = P.ch0; g < P.ch1; ++g) total += (int64_t)P.M * chunks[g].K;
+  const int64_t item = std::min(kRowItemMax, std::max(kRowItemMin, total / (152 * 16)));
   for (int p = 0; p < (int)probs.size(); ++p) {
-    const RowCoupProb& P = probs[p];
+    const RowCoupProbT<T>& P = probs[p];
     int64_t kt = 0;
     for (int g = P.ch0; g < P.ch1; ++g) kt += chunks[g].K;
     flops += 2.0 * P.M * (double)kt * P.ncol;
-    bytes += 4.0 * P.M * (double)kt;
+    bytes += sizeof(T) * (double)P.M * (double)kt;
     for (int r0 = 0; r0 < P.M; r0 += 256) {
       const int rows = std::min(P.M - r0, 256);
-      // cut the chunk range into parts of about kRowItemEntries entries
+      // cut the chunk range into parts of about `item` entries
       std::vector<std::pair<int, int>> parts;
       int start = P.ch0;
       int64_t acc = 0;
       for (int g = P.ch0; g < P.ch1; ++g) {
         acc += (int64_t)rows * chunks[g].K;
-        if (acc >= kRowItemEntries && g + 1 < P.ch1) {
+        if (acc >= item && g + 1 < P.ch1) {
           parts.emplace_back(start, g + 1);
           start = g + 1;
           acc = 0;
@@ -683,120 +700,197 @@ void RowCoupBatch::upload(cudaStream_t s) {
   partial.alloc(std::max<int64_t>(nparts, 1) * rowcoup_nc(ncol) * 256);
 }
 
-template <int NC>
-static void rowcoup_go(const RowCoupBatch& b, cudaStream_t s) {
+template <class T, int NC>
+static void rowcoup_go(const RowCoupBatchT<T>& b, cudaStream_t s) {
   constexpr int NCP = rowcoup_ncp(NC);
-  const size_t smem = (size_t)8 * kRowChunk * NCP * sizeof(float);
-  // the reduction reuses the staging buffer: G * NC * RW <= 256 * NC floats
+  const size_t smem = (size_t)8 * kRowChunk * NCP * sizeof(T);
+  // the reduction reuses the staging buffer: G * NC * RW <= 256 * NC entries
   static_assert(8 * kRowChunk * NCP >= 256 * NC, "reduction buffer");
   if (smem > 48 * 1024)
-    SPD_CUDA(cudaFuncSetAttribute(k_coupling_rows<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    SPD_CUDA(cudaFuncSetAttribute(k_coupling_rows<T, NC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int c0 = 0; c0 < b.ncol; c0 += NC) {
-    k_coupling_rows<NC><<<(unsigned)b.work.size(), 256, smem, s>>>(
+    k_coupling_rows<T, NC><<<(unsigned)b.work.size(), 256, smem, s>>>(
         b.d_probs.p, b.d_chunks.p, b.d_work.p, b.partial.p, c0);
     SPD_LAUNCHED();
     if (!b.red.empty()) {
-      k_coupling_rows_reduce<NC><<<(unsigned)b.red.size(), 256, 0, s>>>(b.d_probs.p, b.d_red.p,
-                                                                        b.partial.p, c0);
+      k_coupling_rows_reduce<T, NC><<<(unsigned)b.red.size(), 256, 0, s>>>(
+          b.d_probs.p, b.d_red.p, b.partial.p, c0);
       SPD_LAUNCHED();
     }
   }
 }
 
-void RowCoupBatch::launch(cudaStream_t s) const {
-  if (work.empty()) return;
-  ProfScope ps("h2_coupling_f32", s, flops, bytes);
-  switch (rowcoup_nc(ncol)) {
-    case 1: rowcoup_go<1>(*this, s); break;
-    case 2: rowcoup_go<2>(*this, s); break;
-    case 4: rowcoup_go<4>(*this, s); break;
-    case 8: rowcoup_go<8>(*this, s); break;
-    default: rowcoup_go<16>(*this, s); break;
+// several instances' coupling steps (batched sweep): problems and chunks concatenated
+template <class T>
+struct DeferredRowCoup : Deferred {
+  std::vector<RowCoupProbT<T>> probs;
+  std::vector<RowCoupChunkT<T>> chunks;
+  int ncol = 1;
+  const char* tag = "h2_coupling";
+  void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
+    RowCoupBatchT<T> m;
+    m.tag = tag;
+    for (Deferred* d : group) {
+      const auto* x = static_cast<const DeferredRowCoup<T>*>(d);
+      const int off = (int)m.chunks.size();
+      m.chunks.insert(m.chunks.end(), x->chunks.begin(), x->chunks.end());
+      for (RowCoupProbT<T> p : x->probs) {
+        p.ch0 += off;
+        p.ch1 += off;
+        m.probs.push_back(p);
+      }
+      m.ncol = std::max(m.ncol, x->ncol);
+    }
+    m.upload(s);
+    m.launch(s);
   }
+};
+
+template <class T>
+void RowCoupBatchT<T>::launch(cudaStream_t s) const {
+  if (merging()) {
+    if (probs.empty()) { merge_skip(); return; }
+    std::unique_ptr<DeferredRowCoup<T>> d(new DeferredRowCoup<T>());
+    d->probs = probs;
+    d->chunks = chunks;
+    d->ncol = ncol;
+    d->tag = tag;
+    merge_ctx().m->submit(std::string(sizeof(T) == 8 ? "rowcoup_f64_" : "rowcoup_f32_") +
+                              std::to_string(rowcoup_nc(ncol)), std::move(d));
+    return;
+  }
+  if (work.empty()) return;
+  ProfScope ps(tag, s, flops, bytes);
+  switch (rowcoup_nc(ncol)) {
+    case 1: rowcoup_go<T, 1>(*this, s); break;
+    case 2: rowcoup_go<T, 2>(*this, s); break;
+    case 4: rowcoup_go<T, 4>(*this, s); break;
+    case 8: rowcoup_go<T, 8>(*this, s); break;
+    default: rowcoup_go<T, 16>(*this, s); break;
+  }
+}
+
+template struct RowCoupBatchT<double>;
+template struct RowCoupBatchT<float>;
+
+// Offsets of the destination-major coupling matrices (once per handle).
+static void coup_dm_offsets(spdhss_h2_s* h) {
+  if (!h->coup_dm_off.empty()) return;
+  const TreeHost& T = h->th;
+  const int64_t NN = T.nn();
+  h->coup_dm_off.assign(NN + 1, 0);
+  for (int64_t i = 0; i < NN; ++i) {
+    int64_t kt = 0;
+    if (h->rank(i) > 0)
+      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) kt += h->rank(T.far_idx[e]);
+    h->coup_dm_off[i + 1] = h->coup_dm_off[i] + (int64_t)h->rank(i) * kt;
+  }
+}
+
+// The destination-major copy of the couplings in type TD.
+template <class TD>
+static void coup_dm_build(spdhss_h2_s* h, DevBuf<TD>& out, cudaStream_t s) {
+  const TreeHost& T = h->th;
+  const int64_t NN = T.nn();
+  coup_dm_offsets(h);
+  out.alloc(std::max<int64_t>(h->coup_dm_off[NN], 1));
+  std::vector<CopyDM<TD>> cps;
+  int64_t maxe = 1;
+  for (int64_t i = 0; i < NN; ++i) {
+    const int ki = h->rank(i);
+    if (ki == 0) continue;
+    int64_t col = 0;
+    for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
+      const int64_t j = T.far_idx[e];
+      const int kj = h->rank(j);
+      if (kj == 0) continue;
+      CopyDM<TD> c;
+      c.src = h->coup.p + h->far_boff[e];
+      c.trans = h->far_trans[e];
+      c.lds = c.trans ? kj : ki;
+      c.dst = out.p + h->coup_dm_off[i] + col * ki;
+      c.ldd = ki;
+      c.m = ki;
+      c.n = kj;
+      cps.push_back(c);
+      maxe = std::max<int64_t>(maxe, (int64_t)ki * kj);
+      col += kj;
+    }
+  }
+  for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
+    std::vector<CopyDM<TD>> part(cps.begin() + b0, cps.begin() + std::min(cps.size(), b0 + 65535));
+    DevBuf<CopyDM<TD>> dp;
+    dp.upload(part, s);
+    const int gx = (int)std::min<int64_t>(ceil_div(maxe, 256), 16);
+    k_copy_dm<TD><<<dim3(gx, (unsigned)part.size()), 256, 0, s>>>(dp.p);
+    SPD_LAUNCHED();
+    SPD_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+// The destination-major coupling step of plan p (one streaming problem per node).
+template <class T>
+static void rowcoup_plan(const spdhss_h2_s* h, H2PlanT<T>& p, int ncol, const T* A,
+                         cudaStream_t s) {
+  const TreeHost& T_ = h->th;
+  const int64_t K = std::max<int64_t>(h->Ktot, 1);
+  RowCoupBatchT<T>& rb = p.rowcoup;
+  rb.ncol = ncol;
+  rb.tag = sizeof(T) == 4 ? "h2_coupling_f32" : "h2_coupling";
+  for (int64_t i = 0; i < T_.nn(); ++i) {
+    const int ki = h->rank(i);
+    if (ki == 0 || T_.far_off[i] == T_.far_off[i + 1]) continue;
+    RowCoupProbT<T> pr;
+    pr.C = p.yhat.p + h->skel_off[i];
+    pr.ldc = K;
+    pr.M = ki;
+    pr.ncol = ncol;
+    pr.A = A + h->coup_dm_off[i];
+    pr.ch0 = (int)rb.chunks.size();
+    int64_t col = 0;
+    for (int64_t e = T_.far_off[i]; e < T_.far_off[i + 1]; ++e) {
+      const int64_t j = T_.far_idx[e];
+      const int kj = h->rank(j);
+      for (int k0 = 0; k0 < kj; k0 += kRowChunk)
+        rb.chunks.push_back(RowCoupChunkT<T>{p.xhat.p + h->skel_off[j] + k0, K, col + k0,
+                                             std::min(kRowChunk, kj - k0)});
+      col += kj;
+    }
+    pr.ch1 = (int)rb.chunks.size();
+    rb.probs.push_back(pr);
+  }
+  rb.upload(s);
+  p.use_rowcoup = true;
+  p.coupling = GemmBatchT<T>();
+}
+
+void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStream_t s) {
+  // Few columns: the coupling step streams the destination-major FP64 copy (each entry read
+  // once, coalesced, spread over many CTAs); the grouped GEMM would give every node one CTA
+  // with a long serial loop over its partners.  The copy is made on first use and kept.
+  if (nslot == 1 && ncol <= 4) {
+    spdhss_h2_s* hm = const_cast<spdhss_h2_s*>(h);   // a cache of the handle
+    if (hm->coup_dd.n == 0) coup_dm_build<double>(hm, hm->coup_dd, s);
+    h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, nullptr, s);
+    rowcoup_plan<double>(h, p, ncol, h->coup_dd.p, s);
+    SPD_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, h->coup.p, s);
 }
 
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
-  const TreeHost& T = h->th;
   if (h->basis_f.n == 0) {
     h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
     convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
-    // destination-major FP32 couplings
-    const int64_t NN = T.nn();
-    h->coup_fd_off.assign(NN + 1, 0);
-    for (int64_t i = 0; i < NN; ++i) {
-      int64_t kt = 0;
-      if (h->rank(i) > 0)
-        for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) kt += h->rank(T.far_idx[e]);
-      h->coup_fd_off[i + 1] = h->coup_fd_off[i] + (int64_t)h->rank(i) * kt;
-    }
-    h->coup_fd.alloc(std::max<int64_t>(h->coup_fd_off[NN], 1));
-    std::vector<CopyD2F> cps;
-    int64_t maxe = 1;
-    for (int64_t i = 0; i < NN; ++i) {
-      const int ki = h->rank(i);
-      if (ki == 0) continue;
-      int64_t col = 0;
-      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
-        const int64_t j = T.far_idx[e];
-        const int kj = h->rank(j);
-        if (kj == 0) continue;
-        CopyD2F c;
-        c.src = h->coup.p + h->far_boff[e];
-        c.trans = h->far_trans[e];
-        c.lds = c.trans ? kj : ki;
-        c.dst = h->coup_fd.p + h->coup_fd_off[i] + col * ki;
-        c.ldd = ki;
-        c.m = ki;
-        c.n = kj;
-        cps.push_back(c);
-        maxe = std::max<int64_t>(maxe, (int64_t)ki * kj);
-        col += kj;
-      }
-    }
-    for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
-      std::vector<CopyD2F> part(cps.begin() + b0, cps.begin() + std::min(cps.size(), b0 + 65535));
-      DevBuf<CopyD2F> dp;
-      dp.upload(part, s);
-      const int gx = (int)std::min<int64_t>(ceil_div(maxe, 256), 16);
-      k_copy_d2f<<<dim3(gx, (unsigned)part.size()), 256, 0, s>>>(dp.p);
-      SPD_LAUNCHED();
-      SPD_CUDA(cudaStreamSynchronize(s));
-    }
+    coup_dm_build<float>(h, h->coup_fd, s);
   }
   auto it = h->plans_f.find(ncol);
   if (it == h->plans_f.end()) {
     std::unique_ptr<H2PlanF> p(new H2PlanF());
     h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, nullptr, s);
-    // coupling: one streaming problem per destination node
-    const int64_t K = std::max<int64_t>(h->Ktot, 1);
-    RowCoupBatch& rb = p->rowcoup;
-    rb.ncol = ncol;
-    for (int64_t i = 0; i < T.nn(); ++i) {
-      const int ki = h->rank(i);
-      if (ki == 0 || T.far_off[i] == T.far_off[i + 1]) continue;
-      RowCoupProb pr;
-      pr.C = p->yhat.p + h->skel_off[i];
-      pr.ldc = K;
-      pr.M = ki;
-      pr.ncol = ncol;
-      pr.A = h->coup_fd.p + h->coup_fd_off[i];
-      pr.ch0 = (int)rb.chunks.size();
-      int64_t col = 0;
-      for (int64_t e = T.far_off[i]; e < T.far_off[i + 1]; ++e) {
-        const int64_t j = T.far_idx[e];
-        const int kj = h->rank(j);
-        for (int k0 = 0; k0 < kj; k0 += kRowChunk)
-          rb.chunks.push_back(RowCoupChunk{p->xhat.p + h->skel_off[j] + k0, K, col + k0,
-                                           std::min(kRowChunk, kj - k0)});
-        col += kj;
-      }
-      pr.ch1 = (int)rb.chunks.size();
-      rb.probs.push_back(pr);
-    }
-    rb.upload(s);
-    p->use_rowcoup = true;
-    p->coupling = GemmBatchT<float>();
+    rowcoup_plan<float>(h, *p, ncol, h->coup_fd.p, s);
     SPD_CUDA(cudaStreamSynchronize(s));
     it = h->plans_f.emplace(ncol, std::move(p)).first;
   }

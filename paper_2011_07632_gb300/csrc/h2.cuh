@@ -10,21 +10,24 @@
 
 namespace spd {
 
-// FP32 couplings in destination-major form: node i owns one column-major k_i x (sum of its
-// far partners' ranks) matrix [B_ij1 B_ij2 ...], so the coupling step of the FP32 product
+// Couplings in destination-major form (FP32 copies for the mixed-precision products, FP64
+// copies for products with at most 4 columns): node i owns one column-major
+// k_i x (sum of its far partners' ranks) matrix [B_ij1 B_ij2 ...], so the coupling step
 // streams every entry exactly once and coalesced.  The columns are cut into chunks of at
 // most 64 that stay within one partner; the CTA of a node stages the x^_j pieces of a few
 // chunks in shared memory and each thread accumulates one row over its chunks.
-struct RowCoupProb {
-  float* C;          // y^_i (k_i x ncol, ld ldc)
+template <class T>
+struct RowCoupProbT {
+  T* C;              // y^_i (k_i x ncol, ld ldc)
   int64_t ldc;
   int M;             // k_i
   int ncol;
-  const float* A;    // k_i x (sum k_j), ld k_i
+  const T* A;        // k_i x (sum k_j), ld k_i
   int ch0, ch1;      // chunk range
 };
-struct RowCoupChunk {
-  const float* x;    // x^_j rows [kk0, kk0 + K) (ld ldx)
+template <class T>
+struct RowCoupChunkT {
+  const T* x;        // x^_j rows [kk0, kk0 + K) (ld ldx)
   int64_t ldx;
   int64_t col;       // first column of the chunk in A
   int K;             // <= 64
@@ -40,17 +43,19 @@ struct RowCoupRed {
   int64_t part0;
   int nparts;
 };
-struct RowCoupBatch {
-  std::vector<RowCoupProb> probs;
-  std::vector<RowCoupChunk> chunks;
+template <class T>
+struct RowCoupBatchT {
+  std::vector<RowCoupProbT<T>> probs;
+  std::vector<RowCoupChunkT<T>> chunks;
   std::vector<RowCoupWork> work;
   std::vector<RowCoupRed> red;
-  DevBuf<RowCoupProb> d_probs;
-  DevBuf<RowCoupChunk> d_chunks;
+  DevBuf<RowCoupProbT<T>> d_probs;
+  DevBuf<RowCoupChunkT<T>> d_chunks;
   DevBuf<RowCoupWork> d_work;
   DevBuf<RowCoupRed> d_red;
-  DevBuf<float> partial;          // nparts x NC x 256
+  DevBuf<T> partial;          // nparts x NC x 256
   int ncol = 1;
+  const char* tag = "h2_coupling";
   double flops = 0.0, bytes = 0.0;
   void upload(cudaStream_t s);
   void launch(cudaStream_t s) const;
@@ -64,7 +69,7 @@ struct RowCoupBatch {
 // FP32 kernel entries, FP32 accumulation).
 template <class T>
 struct H2PlanT {
-  RowCoupBatch rowcoup;   // FP32 plans: the coupling step (replaces `coupling`)
+  RowCoupBatchT<T> rowcoup;   // destination-major coupling step (replaces `coupling`)
   bool use_rowcoup = false;
   int ncol = 0;      // columns per slot
   int nslot = 1;
@@ -102,8 +107,11 @@ struct spdhss_h2_s {
   std::map<int, std::unique_ptr<spd::H2Plan>> plans;   // by nrhs
   // FP32 copies of the generators for the mixed-precision products (made on first use)
   spd::DevBuf<float> basis_f;
-  spd::DevBuf<float> coup_fd;                 // destination-major FP32 couplings
-  std::vector<int64_t> coup_fd_off;           // per node: offset of its coupling matrix
+  // destination-major couplings (made on first use): FP32 and FP64 copies, and per node the
+  // offset of its coupling matrix in them
+  spd::DevBuf<float> coup_fd;
+  spd::DevBuf<double> coup_dd;
+  std::vector<int64_t> coup_dm_off;
   std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
 
   int rank(int64_t i) const { return (int)(skel_off[i + 1] - skel_off[i]); }

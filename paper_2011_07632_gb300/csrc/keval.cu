@@ -404,13 +404,28 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   if (mx <= 16) cb = -(mx <= 1 ? 1 : (mx <= 2 ? 2 : (mx <= 4 ? 4 : (mx <= 8 ? 8 : 16))));
   else cb = 64;
   const int step = cb < 0 ? -cb : cb;
-  // split the segments of few-column problems when there are too few CTAs for the GPU
+  // the problems as launched: the many-column kernel takes 32 rows per CTA, so its
+  // problems are cut into 32-row blocks (disjoint output rows)
+  exec_probs.clear();
+  if (cb > 0) {
+    for (const auto& P : probs)
+      for (int rb = 0; rb < P.rows; rb += 32) {
+        NearProbT<T> q = P;
+        q.row0 = P.row0 + rb;
+        q.rows = std::min(32, P.rows - rb);
+        q.out = P.out + rb;
+        exec_probs.push_back(q);
+      }
+  } else {
+    exec_probs = probs;
+  }
+  // split the segments when there are too few CTAs for the GPU
   parts = 1;
   part_probs.clear();
   red.clear();
-  if (cb < 0 && !probs.empty()) {
+  if (!exec_probs.empty()) {
     int64_t ctas = 0, maxseg = 1;
-    for (const auto& p : probs) {
+    for (const auto& p : exec_probs) {
       ctas += (p.ncol + step - 1) / step;
       maxseg = std::max<int64_t>(maxseg, p.seg1 - p.seg0);
     }
@@ -419,8 +434,8 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   }
   if (parts > 1) {
     int64_t off = 0;
-    for (int p = 0; p < (int)probs.size(); ++p) {
-      const NearProbT<T>& P = probs[p];
+    for (int p = 0; p < (int)exec_probs.size(); ++p) {
+      const NearProbT<T>& P = exec_probs[p];
       const int ns = P.seg1 - P.seg0;
       const int np = std::min(parts, std::max(ns, 1));
       const int64_t tot = (int64_t)P.rows * P.ncol;
@@ -442,7 +457,7 @@ void NearBatchT<T>::upload(cudaStream_t s) {
     int64_t o2 = 0;
     size_t k = 0;
     for (size_t r = 0; r < red.size(); ++r) {
-      const NearProbT<T>& P = probs[red[r].x];
+      const NearProbT<T>& P = exec_probs[red[r].x];
       const int64_t tot = (int64_t)P.rows * P.ncol;
       for (int q = 0; q < red[r].z; ++q, ++k) part_probs[k].out = scratch.p + o2 + (int64_t)q * tot;
       o2 += tot * red[r].z;
@@ -450,7 +465,7 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   }
   flops = 0.0;
   evals = 0.0;
-  const std::vector<NearProbT<T>>& wp = parts > 1 ? part_probs : probs;
+  const std::vector<NearProbT<T>>& wp = parts > 1 ? part_probs : exec_probs;
   for (int p = 0; p < (int)wp.size(); ++p)
     for (int c0 = 0; c0 < wp[p].ncol; c0 += step) work.push_back(make_int2(p, c0));
   for (int p = 0; p < (int)probs.size(); ++p) {
@@ -460,7 +475,7 @@ void NearBatchT<T>::upload(cudaStream_t s) {
       flops += 2.0 * e * probs[p].ncol;
     }
   }
-  d_probs.upload(probs, s);
+  d_probs.upload(exec_probs, s);
   d_segs.upload(segs, s);
   d_work.upload(work, s);
   if (parts > 1) {

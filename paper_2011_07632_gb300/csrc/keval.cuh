@@ -83,7 +83,8 @@ template <class T>
 struct NearBatchT {
   std::vector<NearProbT<T>> probs;
   std::vector<NearSegT<T>> segs;
-  std::vector<int2> work;   // (prob, first column)
+  std::vector<int2> work;   // (prob, first column) over the launched problems
+  std::vector<NearProbT<T>> exec_probs;   // the problems as launched (d_probs)
   DevBuf<NearProbT<T>> d_probs;
   DevBuf<NearSegT<T>> d_segs;
   DevBuf<int2> d_work;

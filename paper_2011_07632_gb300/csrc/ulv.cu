@@ -320,9 +320,98 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
   }
 }
 
+// F_i and B_i for every node and the root's explicit triangular inverses: the forward and
+// backward steps of the solve applied to identity matrices, with the batched kernels of the
+// factorization (the same operations as a solve, with m_i columns).
+static void ulv_explicit(spdhss_ulv_s* u, cudaStream_t s) {
+  if (!u->Foff.empty()) return;
+  const TreeHost& T = u->hs->h2->th;
+  const int64_t NN = T.nn();
+  u->Foff.assign(NN + 1, 0);
+  for (int64_t i = 0; i < NN; ++i) {
+    const int64_t m = (T.depth_of(i) == 0) ? 0 : u->m[i];
+    u->Foff[i + 1] = u->Foff[i] + m * m;
+  }
+  u->Fbuf.alloc(std::max<int64_t>(u->Foff[NN], 1));
+  u->Bbuf.alloc(std::max<int64_t>(u->Foff[NN], 1));
+  Batch<CopyProb> id;
+  Batch<HhApplyProb> qt, q;
+  Batch<TrsmProb> fw, bk;
+  GemmBatch uf, ub;
+  for (int64_t i = 0; i < NN; ++i) {
+    const int m = (T.depth_of(i) == 0) ? 0 : u->m[i];
+    if (m == 0) continue;
+    const int r = u->r[i];
+    double* F = u->Fbuf.p + u->Foff[i];
+    double* B = u->Bbuf.p + u->Foff[i];
+    double* Di = u->Dbuf.p + u->Doff[i];
+    for (double* X : {F, B}) {
+      CopyProb c{};
+      c.src = nullptr; c.lds = m; c.dst = X; c.ldd = m; c.m = m; c.n = m; c.alpha = 1.0;
+      id.push(c);
+    }
+    if (r > 0) {
+      HhApplyProb hp;
+      hp.V = u->Wbuf.p + u->Woff[i]; hp.ldv = m; hp.tau = u->taub.p + u->toff[i];
+      hp.k = u->rdev.p + i; hp.m = m; hp.ncol = m;
+      hp.B = F; hp.ldb = m;
+      qt.push(hp);
+      hp.B = B;
+      q.push(hp);
+    }
+    if (m - r > 0) {
+      fw.push(TrsmProb{Di + r + (int64_t)r * m, m, F + r, m, m - r, m, 1, 0});
+      bk.push(TrsmProb{Di + r + (int64_t)r * m, m, B + r, m, m - r, m, 1, 1});
+      if (r > 0) {
+        uf.add(F, m, r, m, Di + r, m, 1, F + r, m, 0, m - r, -1.0, 1.0);
+        ub.add(B + r, m, m - r, m, Di + r, m, 0, B, m, 0, r, -1.0, 1.0);
+      }
+    }
+  }
+  id.upload(s);
+  identity_launch(id, s);
+  // forward: Q^T, complement solve, kept rows
+  qt.tag = q.tag = "hh_ulv_explicit";
+  qt.upload(s);
+  householder_launch(qt, 1, s);
+  fw.tag = bk.tag = "trsm_ulv_explicit";
+  fw.upload(s);
+  trsm_launch(fw, s);
+  uf.tag = ub.tag = "gemm_ulv_explicit";
+  uf.run(s);
+  // backward: kept rows into the complement, transposed complement solve, Q
+  ub.run(s);
+  bk.upload(s);
+  trsm_launch(bk, s);
+  q.upload(s);
+  householder_launch(q, 0, s);
+  // root: L^{-1} and L^{-T}
+  const int mr = u->mroot;
+  if (mr > 0) {
+    u->rootF.alloc((size_t)mr * mr);
+    u->rootB.alloc((size_t)mr * mr);
+    Batch<CopyProb> ir;
+    for (double* X : {u->rootF.p, u->rootB.p}) {
+      CopyProb c{};
+      c.src = nullptr; c.lds = mr; c.dst = X; c.ldd = mr; c.m = mr; c.n = mr; c.alpha = 1.0;
+      ir.push(c);
+    }
+    ir.upload(s);
+    identity_launch(ir, s);
+    Batch<TrsmProb> rt;
+    rt.push(TrsmProb{u->root.p, mr, u->rootF.p, mr, mr, mr, 1, 0});
+    rt.push(TrsmProb{u->root.p, mr, u->rootB.p, mr, mr, mr, 1, 1});
+    rt.tag = "trsm_ulv_explicit";
+    rt.upload(s);
+    trsm_launch(rt, s);
+  }
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
 UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
   auto it = u->plans.find(ncol);
   if (it != u->plans.end()) return *it->second;
+  ulv_explicit(u, s);
   std::unique_ptr<UlvPlan> pp(new UlvPlan());
   UlvPlan& P = *pp;
   const TreeHost& T = u->hs->h2->th;
@@ -331,102 +420,76 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
   P.ncol = ncol;
   const int nlev = std::max(L - 1, 0);
   P.bw.resize(nlev + 1);
+  P.tw.resize(nlev + 1);
   P.ldk.assign(nlev + 1, 0);
-  P.qt.resize(nlev); P.q.resize(nlev); P.fw.resize(nlev); P.bk.resize(nlev);
-  P.upd_f.resize(nlev); P.upd_b.resize(nlev); P.up.resize(nlev); P.down.resize(nlev);
+  P.fwd.resize(nlev); P.bwd.resize(nlev); P.up.resize(nlev); P.down.resize(nlev);
   // per-level row offsets of every node block
   std::vector<int64_t> moff(T.nn(), 0);
-  if (D == 0) {
-    P.bw[0].alloc((size_t)n * ncol);
-    P.ldk[0] = n;
-    P.root_f.push(TrsmProb{u->root.p, n, P.bw[0].p, n, (int)n, ncol, 1, 0});
-    P.root_b.push(TrsmProb{u->root.p, n, P.bw[0].p, n, (int)n, ncol, 1, 1});
-    P.root_f.upload(s); trsm_prepare(P.root_f, s);
-    P.root_b.upload(s); trsm_prepare(P.root_b, s);
-    SPD_CUDA(cudaStreamSynchronize(s));
-    it = u->plans.emplace(ncol, std::move(pp)).first;
-    return *it->second;
-  }
-  for (int k = 1; k <= L - 1; ++k) {
-    const int t = D + 1 - k;
-    const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
-    int64_t tot = 0;
-    for (int64_t i = o; i < o + nn; ++i) {
-      moff[i] = (k == 1) ? T.begin[i] : tot;
-      tot += u->m[i];
+  if (D > 0) {
+    for (int k = 1; k <= L - 1; ++k) {
+      const int t = D + 1 - k;
+      const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
+      int64_t tot = 0;
+      for (int64_t i = o; i < o + nn; ++i) {
+        moff[i] = (k == 1) ? T.begin[i] : tot;
+        tot += u->m[i];
+      }
+      if (k == 1) tot = n;
+      P.ldk[k - 1] = std::max<int64_t>(tot, 1);
+      P.bw[k - 1].alloc((size_t)P.ldk[k - 1] * ncol);
+      P.tw[k - 1].alloc((size_t)P.ldk[k - 1] * ncol);
     }
-    if (k == 1) tot = n;
-    P.ldk[k - 1] = std::max<int64_t>(tot, 1);
-    P.bw[k - 1].alloc((size_t)P.ldk[k - 1] * ncol);
   }
-  P.ldk[nlev] = std::max(u->mroot, 1);
+  P.ldk[nlev] = (D == 0) ? n : std::max(u->mroot, 1);
   P.bw[nlev].alloc((size_t)P.ldk[nlev] * ncol);
-  for (int k = 1; k <= L - 1; ++k) {
+  P.tw[nlev].alloc((size_t)P.ldk[nlev] * ncol);
+  for (int k = 1; k <= L - 1 && D > 0; ++k) {
     const int t = D + 1 - k;
     const int64_t o = T.depth_off[t], nn = T.depth_off[t + 1] - o;
     const int64_t ld = P.ldk[k - 1];
-    double* bw = P.bw[k - 1].p;
     const int64_t ldn = P.ldk[k];
     double* bn = P.bw[k].p;
     for (int64_t i = o; i < o + nn; ++i) {
       const int m = u->m[i], r = u->r[i];
       if (m == 0) continue;
-      double* blk = bw + moff[i];
-      double* Di = u->Dbuf.p + u->Doff[i];
-      if (r > 0) {
-        HhApplyProb hp;
-        hp.V = u->Wbuf.p + u->Woff[i]; hp.ldv = m; hp.tau = u->taub.p + u->toff[i];
-        hp.k = u->rdev.p + i; hp.B = blk; hp.ldb = ld; hp.m = m; hp.ncol = ncol;
-        P.qt[k - 1].push(hp);
-        P.q[k - 1].push(hp);
-      }
-      if (m - r > 0) {
-        P.fw[k - 1].push(TrsmProb{Di + r + (int64_t)r * m, m, blk + r, ld, m - r, ncol, 1, 0});
-        P.bk[k - 1].push(TrsmProb{Di + r + (int64_t)r * m, m, blk + r, ld, m - r, ncol, 1, 1});
-        if (r > 0) {
-          P.upd_f[k - 1].add(blk, ld, r, ncol, Di + r, m, 1, blk + r, ld, 0, m - r, -1.0, 1.0);
-          P.upd_b[k - 1].add(blk + r, ld, m - r, ncol, Di + r, m, 0, blk, ld, 0, r, -1.0, 1.0);
-        }
-      }
-      // position of i's reduced part inside its parent's block (or the root block)
+      double* blk = P.bw[k - 1].p + moff[i];
+      double* tb = P.tw[k - 1].p + moff[i];
+      P.fwd[k - 1].add(tb, ld, m, ncol, u->Fbuf.p + u->Foff[i], m, 0, blk, ld, 0, m, 1.0, 0.0);
+      P.bwd[k - 1].add(blk, ld, m, ncol, u->Bbuf.p + u->Foff[i], m, 0, tb, ld, 0, m, 1.0, 0.0);
+      // position of i's kept rows inside its parent's block (or the root block)
       if (r > 0) {
         const int64_t par = T.parent[i];
         int64_t pos = 0;
         for (int64_t c = T.child_begin[par]; c < i; ++c) pos += u->r[c];
         const int64_t pbase = (k == L - 1) ? 0 : moff[par];
         CopyProb cu{};
-        cu.src = blk; cu.lds = ld; cu.dst = bn + pbase + pos; cu.ldd = ldn; cu.m = r; cu.n = ncol;
+        cu.src = tb; cu.lds = ld; cu.dst = bn + pbase + pos; cu.ldd = ldn; cu.m = r; cu.n = ncol;
         cu.alpha = 1.0;
         P.up[k - 1].push(cu);
         CopyProb cd{};
-        cd.src = bn + pbase + pos; cd.lds = ldn; cd.dst = blk; cd.ldd = ld; cd.m = r; cd.n = ncol;
+        cd.src = bn + pbase + pos; cd.lds = ldn; cd.dst = tb; cd.ldd = ld; cd.m = r; cd.n = ncol;
         cd.alpha = 1.0;
         P.down[k - 1].push(cd);
       }
     }
   }
-  const int mr = u->mroot;
+  const int mr = (D == 0) ? (int)n : u->mroot;
   if (mr > 0) {
-    P.root_f.push(TrsmProb{u->root.p, mr, P.bw[nlev].p, P.ldk[nlev], mr, ncol, 1, 0});
-    P.root_b.push(TrsmProb{u->root.p, mr, P.bw[nlev].p, P.ldk[nlev], mr, ncol, 1, 1});
+    const int64_t ldr = P.ldk[nlev];
+    P.root_f.add(P.tw[nlev].p, ldr, mr, ncol, u->rootF.p, mr, 0, P.bw[nlev].p, ldr, 0, mr, 1.0, 0.0);
+    P.root_b.add(P.bw[nlev].p, ldr, mr, ncol, u->rootB.p, mr, 0, P.tw[nlev].p, ldr, 0, mr, 1.0, 0.0);
   }
   for (int k = 0; k < nlev; ++k) {
-    P.qt[k].tag = P.q[k].tag = "hh_ulv_solve";
-    P.fw[k].tag = P.bk[k].tag = "trsm_ulv_solve";
+    P.fwd[k].tag = P.bwd[k].tag = "gemm_ulv_solve";
     P.up[k].tag = P.down[k].tag = "copy_ulv_solve";
-    P.qt[k].upload(s); householder_prepare(P.qt[k], s);
-    P.q[k].upload(s); householder_prepare(P.q[k], s);
-    P.fw[k].upload(s); trsm_prepare(P.fw[k], s);
-    P.bk[k].upload(s); trsm_prepare(P.bk[k], s);
-    P.upd_f[k].tag = P.upd_b[k].tag = "ulv_solve_gemm";
-    P.upd_f[k].upload(s);
-    P.upd_b[k].upload(s);
+    P.fwd[k].upload(s);
+    P.bwd[k].upload(s);
     P.up[k].upload(s);
     P.down[k].upload(s);
   }
-  P.root_f.tag = P.root_b.tag = "trsm_ulv_root";
-  P.root_f.upload(s); trsm_prepare(P.root_f, s);
-  P.root_b.upload(s); trsm_prepare(P.root_b, s);
+  P.root_f.tag = P.root_b.tag = "gemm_ulv_root";
+  P.root_f.upload(s);
+  P.root_b.upload(s);
   SPD_CUDA(cudaStreamSynchronize(s));
   it = u->plans.emplace(ncol, std::move(pp)).first;
   return *it->second;
@@ -435,18 +498,14 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
 void ulv_solve_sorted(const spdhss_ulv_s* u, const UlvPlan& P, cudaStream_t s) {
   const int nlev = std::max(u->L - 1, 0);
   for (int k = 0; k < nlev; ++k) {
-    householder_launch(P.qt[k], 1, s);
-    trsm_launch(P.fw[k], s);
-    P.upd_f[k].launch(s);
+    P.fwd[k].launch(s);
     copy_launch(P.up[k], s);
   }
-  trsm_launch(P.root_f, s);
-  trsm_launch(P.root_b, s);
+  P.root_f.launch(s);
+  P.root_b.launch(s);
   for (int k = nlev - 1; k >= 0; --k) {
     copy_launch(P.down[k], s);
-    P.upd_b[k].launch(s);
-    trsm_launch(P.bk[k], s);
-    householder_launch(P.q[k], 0, s);
+    P.bwd[k].launch(s);
   }
 }
 

@@ -6,16 +6,20 @@
 namespace spd {
 
 // Solve plan for a fixed number of right-hand sides; works in place on bw[0] (the leaf
-// level buffer, sorted order, ld n).
+// level buffer, sorted order, ld n).  Every node's forward step (Q_i^T, the complement
+// solve, the update of the kept rows) is one explicit m_i x m_i matrix F_i, and its
+// backward step (the update from the parent's solution, the transposed complement solve,
+// Q_i) another, B_i (both made once per factorization by running those steps on the
+// identity); the root's solves are the explicit inverses of its Cholesky factor and of
+// its transpose.  A solve is then two grouped GEMMs and two copies per level, spread over
+// the whole GPU, instead of dependent chains of reflectors and substitutions.
 struct UlvPlan {
   int ncol = 0;
-  std::vector<DevBuf<double>> bw;            // per level 1..L-1 (index k-1), plus the root
+  std::vector<DevBuf<double>> bw, tw;        // per level 1..L-1 (index k-1), plus the root
   std::vector<int64_t> ldk;                  // leading dimension per level buffer
-  std::vector<Batch<HhApplyProb>> qt, q;     // per level: Q^T / Q on every node block
-  std::vector<Batch<TrsmProb>> fw, bk;       // per level: L_q^{-1}, L_q^{-T}
-  std::vector<GemmBatch> upd_f, upd_b;       // per level: b_p -= X^T y_q ; y_q -= X x_p
-  std::vector<Batch<CopyProb>> up, down;     // per level: reduced parts to / from the parent
-  Batch<TrsmProb> root_f, root_b;
+  std::vector<GemmBatch> fwd, bwd;           // per level: t = F_i b ; b = B_i t
+  std::vector<Batch<CopyProb>> up, down;     // per level: kept rows to / from the parent
+  GemmBatch root_f, root_b;                  // t = L^{-1} b ; b = L^{-T} t
 };
 
 }  // namespace spd
@@ -29,6 +33,9 @@ struct spdhss_ulv_s {
   spd::DevBuf<int> rdev;                     // per node reflector counts (device)
   int mroot = 0;
   spd::DevBuf<double> root;                  // Cholesky factor of the root block
+  // explicit per-node solve matrices (see UlvPlan), made on the first solve plan
+  std::vector<int64_t> Foff;
+  spd::DevBuf<double> Fbuf, Bbuf, rootF, rootB;
   std::map<int, std::unique_ptr<spd::UlvPlan>> plans;
   size_t stored_bytes() const { return Dbuf.bytes() + Wbuf.bytes() + taub.bytes() + Ubuf.bytes() + root.bytes(); }
 };
