@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
         Bs[kk][nn] = v;
       }
       __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < GK; ++kk) {
+      const int kc = min(GK, S.K - k0);   // no FMA on the padding of a short segment
+#pragma unroll 4
+      for (int kk = 0; kk < kc; ++kk) {
         T a[4], b[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= P.N) continue;
-      T* c = P.C + gm + (int64_t)gn * P.ldc;
+      T* c = P.tC ? P.C + gn + (int64_t)gm * P.ldc : P.C + gm + (int64_t)gn * P.ldc;
       T v = (T)P.alpha * acc[i][j];
       if (P.beta != 0.0) v += (T)P.beta * (*c);
       *c = v;
@@ -135,8 +136,9 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
         Bs[kk][nn] = v;
       }
       __syncthreads();
+      const int kc = min(KB, S.K - k0);   // no FMA on the padding of a short segment
 #pragma unroll 8
-      for (int kk = 0; kk < KB; ++kk) {
+      for (int kk = 0; kk < kc; ++kk) {
         const T a = As[kk][row];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) acc[c] = fmaT(a, Bs[kk][cg * CPT + c], acc[c]);
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
     for (int c = 0; c < CPT; ++c) {
       const int gn = n0 + cg * CPT + c;
       if (gn < P.N) {
-        T* cp = P.C + gm + (int64_t)gn * P.ldc;
+        T* cp = P.tC ? P.C + gn + (int64_t)gm * P.ldc : P.C + gm + (int64_t)gn * P.ldc;
         T v = (T)P.alpha * acc[c];
         if (P.beta != 0.0) v += (T)P.beta * (*cp);
         *cp = v;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
     const int4 kp = kparts[t.w - 1];
     klo = kp.x;
     khi = kp.y;
-    pout = partial + (int64_t)kp.z * (NB * MB);
+    pout = partial + (int64_t)kp.z * (4 * MB);   // slots have the 4-column stride
   }
   __shared__ T As[KB][MB + 1];
   __shared__ T Bs[KB][NB];
@@ -217,9 +219,11 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
         Bs[kk][nn] = v;
       }
       __syncthreads();
+      const int kc = min(KB, ke - k0);   // no FMA on the padding of a short segment
 #pragma unroll
       for (int q = 0; q < KB / 4; ++q) {
         const int kk = kg * (KB / 4) + q;
+        if (kk >= kc) break;
         const T a = As[kk][row];
 #pragma unroll
         for (int c = 0; c < NB; ++c) acc[c] = fmaT(a, Bs[kk][c], acc[c]);
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
         const int gn = n0 + c;
         if (gn < P.N) {
           const T v0 = (red[0][c][row] + red[1][c][row]) + (red[2][c][row] + red[3][c][row]);
-          T* cp = P.C + gm + (int64_t)gn * P.ldc;
+          T* cp = P.tC ? P.C + gn + (int64_t)gm * P.ldc : P.C + gm + (int64_t)gn * P.ldc;
           T v = (T)P.alpha * v0;
           if (P.beta != 0.0) v += (T)P.beta * (*cp);
           *cp = v;
@@ -267,9 +271,9 @@ __global__ void __launch_bounds__(64) k_gemm_kreduce(const GemmProbT<T>* __restr
   for (int c = 0; c < NB; ++c) {
     const int gn = r.z + c;
     if (gn >= P.N) break;
-    T v0 = partial[(int64_t)r.w * (NB * MB) + c * MB + row];
-    for (int q = 1; q < np; ++q) v0 += partial[(int64_t)(r.w + q) * (NB * MB) + c * MB + row];
-    T* cp = P.C + gm + (int64_t)gn * P.ldc;
+    T v0 = partial[(int64_t)r.w * (4 * MB) + c * MB + row];
+    for (int q = 1; q < np; ++q) v0 += partial[(int64_t)(r.w + q) * (4 * MB) + c * MB + row];
+    T* cp = P.tC ? P.C + gn + (int64_t)gm * P.ldc : P.C + gm + (int64_t)gn * P.ldc;
     T v = (T)P.alpha * v0;
     if (P.beta != 0.0) v += (T)P.beta * (*cp);
     *cp = v;
@@ -301,57 +305,113 @@ static void gemm_dispatch(int nb, int g, const GemmProbT<T>* pr, const GemmSegT<
   }
 }
 
+// tile footprint of a variant: rows x columns per CTA
+static inline void gemm_tile_shape(int nb, int* tm, int* tn) {
+  *tm = 64;
+  *tn = nb ? nb : 64;
+}
+
+// fraction of the tile FMAs that are not padding for an M x N product on variant nb
+static inline double gemm_fill(int M, int N, int nb) {
+  int tm, tn;
+  gemm_tile_shape(nb, &tm, &tn);
+  const double tiles = (double)((M + tm - 1) / tm) * (double)((N + tn - 1) / tn);
+  return tiles > 0 ? (double)M * N / (tiles * tm * tn) : 1.0;
+}
+
 template <class T>
 void GemmBatchT<T>::upload(cudaStream_t s) {
   tiles.clear();
+  lprobs.clear();
+  lsegs.clear();
+  vnb.clear();
+  vbeg.clear();
   flops = 0.0;
   bytes = 0.0;
   int maxn = 0;
   for (const auto& p : probs) maxn = std::max(maxn, p.N);
   nb = gemm_variant(maxn);
-  const int tm = nb ? 64 : GM, tn = nb ? nb : GN;
+  // orientation and variant of every problem
+  std::vector<int> pv(probs.size());
   for (int p = 0; p < (int)probs.size(); ++p) {
-    for (int m0 = 0; m0 < probs[p].M; m0 += tm)
-      for (int n0 = 0; n0 < probs[p].N; n0 += tn) tiles.push_back(make_int4(p, m0, n0, 0));
+    const GemmProbT<T>& P = probs[p];
     double kk = 0.0;
-    for (int g = probs[p].seg0; g < probs[p].seg1; ++g) {
+    for (int g = P.seg0; g < P.seg1; ++g) {
       kk += segs[g].K;
-      bytes += sizeof(T) * ((double)probs[p].M * segs[g].K + (double)segs[g].K * probs[p].N);
+      bytes += sizeof(T) * ((double)P.M * segs[g].K + (double)segs[g].K * P.N);
     }
-    flops += 2.0 * probs[p].M * (double)probs[p].N * kk;
-    bytes += sizeof(T) * (double)probs[p].M * probs[p].N * (probs[p].beta != 0.0 ? 2.0 : 1.0);
+    flops += 2.0 * P.M * (double)P.N * kk;
+    bytes += sizeof(T) * (double)P.M * P.N * (P.beta != 0.0 ? 2.0 : 1.0);
+    const int v = gemm_variant(P.N), vt = gemm_variant(P.M);
+    const bool tr = gemm_fill(P.N, P.M, vt) > 2.0 * gemm_fill(P.M, P.N, v);
+    GemmProbT<T> q = P;
+    q.seg0 = (int)lsegs.size();
+    for (int g = P.seg0; g < P.seg1; ++g) {
+      GemmSegT<T> sg = segs[g];
+      if (tr) {   // C^T = B^T A^T
+        GemmSegT<T> t2 = sg;
+        t2.A = sg.B; t2.lda = sg.ldb; t2.tA = !sg.tB;
+        t2.B = sg.A; t2.ldb = sg.lda; t2.tB = !sg.tA;
+        sg = t2;
+      }
+      lsegs.push_back(sg);
+    }
+    q.seg1 = (int)lsegs.size();
+    if (tr) { q.M = P.N; q.N = P.M; q.tC = !P.tC; }
+    lprobs.push_back(q);
+    pv[p] = tr ? vt : v;
   }
-  // matrix-vector-like products on too few tiles to fill the GPU: split the K range of each
-  // tile over several CTAs (partial sums, added in order by k_gemm_kreduce)
+  // tiles grouped by variant
+  static const int kVariants[7] = {1, 2, 4, 8, 16, 32, 0};
   kparts.clear();
   reds.clear();
   rednp.clear();
-  if (nb >= 1 && nb <= 4 && !tiles.empty() && (int64_t)tiles.size() < 2 * 152) {
-    const int want = (int)std::min<int64_t>(16, ceil_div(4 * 152, (int64_t)tiles.size()));
-    std::vector<int4> nt;
-    int slot = 0;
-    for (const int4& t : tiles) {
-      int K = 0;
-      for (int g = probs[t.x].seg0; g < probs[t.x].seg1; ++g) K += segs[g].K;
-      const int kp = std::min(want, (K + 127) / 128);
-      if (kp <= 1) { nt.push_back(t); continue; }
-      reds.push_back(make_int4(t.x, t.y, t.z, slot));
-      rednp.push_back(kp);
-      for (int q = 0; q < kp; ++q) {
-        const int lo = (int)((int64_t)K * q / kp), hi = (int)((int64_t)K * (q + 1) / kp);
-        kparts.push_back(make_int4(lo, hi, slot + q, 0));
-        nt.push_back(make_int4(t.x, t.y, t.z, (int)kparts.size()));
-      }
-      slot += kp;
+  int slot = 0;
+  for (int v : kVariants) {
+    std::vector<int4> vt;
+    int tm, tn;
+    gemm_tile_shape(v, &tm, &tn);
+    for (int p = 0; p < (int)lprobs.size(); ++p) {
+      if (pv[p] != v) continue;
+      for (int m0 = 0; m0 < lprobs[p].M; m0 += tm)
+        for (int n0 = 0; n0 < lprobs[p].N; n0 += tn) vt.push_back(make_int4(p, m0, n0, 0));
     }
-    tiles.swap(nt);
+    if (vt.empty()) continue;
+    // matrix-vector-like products on too few tiles to fill the GPU: split the K range of
+    // each tile over several CTAs (partial sums, added in order by k_gemm_kreduce)
+    if (v >= 1 && v <= 4 && (int64_t)vt.size() < 2 * 152) {
+      const int want = (int)std::min<int64_t>(16, ceil_div(4 * 152, (int64_t)vt.size()));
+      std::vector<int4> nt;
+      for (const int4& t : vt) {
+        int K = 0;
+        for (int g = lprobs[t.x].seg0; g < lprobs[t.x].seg1; ++g) K += lsegs[g].K;
+        const int kp = std::min(want, (K + 127) / 128);
+        if (kp <= 1) { nt.push_back(t); continue; }
+        reds.push_back(make_int4(t.x, t.y, t.z, slot));
+        rednp.push_back(kp);
+        for (int q = 0; q < kp; ++q) {
+          const int lo = (int)((int64_t)K * q / kp), hi = (int)((int64_t)K * (q + 1) / kp);
+          kparts.push_back(make_int4(lo, hi, slot + q, 0));
+          nt.push_back(make_int4(t.x, t.y, t.z, (int)kparts.size()));
+        }
+        slot += kp;
+      }
+      vt.swap(nt);
+    }
+    vnb.push_back(v);
+    vbeg.push_back((int64_t)tiles.size());
+    tiles.insert(tiles.end(), vt.begin(), vt.end());
+  }
+  vbeg.push_back((int64_t)tiles.size());
+  if (!reds.empty()) {
     d_kparts.upload(kparts, s);
     d_reds.upload(reds, s);
     d_rednp.upload(rednp, s);
-    d_partial.alloc(std::max(slot, 1) * (size_t)nb * 64);
+    // slots are sized for the widest split variant (4 columns)
+    d_partial.alloc(std::max(slot, 1) * (size_t)4 * 64);
   }
-  d_segs.upload(segs, s);
-  d_probs.upload(probs, s);
+  d_segs.upload(lsegs, s);
+  d_probs.upload(lprobs, s);
   d_tiles.upload(tiles, s);
 }
 
@@ -393,18 +453,17 @@ void GemmBatchT<T>::launch(cudaStream_t s) const {
   const int64_t nt = (int64_t)tiles.size();
   if (nt == 0) return;
   ProfScope ps(tag, s, flops, bytes);
-  for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
-    const int g = (int)std::min<int64_t>(nt - b0, 2147483647LL);
-    gemm_dispatch<T>(nb, g, d_probs.p, d_segs.p, d_tiles.p + b0, s, d_kparts.p, d_partial.p);
-    SPD_LAUNCHED();
+  for (size_t v = 0; v < vnb.size(); ++v) {
+    for (int64_t b0 = vbeg[v]; b0 < vbeg[v + 1]; b0 += 2147483647LL) {
+      const int g = (int)std::min<int64_t>(vbeg[v + 1] - b0, 2147483647LL);
+      gemm_dispatch<T>(vnb[v], g, d_probs.p, d_segs.p, d_tiles.p + b0, s, d_kparts.p, d_partial.p);
+      SPD_LAUNCHED();
+    }
   }
   if (!reds.empty()) {
-    const unsigned g = (unsigned)reds.size();
-    switch (nb) {
-      case 1: k_gemm_kreduce<T, 1><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
-      case 2: k_gemm_kreduce<T, 2><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
-      default: k_gemm_kreduce<T, 4><<<g, 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p, d_partial.p); break;
-    }
+    // the reduction reads the slots with the 4-column stride used for every split variant
+    k_gemm_kreduce<T, 4><<<(unsigned)reds.size(), 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p,
+                                                                d_partial.p);
     SPD_LAUNCHED();
   }
 }

@@ -25,6 +25,7 @@ struct GemmProbT {
   int M, N;
   int seg0, seg1;
   double alpha, beta;
+  int tC = 0;   // 1: the product is stored transposed, (m, n) at C[n + m * ldc]
 };
 using GemmSeg = GemmSegT<double>;
 using GemmProb = GemmProbT<double>;
@@ -59,9 +60,16 @@ struct GemmBatchT {
   void launch(cudaStream_t s) const;
   void run(cudaStream_t s) { upload(s); launch(s); }
   void clear() { segs.clear(); probs.clear(); tiles.clear(); kparts.clear(); reds.clear(); rednp.clear(); }
-  std::vector<int4> tiles;   // (prob, m0, n0, 0)
+  std::vector<int4> tiles;   // (prob, m0, n0, K part + 1 or 0), grouped by kernel variant
   const char* tag = "gemm";
   int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
+  // launched problems: every problem in the orientation (C or C^T = B^T A^T) that wastes
+  // the fewest padded FMAs, grouped by the kernel variant of its column count; one launch
+  // per variant over the tile range [vbeg[v], vbeg[v + 1])
+  std::vector<GemmProbT<T>> lprobs;
+  std::vector<GemmSegT<T>> lsegs;
+  std::vector<int> vnb;
+  std::vector<int64_t> vbeg;
   double flops = 0.0, bytes = 0.0;   // algorithmic work of one launch
   DevBuf<GemmSegT<T>> d_segs;
   DevBuf<GemmProbT<T>> d_probs;

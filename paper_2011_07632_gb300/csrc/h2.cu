@@ -344,6 +344,44 @@ static int lca_level(const TreeHost& T, int64_t i, int64_t j) {
   return T.level_of_depth(T.depth_of(i));
 }
 
+// Near blocks are stored (instead of evaluated in every product) when they take at most
+// this many bytes: every later product then reads them once instead of spending ~40 FP64
+// operations per entry on the kernel function.
+constexpr int64_t kNearStoreBytes = int64_t(16) << 30;
+
+static bool near_store(spdhss_h2_s* h, cudaStream_t s) {
+  if (h->near_state) return h->near_state == 1;
+  const TreeHost& T = h->th;
+  const int D = T.D;
+  h->near_boff.assign(T.near_idx.size(), 0);
+  int64_t tot = 0;
+  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i)
+    for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
+      h->near_boff[e] = tot;
+      tot += T.size(i) * T.size(T.near_idx[e]);
+    }
+  if (tot * (int64_t)sizeof(double) > kNearStoreBytes) {
+    h->near_state = 2;
+    return false;
+  }
+  h->near_blk.alloc(std::max<int64_t>(tot, 1));
+  Batch<TileProb> tb;
+  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i)
+    for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
+      const int64_t j = T.near_idx[e];
+      TileProb tp;
+      tp.xr = h->td.xs.p; tp.ldxr = T.n; tp.r0 = T.begin[i]; tp.rows = (int)T.size(i);
+      tp.xc = h->td.xs.p; tp.ldxc = T.n; tp.c0 = T.begin[j]; tp.cols = (int)T.size(j);
+      tp.out = h->near_blk.p + h->near_boff[e]; tp.ldo = T.size(i);
+      tp.diag_add = (i == j) ? h->kfn.shift : 0.0;
+      tb.push(tp);
+    }
+  tb.upload(s);
+  tile_launch(tb, h->kfn, T.dim, s);
+  h->near_state = 1;
+  return true;
+}
+
 template <class F>
 static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int nslot,
                             const F* Ub, const F* Cb, cudaStream_t s) {
@@ -418,9 +456,65 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
     if (h->rank(i) > 0)
       p.leaf_out.seg(U(i), h->U_rows[i], 0, p.yhat.p + h->skel_off[i], K, 0, h->rank(i));
   }
-  // near field
+  // near field: grouped GEMMs over the stored blocks (FP64), else evaluated on the fly
   p.near = NearBatchT<F>();
-  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
+  p.near_g = GemmBatchT<F>();
+  p.near_stored = false;
+  if constexpr (std::is_same<F, double>::value) {
+    if (near_store(const_cast<spdhss_h2_s*>(h), s)) {   // the blocks are a cache of the handle
+      p.near_stored = true;
+      p.near_rows = (nslot == 1 && ncol <= 4);
+      if (p.near_rows) {
+        // each leaf's blocks form one |I_i| x sum |I_j| row block: stream it like the couplings
+        RowCoupBatchT<F>& rb = p.near_r;
+        rb.ncol = ncol;
+        rb.tag = "near_h2_stored";
+        for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
+          if (T.near_off[i] == T.near_off[i + 1] || T.size(i) == 0) continue;
+          RowCoupProbT<F> pr;
+          pr.C = p.ys.p + T.begin[i];
+          pr.ldc = n;
+          pr.M = (int)T.size(i);
+          pr.ncol = ncol;
+          pr.A = h->near_blk.p + h->near_boff[T.near_off[i]];
+          pr.beta = 1;
+          pr.ch0 = (int)rb.chunks.size();
+          int64_t col = 0;
+          for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
+            const int64_t j = T.near_idx[e];
+            const int sj = (int)T.size(j);
+            for (int k0 = 0; k0 < sj; k0 += kRowChunk)
+              rb.chunks.push_back(RowCoupChunkT<F>{p.xs.p + T.begin[j] + k0, n, col + k0,
+                                                   std::min(kRowChunk, sj - k0)});
+            col += sj;
+          }
+          pr.ch1 = (int)rb.chunks.size();
+          rb.probs.push_back(pr);
+        }
+        rb.upload(s);
+      }
+      for (int64_t i = T.depth_off[D]; !p.near_rows && i < T.depth_off[D + 1]; ++i) {
+        for (int sl = 0; sl < nslot; ++sl) {
+          bool opened = false;
+          for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
+            const int64_t j = T.near_idx[e];
+            if (nslot > 1) {
+              if (j == i) continue;
+              if (lca_level(T, i, j) - 2 != sl) continue;
+            }
+            if (!opened) {
+              p.near_g.prob(p.ys.p + T.begin[i] + (int64_t)sl * ncol * n, n, (int)T.size(i),
+                            ncol, 1.0, 1.0);
+              opened = true;
+            }
+            p.near_g.seg(h->near_blk.p + h->near_boff[e], T.size(i), 0, p.xs.p + T.begin[j], n,
+                         0, (int)T.size(j));
+          }
+        }
+      }
+    }
+  }
+  for (int64_t i = T.depth_off[D]; !p.near_stored && i < T.depth_off[D + 1]; ++i) {
     for (int sl = 0; sl < nslot; ++sl) {
       bool opened = false;
       for (int64_t e = T.near_off[i]; e < T.near_off[i + 1]; ++e) {
@@ -441,6 +535,8 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   const bool f32 = sizeof(F) == 4;
   p.coupling.tag = nslot > 1 ? "h2_coupling_sample" : (f32 ? "h2_coupling_f32" : "h2_coupling");
   p.near.tag = nslot > 1 ? "near_sample" : (f32 ? "near_h2_f32" : "near_h2");
+  p.near_g.tag = nslot > 1 ? "near_sample_stored" : "near_h2_stored";
+  p.near_g.upload(s);
   const char* btag = f32 ? "h2_basis_f32" : "h2_basis";
   p.up_leaf.tag = p.leaf_out.tag = btag;
   for (auto& g : p.up) g.tag = btag;
@@ -506,7 +602,6 @@ __global__ void k_copy_dm(const CopyDM<TD>* __restrict__ probs) {
 // its chunks.  With Mw warps of rows, the CTA holds G = 8 / Mw groups; in round t group g
 // takes chunk t * G + g.  Partial sums of the groups are added in group order, and the
 // parts of a node split over several CTAs are added in part order (deterministic).
-constexpr int kRowChunk = 64;
 // coupling entries per CTA: about total / (152 SMs x 16), within [4096, 2^20], so that small
 // products still spread over many CTAs and large ones keep long streams
 constexpr int64_t kRowItemMax = int64_t(1) << 20;
@@ -616,7 +711,10 @@ __global__ void __launch_bounds__(256) k_coupling_rows(const RowCoupProbT<T>* __
     if (W.part < 0) {
 #pragma unroll
       for (int c = 0; c < NC; ++c)
-        if (c < ncl) P.C[r + (int64_t)(c0 + c) * P.ldc] = acc[c];
+        if (c < ncl) {
+          T* cp = P.C + r + (int64_t)(c0 + c) * P.ldc;
+          *cp = P.beta ? *cp + acc[c] : acc[c];
+        }
     } else {
       T* pt = partial + W.part * (NC * 256);
 #pragma unroll
@@ -638,7 +736,8 @@ __global__ void __launch_bounds__(256) k_coupling_rows_reduce(const RowCoupProbT
   for (int c = 0; c < ncl; ++c) {
     T v = T(0);
     for (int q = 0; q < R.nparts; ++q) v += partial[(R.part0 + q) * (NC * 256) + c * 256 + rl];
-    P.C[R.r0 + rl + (int64_t)(c0 + c) * P.ldc] = v;
+    T* cp = P.C + R.r0 + rl + (int64_t)(c0 + c) * P.ldc;
+    *cp = P.beta ? *cp + v : v;
   }
 }
 
@@ -907,7 +1006,9 @@ static void h2_plan_run_t(const spdhss_h2_s* h, const H2PlanT<T>& p, cudaStream_
   else p.coupling.launch(s);
   for (const auto& g : p.down) g.launch(s);
   p.leaf_out.launch(s);
-  p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);
+  if (p.near_rows) p.near_r.launch(s);
+  else if (p.near_stored) p.near_g.launch(s);
+  else p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);
 }
 
 void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s) { h2_plan_run_t(h, p, s); }

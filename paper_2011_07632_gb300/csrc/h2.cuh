@@ -16,6 +16,8 @@ namespace spd {
 // streams every entry exactly once and coalesced.  The columns are cut into chunks of at
 // most 64 that stay within one partner; the CTA of a node stages the x^_j pieces of a few
 // chunks in shared memory and each thread accumulates one row over its chunks.
+constexpr int kRowChunk = 64;   // columns per chunk
+
 template <class T>
 struct RowCoupProbT {
   T* C;              // y^_i (k_i x ncol, ld ldc)
@@ -24,6 +26,7 @@ struct RowCoupProbT {
   int ncol;
   const T* A;        // k_i x (sum k_j), ld k_i
   int ch0, ch1;      // chunk range
+  int beta = 0;      // 1: add to C instead of overwriting it
 };
 template <class T>
 struct RowCoupChunkT {
@@ -80,6 +83,9 @@ struct H2PlanT {
   std::vector<GemmBatchT<T>> down;     // per depth 1 .. D-1
   GemmBatchT<T> leaf_out;
   NearBatchT<T> near;
+  GemmBatchT<T> near_g;     // the near field from the stored blocks (replaces `near`)
+  RowCoupBatchT<T> near_r;  // ... streamed row by row for at most 4 columns
+  bool near_stored = false, near_rows = false;
 };
 using H2Plan = H2PlanT<double>;
 using H2PlanF = H2PlanT<float>;
@@ -105,6 +111,13 @@ struct spdhss_h2_s {
   spd::DevBuf<double> coup;
   int max_rank = 0;
   std::map<int, std::unique_ptr<spd::H2Plan>> plans;   // by nrhs
+  // near-field blocks K(X_i, X_j) (+ shift on the diagonal) of every leaf near pair, stored
+  // on the first FP64 product when they fit kNearStoreBytes: per near-list entry the
+  // offset of its |I_i| x |I_j| block; the blocks of leaf i are consecutive (one
+  // |I_i| x sum |I_j| column-major row block)
+  std::vector<int64_t> near_boff;
+  spd::DevBuf<double> near_blk;
+  int near_state = 0;   // 0: not decided, 1: stored, 2: evaluated on the fly
   // FP32 copies of the generators for the mixed-precision products (made on first use)
   spd::DevBuf<float> basis_f;
   // destination-major couplings (made on first use): FP32 and FP64 copies, and per node the
