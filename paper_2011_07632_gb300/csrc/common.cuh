@@ -41,9 +41,12 @@ struct ProfScope {
 
 // Householder QR flops for k steps on an m x n matrix: per step, every trailing column
 // takes a dot product and an update (4 flops per entry) and a recomputed norm (2 flops).
+// Householder QR, k steps on m x n: per step the reflector (3 (m - j)) and its application
+// to the n - j - 1 trailing columns (4 (m - j) each); column norms are downdated (O(n)).
 inline double qr_flops(int64_t m, int64_t n, int64_t k, bool pivot) {
+  (void)pivot;
   double f = 0.0;
-  for (int64_t j = 0; j < k; ++j) f += (double)(m - j) * (double)(n - j - 1) * (pivot ? 6.0 : 4.0);
+  for (int64_t j = 0; j < k; ++j) f += (double)(m - j) * (4.0 * (double)(n - j - 1) + 3.0);
   return f;
 }
 

@@ -984,6 +984,23 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Column norms are downdated after every step, |a_p(j+1:)|^2 = |a_p(j:)|^2 - R_jp^2, and
+// recomputed from the column when cancellation makes the downdate unreliable: when
+// (1 - (R_jp/vn1)^2) (vn1/vn2)^2 falls to sqrt(eps) or below, vn2 being the norm at the
+// last recomputation (the safeguard of LAPACK's column-pivoted QR, Drmac and Bujanovic).
+// Returns 1 when the caller must recompute vn1 = vn2 = |a_p(j+1:)|.
+constexpr double kQrTol3z = 1.0536712127723509e-08;   // sqrt(2^-53)
+
+__device__ __forceinline__ int qr_downdate(double rjp, double& vn1, double vn2) {
+  if (vn1 == 0.0) return 0;
+  double t = fabs(rjp) / vn1;
+  t = fmax(1.0 - t * t, 0.0);
+  const double r = vn1 / vn2;
+  if (t * r * r <= kQrTol3z) return 1;
+  vn1 *= sqrt(t);
+  return 0;
+}
+
 __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs, int pivot) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -1012,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
       double s = 0.0;
       for (int i = lane; i < m; i += 32) { const double a = A[i + (int64_t)p * ld]; s += a * a; }
       s = warp_sum(s);
-      if (lane == 0) { P.norms[p] = sqrt(s); P.piv[p] = p; }
+      if (lane == 0) { P.norms[p] = sqrt(s); P.norms[n + p] = P.norms[p]; P.piv[p] = p; }
     }
   }
   __threadfence();
@@ -1069,6 +1086,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
         if (threadIdx.x == 0) {
           const int tp = P.piv[j]; P.piv[j] = P.piv[pc]; P.piv[pc] = tp;
           const double tn = P.norms[j]; P.norms[j] = P.norms[pc]; P.norms[pc] = tn;
+          const double t2 = P.norms[n + j]; P.norms[n + j] = P.norms[n + pc]; P.norms[n + pc] = t2;
         }
       }
       __syncthreads();
@@ -1107,34 +1125,45 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
     for (int i = threadIdx.x; i < len; i += blockDim.x)
       s_v[i] = (i == 0) ? 1.0 : A[j + i + (int64_t)j * ld];
     __syncthreads();
-    if (tau != 0.0) {
+    {
       int t = 0;
       for (int p = first_owned(j + 1); p < n; p += C, ++t) {
         if (t % nw != warp) continue;
         double* col = A + j + (int64_t)p * ld;
-        double w = 0.0;
-        for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
-        w = warp_sum(w) * tau;
-        double s = 0.0;
-        for (int i = lane; i < len; i += 32) {
-          const double a = col[i] - w * s_v[i];
-          col[i] = a;
-          if (i > 0) s += a * a;
+        if (tau != 0.0) {
+          double w = 0.0;
+          for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
+          w = warp_sum(w) * tau;
+          if (pivot && !P.downdate) {   // update and recompute the norm in one pass
+            double s = 0.0;
+            for (int i = lane; i < len; i += 32) {
+              const double a = col[i] - w * s_v[i];
+              col[i] = a;
+              if (i > 0) s += a * a;
+            }
+            s = warp_sum(s);
+            if (lane == 0) P.norms[p] = sqrt(s);
+            continue;
+          }
+          for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
         }
         if (pivot) {
-          s = warp_sum(s);
-          if (lane == 0) P.norms[p] = sqrt(s);
+          int rc = 1;
+          if (P.downdate) {
+            if (lane == 0) {
+              double v1 = P.norms[p];
+              rc = qr_downdate(col[0], v1, P.norms[n + p]);
+              P.norms[p] = v1;
+            }
+            rc = __shfl_sync(0xffffffffu, rc, 0);
+          }
+          if (rc) {
+            double s = 0.0;
+            for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
+            s = warp_sum(s);
+            if (lane == 0) { P.norms[p] = sqrt(s); P.norms[n + p] = P.norms[p]; }
+          }
         }
-      }
-    } else if (pivot) {
-      int t = 0;
-      for (int p = first_owned(j + 1); p < n; p += C, ++t) {
-        if (t % nw != warp) continue;
-        const double* col = A + j + (int64_t)p * ld;
-        double s = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
-        s = warp_sum(s);
-        if (lane == 0) P.norms[p] = sqrt(s);
       }
     }
     __threadfence();
@@ -1158,7 +1187,7 @@ constexpr size_t kQrSmemBudget = 200 * 1024;
 
 struct QrSmemLayout {
   int nown, ldm;
-  size_t cols, norms, pos2col, col2pos, v, total;
+  size_t cols, norms, norms2, pos2col, col2pos, v, total;
 };
 __host__ __device__ inline QrSmemLayout qr_smem_layout(int m, int n, int C) {
   QrSmemLayout L;
@@ -1166,7 +1195,8 @@ __host__ __device__ inline QrSmemLayout qr_smem_layout(int m, int n, int C) {
   L.ldm = m + (m & 1);
   L.cols = 0;
   L.norms = L.cols + (size_t)L.nown * L.ldm * sizeof(double);
-  L.pos2col = L.norms + (size_t)L.nown * sizeof(double);
+  L.norms2 = L.norms + (size_t)L.nown * sizeof(double);
+  L.pos2col = L.norms2 + (size_t)L.nown * sizeof(double);
   L.col2pos = L.pos2col + (size_t)n * sizeof(int);
   L.v = (L.col2pos + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
   L.total = L.v + (size_t)L.ldm * sizeof(double);
@@ -1182,7 +1212,8 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
   extern __shared__ __align__(16) unsigned char smem_qr[];
   const QrSmemLayout Ly = qr_smem_layout(mmax, nmax, C);
   double* cols = reinterpret_cast<double*>(smem_qr + Ly.cols);
-  double* norms = reinterpret_cast<double*>(smem_qr + Ly.norms);
+  double* norms = reinterpret_cast<double*>(smem_qr + Ly.norms);     // downdated norms
+  double* norms2 = reinterpret_cast<double*>(smem_qr + Ly.norms2);   // at the last recompute
   int* pos2col = reinterpret_cast<int*>(smem_qr + Ly.pos2col);
   int* col2pos = reinterpret_cast<int*>(smem_qr + Ly.col2pos);
   double* s_v = reinterpret_cast<double*>(smem_qr + Ly.v);   // the reflector, m - j entries
@@ -1208,7 +1239,7 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
       s += a * a;
     }
     s = warp_sum(s);
-    if (lane == 0) norms[t] = sqrt(s);
+    if (lane == 0) { norms[t] = sqrt(s); norms2[t] = norms[t]; }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) { pos2col[i] = i; col2pos[i] = i; }
   cl.sync();
@@ -1307,19 +1338,29 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
         double w = 0.0;
         for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
         w = warp_sum(w) * tau;
-        double s = 0.0;
-        for (int i = lane; i < len; i += 32) {
-          const double a = col[i] - w * s_v[i];
-          col[i] = a;
-          if (i > 0) s += a * a;
+        if (!P.downdate) {   // update and recompute the norm in one pass
+          double s = 0.0;
+          for (int i = lane; i < len; i += 32) {
+            const double a = col[i] - w * s_v[i];
+            col[i] = a;
+            if (i > 0) s += a * a;
+          }
+          s = warp_sum(s);
+          if (lane == 0) norms[t] = sqrt(s);
+          continue;
         }
-        s = warp_sum(s);
-        if (lane == 0) norms[t] = sqrt(s);
-      } else {
+        for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
+      }
+      int rc = 1;
+      if (P.downdate) {
+        if (lane == 0) rc = qr_downdate(col[0], norms[t], norms2[t]);
+        rc = __shfl_sync(0xffffffffu, rc, 0);
+      }
+      if (rc) {
         double s = 0.0;
         for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
         s = warp_sum(s);
-        if (lane == 0) norms[t] = sqrt(s);
+        if (lane == 0) { norms[t] = sqrt(s); norms2[t] = norms[t]; }
       }
     }
     __syncthreads();

@@ -142,7 +142,9 @@ struct QrProb {
   int* piv;       // n entries (may be null when pivot == 0)
   double* tau;    // kmax entries
   int* rank;      // 1 entry
-  double* norms;  // n entries of scratch
+  double* norms;  // 2n entries of scratch (downdated norms, norms at the last recompute)
+  int downdate = 1;   // 0: recompute every remaining norm at every step (nearly full-rank
+                      //    matrices, where downdates would be recomputed anyway)
 };
 // returns the profiler record of the launch (-1 when profiling is off); the caller adds
 // the flops with prof_add_flops once the ranks are known

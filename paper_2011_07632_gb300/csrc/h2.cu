@@ -132,7 +132,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
         coff[b + 1] = coff[b] + m;
         maxm = std::max(maxm, m);
       }
-      DevBuf<double> G(goff[nb]), tau(coff[nb]), norms(coff[nb]);
+      DevBuf<double> G(goff[nb]), tau(coff[nb]), norms(2 * coff[nb]);
       DevBuf<int> piv(coff[nb]), rk(nb);
       Batch<ProxyProb> pb;
       Batch<QrProb> qb;
@@ -164,7 +164,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
         q.A = G.p + goff[b]; q.lda = np; q.m = np; q.n = mrows[i];
         q.kmax = std::min(np, mrows[i]); q.rtol = h->tol;
         q.piv = piv.p + coff[b]; q.tau = tau.p + coff[b]; q.rank = rk.p + b;
-        q.norms = norms.p + coff[b];
+        q.norms = norms.p + 2 * coff[b];
         qb.push(q);
       }
       pb.upload(s);

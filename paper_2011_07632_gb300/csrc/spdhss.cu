@@ -186,7 +186,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
     DevBuf<double> F(std::max<int64_t>(mmo[nn], 1));      // S_i or L_i
     DevBuf<double> W(std::max<int64_t>(wo[nn], 1));       // nonleaf: Lambda_i, all pending slots
     DevBuf<double> Q(std::max<int64_t>(qo[nn], 1));       // QR workspace (m x s)
-    DevBuf<double> tau(std::max<int64_t>(mo[nn], 1)), norms(std::max<int64_t>(nn * sc, 1));
+    DevBuf<double> tau(std::max<int64_t>(mo[nn], 1)), norms(std::max<int64_t>(2 * nn * sc, 1));
     DevBuf<int> piv(std::max<int64_t>(nn * sc, 1)), rkd(std::max<int64_t>(nn, 1));
 
     // (a) factor the diagonal blocks
@@ -304,7 +304,8 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         q.A = Q.p + qo[a]; q.lda = std::max(m, 1); q.m = m; q.n = sc;
         q.kmax = std::min(r, std::min(m, sc)); q.rtol = 1e-14;
         q.piv = piv.p + a * sc; q.tau = tau.p + mo[a]; q.rank = rkd.p + a;
-        q.norms = norms.p + a * sc;
+        q.norms = norms.p + 2 * a * sc;
+        q.downdate = 0;   // sketches are close to full rank: every norm would be recomputed
         qb.push(q);
       }
       cb.upload(s); copy_launch(cb, s);
