@@ -1001,6 +1001,22 @@ __device__ __forceinline__ int qr_downdate(double rjp, double& vn1, double vn2) 
   return 0;
 }
 
+// v^T col over rows [0, len) by one warp: four independent partial sums (rows l, l + 32,
+// l + 64, l + 96 of every 128), so that four loads are in flight per lane
+__device__ __forceinline__ double warp_dot4(const double* __restrict__ v,
+                                            const double* __restrict__ col, int len, int lane) {
+  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+  int i = lane;
+  for (; i + 96 < len; i += 128) {
+    w0 = fma(v[i], col[i], w0);
+    w1 = fma(v[i + 32], col[i + 32], w1);
+    w2 = fma(v[i + 64], col[i + 64], w2);
+    w3 = fma(v[i + 96], col[i + 96], w3);
+  }
+  for (; i < len; i += 32) w0 = fma(v[i], col[i], w0);
+  return warp_sum((w0 + w1) + (w2 + w3));
+}
+
 __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs, int pivot) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -1131,9 +1147,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
         if (t % nw != warp) continue;
         double* col = A + j + (int64_t)p * ld;
         if (tau != 0.0) {
-          double w = 0.0;
-          for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
-          w = warp_sum(w) * tau;
+          const double w = warp_dot4(s_v, col, len, lane) * tau;
           if (pivot && !P.downdate) {   // update and recompute the norm in one pass
             double s = 0.0;
             for (int i = lane; i < len; i += 32) {
@@ -1145,6 +1159,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
             if (lane == 0) P.norms[p] = sqrt(s);
             continue;
           }
+#pragma unroll 4
           for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
         }
         if (pivot) {
@@ -1335,9 +1350,7 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
       if (col2pos[q + t * C] <= j) continue;
       double* col = cols + (int64_t)t * ldm + j;
       if (tau != 0.0) {
-        double w = 0.0;
-        for (int i = lane; i < len; i += 32) w += s_v[i] * col[i];
-        w = warp_sum(w) * tau;
+        const double w = warp_dot4(s_v, col, len, lane) * tau;
         if (!P.downdate) {   // update and recompute the norm in one pass
           double s = 0.0;
           for (int i = lane; i < len; i += 32) {
@@ -1349,6 +1362,7 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
           if (lane == 0) norms[t] = sqrt(s);
           continue;
         }
+#pragma unroll 4
         for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
       }
       int rc = 1;
