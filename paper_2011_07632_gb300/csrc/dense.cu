@@ -1133,7 +1133,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
       __syncthreads();
       const double scale = s_scale;
       for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + (int64_t)j * ld] *= scale;
-      __threadfence();
+      if (C > 1) __threadfence();
     }
     cl.sync();
     const double tau = P.tau[j];
@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
         }
       }
     }
-    __threadfence();
+    if (C > 1) __threadfence();   // peers read the updated columns from global memory
     cl.sync();
   }
   if (q == 0 && threadIdx.x == 0) *P.rank = j;
@@ -1218,6 +1218,14 @@ __host__ __device__ inline QrSmemLayout qr_smem_layout(int m, int n, int C) {
   return L;
 }
 
+template <int LPC>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+  for (int o = LPC / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <int LPC>
 __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ probs, int mmax,
                                                     int nmax) {
   cg::cluster_group cl = cg::this_cluster();
@@ -1346,35 +1354,54 @@ __global__ void __launch_bounds__(256) k_geqp3_smem(const QrProb* __restrict__ p
     }
     __syncthreads();
     const double tau = s_wv[1];
-    for (int t = warp; t < nown; t += nw) {
-      if (col2pos[q + t * C] <= j) continue;
-      double* col = cols + (int64_t)t * ldm + j;
-      if (tau != 0.0) {
-        const double w = warp_dot4(s_v, col, len, lane) * tau;
+    // LPC lanes per column, 32 / LPC columns per warp at a time: short columns spend their
+    // FP64 issue on the products rather than on reduction trees
+    constexpr int G = 32 / LPC;
+    const int g = lane / LPC, sl = lane % LPC;
+    const unsigned FULL = 0xffffffffu;
+    for (int t0 = warp * G; t0 < nown; t0 += nw * G) {
+      const int t = t0 + g;
+      const bool act = t < nown && col2pos[q + min(t, nown - 1) * C] > j;
+      double* col = cols + (int64_t)min(t, nown - 1) * ldm + j;
+      double w = 0.0;
+      if (act && tau != 0.0) {
+        double w0 = 0.0, w1 = 0.0;
+        int i = sl;
+        for (; i + LPC < len; i += 2 * LPC) {
+          w0 = fma(s_v[i], col[i], w0);
+          w1 = fma(s_v[i + LPC], col[i + LPC], w1);
+        }
+        if (i < len) w0 = fma(s_v[i], col[i], w0);
+        w = w0 + w1;
+      }
+      w = group_sum<LPC>(w) * tau;
+      double s = 0.0;
+      if (act && tau != 0.0) {
         if (!P.downdate) {   // update and recompute the norm in one pass
-          double s = 0.0;
-          for (int i = lane; i < len; i += 32) {
+          for (int i = sl; i < len; i += LPC) {
             const double a = col[i] - w * s_v[i];
             col[i] = a;
             if (i > 0) s += a * a;
           }
-          s = warp_sum(s);
-          if (lane == 0) norms[t] = sqrt(s);
-          continue;
-        }
+        } else {
 #pragma unroll 4
-        for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
+          for (int i = sl; i < len; i += LPC) col[i] -= w * s_v[i];
+        }
       }
       int rc = 1;
-      if (P.downdate) {
-        if (lane == 0) rc = qr_downdate(col[0], norms[t], norms2[t]);
-        rc = __shfl_sync(0xffffffffu, rc, 0);
+      if (P.downdate || tau == 0.0) {
+        if (P.downdate) {
+          rc = 0;
+          if (act && sl == 0) rc = qr_downdate(col[0], norms[t], norms2[t]);
+          rc = __shfl_sync(FULL, rc, g * LPC);
+        }
+        if (act && rc)
+          for (int i = 1 + sl; i < len; i += LPC) s += col[i] * col[i];
       }
-      if (rc) {
-        double s = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
-        s = warp_sum(s);
-        if (lane == 0) { norms[t] = sqrt(s); norms2[t] = norms[t]; }
+      s = group_sum<LPC>(s);
+      if (act && sl == 0 && rc) {
+        norms[t] = sqrt(s);
+        if (P.downdate) norms2[t] = norms[t];
       }
     }
     __syncthreads();
@@ -1448,7 +1475,11 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
       const size_t sm = qr_smem_layout(mmax, nmax, C).total;
       static std::once_flag once_s;
       std::call_once(once_s, [] {
-        cudaFuncSetAttribute(k_geqp3_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_geqp3_smem<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kQrSmemBudget);
+        cudaFuncSetAttribute(k_geqp3_smem<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kQrSmemBudget);
+        cudaFuncSetAttribute(k_geqp3_smem<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kQrSmemBudget);
       });
       cudaLaunchConfig_t cfg = {};
@@ -1464,7 +1495,13 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       ProfScope ps(b.tag ? b.tag : "geqp3", s);
-      SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem, (const QrProb*)b.d.p, mmax, nmax));
+      // lanes per column: rows per lane at least 8 where the columns are short
+      if (mmax <= 64)
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<8>, (const QrProb*)b.d.p, mmax, nmax));
+      else if (mmax <= 128)
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<16>, (const QrProb*)b.d.p, mmax, nmax));
+      else
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<32>, (const QrProb*)b.d.p, mmax, nmax));
       SPD_LAUNCHED();
       return ps.slot;
     }
