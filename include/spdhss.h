@@ -221,8 +221,9 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
  *   instance's status (spdhss_last_error names it).  The caller destroys the handles.
  * pcg_solve_batched: pcg_solve for every instance (B[i], X[i]: n_i x nrhs[i], ld[i];
  *   iters_out[i] / relres_out[i]: HOST arrays of nrhs[i] entries or NULL), the iterations
- *   of all instances in lockstep (an instance leaves when it has converged).  status[i]
- *   per instance (NO_CONVERGENCE for one that missed the tolerance). */
+ *   of all instances in lockstep from one host thread: every stage of an iteration is one
+ *   launch over all instances still iterating (an instance leaves when it has converged).
+ *   status[i] per instance (NO_CONVERGENCE for one that missed the tolerance). */
 spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,

@@ -379,6 +379,10 @@ void pcg_impl(const spdhss_h2_s* h2, spdhss_ulv_s* u, const double* B, double* X
               bool& converged, cudaStream_t s, int precision = 0, int refresh = 50);
 void h2_matmul_mixed_impl(spdhss_h2_s* h2, const double* X, double* Y, int nrhs, int64_t ld,
                           cudaStream_t s);
+void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ulv,
+                      const double* const* B, double* const* X, const int* nrhs,
+                      const int64_t* ld, double tol, int maxit, int* const* iters_out,
+                      double* const* relres_out, spdhss_status* status, cudaStream_t s);
 }
 
 extern "C" {
@@ -576,16 +580,21 @@ spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle
     SPD_REQUIRE(h2 && ulv && B && X && nrhs && ld, "NULL argument");
     SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
     SPD_REQUIRE(maxit >= 1, "maxit must be >= 1");
-    run_batched(count, s, st, msg, [&](int i) {
+    StreamScope ss(s);
+    st.assign(count, SPDHSS_OK);
+    msg.assign(count, std::string());
+    for (int i = 0; i < count; ++i) {
       SPD_REQUIRE(h2[i] && ulv[i] && B[i] && X[i], "NULL argument");
       SPD_REQUIRE(ulv[i]->hs->h2 == h2[i], "the ULV factorization belongs to another H2 matrix");
       SPD_REQUIRE(nrhs[i] >= 1, "nrhs must be >= 1");
       SPD_REQUIRE(ld[i] >= h2[i]->th.n, "ld must be >= n");
-      bool conv = false;
-      pcg_impl(h2[i], ulv[i], B[i], X[i], nrhs[i], ld[i], relres_tol, maxit,
-               iters_out ? iters_out[i] : nullptr, relres_out ? relres_out[i] : nullptr, conv, s);
-      if (!conv) throw Error(SPDHSS_NO_CONVERGENCE, "some column missed the tolerance");
-    });
+    }
+    std::vector<spdhss_h2_s*> hv(h2, h2 + count);
+    std::vector<spdhss_ulv_s*> uv(ulv, ulv + count);
+    pcg_batched_impl(count, hv.data(), uv.data(), B, X, nrhs, ld, relres_tol, maxit, iters_out,
+                     relres_out, st.data(), s);
+    for (int i = 0; i < count; ++i)
+      if (st[i] == SPDHSS_NO_CONVERGENCE) msg[i] = "some column missed the tolerance";
   });
   if (outer != SPDHSS_OK) return outer;
   return batched_result("pcg_solve_batched", st, msg, status);

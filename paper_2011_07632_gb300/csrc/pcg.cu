@@ -401,3 +401,370 @@ void h2_matmul_mixed_impl(spdhss_h2_s* h2, const double* X, double* Y, int nrhs,
 }
 
 }  // namespace spd
+
+// ---------------------------------------------------------------------------------------
+// PCG for many independent instances in lockstep, driven by one host thread: every stage
+// of an iteration (each level of the H^2 passes, the coupling and near-field steps, each
+// level of the ULV solve, the dots and vector updates) is one launch over the problems of
+// all active instances, concatenated from the instances' own plans whenever the active
+// set changes.  The recurrences, the true-residual confirmation and the residual
+// replacement are those of pcg_impl, per instance and per column.
+// ---------------------------------------------------------------------------------------
+namespace spd {
+namespace {
+
+void gemm_cat(GemmBatch& out, const GemmBatch& in) {
+  const int off = (int)out.segs.size();
+  out.segs.insert(out.segs.end(), in.segs.begin(), in.segs.end());
+  for (GemmProb p : in.probs) {
+    p.seg0 += off;
+    p.seg1 += off;
+    out.probs.push_back(p);
+  }
+}
+
+void rowcoup_cat(RowCoupBatchT<double>& out, const RowCoupBatchT<double>& in) {
+  const int off = (int)out.chunks.size();
+  out.chunks.insert(out.chunks.end(), in.chunks.begin(), in.chunks.end());
+  for (RowCoupProbT<double> p : in.probs) {
+    p.ch0 += off;
+    p.ch1 += off;
+    out.probs.push_back(p);
+  }
+  out.ncol = std::max(out.ncol, in.ncol);
+}
+
+struct Inst {
+  spdhss_h2_s* h2 = nullptr;
+  spdhss_ulv_s* u = nullptr;
+  H2Plan* PA = nullptr;
+  H2Plan* PR = nullptr;
+  UlvPlan* PU = nullptr;
+  int64_t n = 0, ld = 0;
+  int nrhs = 0, D = 0, nlev = 0;
+  const double* B = nullptr;
+  double* X = nullptr;
+  DevBuf<double> bs, x, r, part;
+  int64_t so = 0;             // offset of this instance's columns in the scalar pools
+  std::vector<double> bn;
+  std::vector<int> hdone, hit;
+  bool active = true;
+};
+
+// scalar pools: rz | pq | rzn | rr, NC entries each (NC = all columns of all instances)
+struct Pools {
+  int64_t NC = 0;
+  DevBuf<double> sc;
+  DevBuf<int> done;
+  double* rz(const Inst& a) const { return sc.p + a.so; }
+  double* pq(const Inst& a) const { return sc.p + NC + a.so; }
+  double* rzn(const Inst& a) const { return sc.p + 2 * NC + a.so; }
+  double* rr(const Inst& a) const { return sc.p + 3 * NC + a.so; }
+  int* dn(const Inst& a) const { return done.p + a.so; }
+};
+
+struct Merged {
+  GemmBatch up_leaf, leaf_out, near_g, coupling, root_f, root_b;
+  std::vector<GemmBatch> up, down, fwd, bwd;
+  RowCoupBatchT<double> rowcoup, near_r;
+  Batch<CopyProb> zero_yhat, z_from_r, rz_from_rzn;
+  std::vector<Batch<CopyProb>> uup, udown;
+  std::vector<DotProb> d_pq, d_rr, d_rz;
+  std::vector<VecProb> v_axpy, v_upd;
+  std::vector<int> near_direct;   // instances whose near field is evaluated on the fly
+};
+
+CopyProb vcopy(double* dst, const double* src, int64_t count) {
+  CopyProb c{};
+  c.src = src; c.lds = count; c.dst = dst; c.ldd = count; c.m = (int)count; c.n = 1;
+  c.alpha = 1.0;
+  return c;
+}
+
+void build_merged(std::vector<Inst>& I, const Pools& pl, Merged& M, cudaStream_t s) {
+  M = Merged();
+  int maxD = 0, maxlev = 0;
+  for (auto& a : I)
+    if (a.active) { maxD = std::max(maxD, a.D); maxlev = std::max(maxlev, a.nlev); }
+  M.up.resize(std::max(maxD - 1, 0));
+  M.down.resize(std::max(maxD - 1, 0));
+  M.fwd.resize(maxlev);
+  M.bwd.resize(maxlev);
+  M.uup.resize(maxlev);
+  M.udown.resize(maxlev);
+  for (int k = 0; k < (int)I.size(); ++k) {
+    Inst& a = I[k];
+    if (!a.active) continue;
+    const H2Plan& P = *a.PA;
+    const int64_t nc = a.n * a.nrhs;
+    gemm_cat(M.up_leaf, P.up_leaf);
+    for (size_t h = 0; h < P.up.size(); ++h) gemm_cat(M.up[h], P.up[h]);
+    // down[t] is depth t + 1, at height nd - t above the leaves; merged top first
+    const int nd = (int)P.down.size();
+    for (int t = 0; t < nd; ++t) gemm_cat(M.down[(maxD - 1) - (nd - t)], P.down[t]);
+    gemm_cat(M.leaf_out, P.leaf_out);
+    if (P.use_rowcoup) rowcoup_cat(M.rowcoup, P.rowcoup);
+    else gemm_cat(M.coupling, P.coupling);
+    if (P.near_rows) rowcoup_cat(M.near_r, P.near_r);
+    else if (P.near_stored) gemm_cat(M.near_g, P.near_g);
+    else M.near_direct.push_back(k);
+    if (P.yhat.n > 0) M.zero_yhat.push(vcopy(P.yhat.p, nullptr, (int64_t)P.yhat.n));
+    // ULV solve by level from the leaves; every root after every forward level
+    const UlvPlan& U = *a.PU;
+    for (int l = 0; l < a.nlev; ++l) {
+      gemm_cat(M.fwd[l], U.fwd[l]);
+      gemm_cat(M.bwd[l], U.bwd[l]);
+      M.uup[l].h.insert(M.uup[l].h.end(), U.up[l].h.begin(), U.up[l].h.end());
+      M.udown[l].h.insert(M.udown[l].h.end(), U.down[l].h.begin(), U.down[l].h.end());
+    }
+    gemm_cat(M.root_f, U.root_f);
+    gemm_cat(M.root_b, U.root_b);
+    double* p = P.xs.p;
+    double* q = P.ys.p;
+    double* z = U.bw[0].p;
+    M.d_pq.push_back(DotProb{p, q, a.n, a.nrhs, a.part.p, pl.pq(a)});
+    M.d_rr.push_back(DotProb{a.r.p, a.r.p, a.n, a.nrhs, a.part.p, pl.rr(a)});
+    M.d_rz.push_back(DotProb{a.r.p, z, a.n, a.nrhs, a.part.p, pl.rzn(a)});
+    M.v_axpy.push_back(VecProb{0, a.x.p, a.r.p, p, q, a.n, a.nrhs, pl.rz(a), pl.pq(a), pl.dn(a)});
+    M.v_upd.push_back(VecProb{1, p, nullptr, z, nullptr, a.n, a.nrhs, pl.rzn(a), pl.rz(a), pl.dn(a)});
+    M.z_from_r.push(vcopy(z, a.r.p, nc));
+    M.rz_from_rzn.push(vcopy(pl.rz(a), pl.rzn(a), a.nrhs));
+  }
+  auto up_g = [&](GemmBatch& g, const char* tag) { g.tag = tag; g.upload(s); };
+  up_g(M.up_leaf, "h2_basis");
+  for (auto& g : M.up) up_g(g, "h2_basis");
+  for (auto& g : M.down) up_g(g, "h2_basis");
+  up_g(M.leaf_out, "h2_basis");
+  up_g(M.coupling, "h2_coupling");
+  up_g(M.near_g, "near_h2_stored");
+  for (auto& g : M.fwd) up_g(g, "gemm_ulv_solve");
+  for (auto& g : M.bwd) up_g(g, "gemm_ulv_solve");
+  up_g(M.root_f, "gemm_ulv_root");
+  up_g(M.root_b, "gemm_ulv_root");
+  M.rowcoup.tag = "h2_coupling";
+  M.near_r.tag = "near_h2_stored";
+  if (!M.rowcoup.probs.empty()) M.rowcoup.upload(s);
+  if (!M.near_r.probs.empty()) M.near_r.upload(s);
+  M.zero_yhat.upload(s);
+  M.z_from_r.upload(s);
+  M.rz_from_rzn.upload(s);
+  for (auto& b : M.uup) b.upload(s);
+  for (auto& b : M.udown) b.upload(s);
+}
+
+void run_h2_merged(const std::vector<Inst>& I, const Merged& M, cudaStream_t s) {
+  M.up_leaf.launch(s);
+  for (const auto& g : M.up) g.launch(s);
+  copy_launch(M.zero_yhat, s);
+  if (!M.rowcoup.probs.empty()) M.rowcoup.launch(s);
+  M.coupling.launch(s);
+  for (const auto& g : M.down) g.launch(s);
+  M.leaf_out.launch(s);
+  if (!M.near_r.probs.empty()) M.near_r.launch(s);
+  M.near_g.launch(s);
+  for (int k : M.near_direct) {
+    const Inst& a = I[k];
+    a.PA->near.launch(a.h2->kfn, a.h2->td.xs.p, a.h2->th.n, a.h2->th.dim, s);
+  }
+}
+
+void run_ulv_merged(const Merged& M, cudaStream_t s) {
+  for (size_t l = 0; l < M.fwd.size(); ++l) {
+    M.fwd[l].launch(s);
+    copy_launch(M.uup[l], s);
+  }
+  M.root_f.launch(s);
+  M.root_b.launch(s);
+  for (int l = (int)M.fwd.size() - 1; l >= 0; --l) {
+    copy_launch(M.udown[l], s);
+    M.bwd[l].launch(s);
+  }
+}
+
+}  // namespace
+
+void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ulv,
+                      const double* const* B, double* const* X, const int* nrhs,
+                      const int64_t* ld, double tol, int maxit, int* const* iters_out,
+                      double* const* relres_out, spdhss_status* status, cudaStream_t s) {
+  std::vector<Inst> I(count);
+  Pools pl;
+  for (int k = 0; k < count; ++k) {
+    Inst& a = I[k];
+    a.h2 = h2[k];
+    a.u = ulv[k];
+    a.n = a.h2->th.n;
+    a.ld = ld[k];
+    a.nrhs = nrhs[k];
+    a.D = a.h2->th.D;
+    a.nlev = std::max(a.u->L - 1, 0);
+    a.B = B[k];
+    a.X = X[k];
+    a.so = pl.NC;
+    pl.NC += a.nrhs;
+    auto get_plan = [&](int key) -> H2Plan* {
+      auto it = a.h2->plans.find(key);
+      if (it == a.h2->plans.end()) {
+        std::unique_ptr<H2Plan> p(new H2Plan());
+        h2_plan_build(a.h2, *p, a.nrhs, 1, s);
+        it = a.h2->plans.emplace(key, std::move(p)).first;
+      }
+      return it->second.get();
+    };
+    a.PA = get_plan(a.nrhs);
+    a.PR = get_plan(-a.nrhs);
+    a.PU = &ulv_plan(a.u, a.nrhs, s);
+  }
+  pl.sc.alloc((size_t)std::max<int64_t>(4 * pl.NC, 1));
+  pl.done.alloc((size_t)std::max<int64_t>(pl.NC, 1));
+  pl.done.zero(s);
+  // start: x = 0, r = b, z = M^{-1} r, p = z, rz = r.z (per instance)
+  for (auto& a : I) {
+    const int64_t nc = a.n * a.nrhs;
+    const int64_t* perm = a.h2->td.perm.p;
+    a.bs.alloc(nc);
+    a.x.alloc(nc);
+    a.r.alloc(nc);
+    a.part.alloc((size_t)DOT_BLOCKS * a.nrhs);
+    if (!is_device_pointer(a.B)) {
+      DevBuf<double> tmp((size_t)a.ld * a.nrhs);
+      SPD_CUDA(cudaMemcpyAsync(tmp.p, a.B, (size_t)a.ld * a.nrhs * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      permute_to_sorted(tmp.p, a.ld, a.bs.p, a.n, a.nrhs, perm, s);
+      SPD_CUDA(cudaStreamSynchronize(s));
+    } else {
+      permute_to_sorted(a.B, a.ld, a.bs.p, a.n, a.nrhs, perm, s);
+    }
+    a.x.zero(s);
+    copy_vec(a.r.p, a.bs.p, nc, s);
+    dots(a.bs.p, a.bs.p, a.n, a.nrhs, a.part.p, pl.rr(a), s);
+    double* z = a.PU->bw[0].p;
+    copy_vec(z, a.r.p, nc, s);
+    ulv_solve_sorted(a.u, *a.PU, s);
+    copy_vec(a.PA->xs.p, z, nc, s);
+    dots(a.r.p, z, a.n, a.nrhs, a.part.p, pl.rz(a), s);
+    a.hdone.assign(a.nrhs, 0);
+    a.hit.assign(a.nrhs, 0);
+  }
+  std::vector<double> hsc(4 * pl.NC);
+  SPD_CUDA(cudaMemcpyAsync(hsc.data(), pl.sc.p, 4 * pl.NC * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SPD_CUDA(cudaStreamSynchronize(s));
+  for (auto& a : I) {
+    a.bn.resize(a.nrhs);
+    for (int c = 0; c < a.nrhs; ++c) {
+      const double v = hsc[3 * pl.NC + a.so + c];
+      a.bn[c] = v > 0.0 ? std::sqrt(v) : 1.0;
+    }
+  }
+  // b - A x of one instance, relative per column (its own plans, direct launches)
+  auto true_residual = [&](Inst& a, std::vector<double>& rel) {
+    const int64_t nc = a.n * a.nrhs;
+    copy_vec(a.PR->xs.p, a.x.p, nc, s);
+    h2_plan_run(a.h2, *a.PR, s);
+    sub(a.bs.p, a.PR->ys.p, a.PR->ys.p, nc, s);
+    dots(a.PR->ys.p, a.PR->ys.p, a.n, a.nrhs, a.part.p, pl.rr(a), s);
+    std::vector<double> h(a.nrhs);
+    SPD_CUDA(cudaMemcpyAsync(h.data(), pl.rr(a), a.nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPD_CUDA(cudaStreamSynchronize(s));
+    rel.resize(a.nrhs);
+    for (int c = 0; c < a.nrhs; ++c) rel[c] = std::sqrt(std::max(h[c], 0.0)) / a.bn[c];
+  };
+  Merged M;
+  build_merged(I, pl, M, s);
+  std::vector<double> hrr(pl.NC);
+  int nactive = count;
+  // Converged instances stay in the merged launches (their updates are masked by the done
+  // flags) until the active set has shrunk by a third: re-concatenating the stage batches
+  // costs more host time than the masked work of a few instances.
+  int merged_active = count;
+  for (int it = 1; it <= maxit && nactive > 0; ++it) {
+    run_h2_merged(I, M, s);                                   // q = A p
+    { std::vector<DotProb> v = M.d_pq; dots_merged(v, s); }
+    { std::vector<VecProb> v = M.v_axpy; vec_merged(v, s); }
+    { std::vector<DotProb> v = M.d_rr; dots_merged(v, s); }
+    SPD_CUDA(cudaMemcpyAsync(hrr.data(), pl.sc.p + 3 * pl.NC, pl.NC * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    SPD_CUDA(cudaStreamSynchronize(s));
+    bool changed_set = false;
+    for (auto& a : I) {
+      if (!a.active) continue;
+      bool any_pass = false;
+      for (int c = 0; c < a.nrhs; ++c) {
+        if (a.hdone[c] == 1) continue;
+        a.hit[c] = it;
+        const double v = hrr[a.so + c];
+        if (!std::isfinite(v)) throw Error(SPDHSS_NUMERIC, "pcg_solve_batched: residual is not finite");
+        if (std::sqrt(std::max(v, 0.0)) / a.bn[c] <= tol) any_pass = true;
+      }
+      if (any_pass) {
+        std::vector<double> trel;
+        true_residual(a, trel);
+        bool changed = false;
+        for (int c = 0; c < a.nrhs; ++c) {
+          if (a.hdone[c] == 1) continue;
+          if (std::sqrt(std::max(hrr[a.so + c], 0.0)) / a.bn[c] > tol) continue;
+          if (trel[c] <= tol) { a.hdone[c] = 1; changed = true; }
+          else {
+            copy_vec(a.r.p + (int64_t)c * a.n, a.PR->ys.p + (int64_t)c * a.n, a.n, s);
+            a.hdone[c] = 2;
+            changed = true;
+          }
+        }
+        if (changed)
+          SPD_CUDA(cudaMemcpyAsync(pl.dn(a), a.hdone.data(), a.nrhs * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+      }
+      bool all = true;
+      for (int c = 0; c < a.nrhs; ++c) all = all && a.hdone[c] == 1;
+      if (all) { a.active = false; --nactive; changed_set = true; }
+    }
+    if (nactive == 0) break;
+    if (changed_set && 3 * nactive <= 2 * merged_active) {
+      build_merged(I, pl, M, s);
+      merged_active = nactive;
+    }
+    copy_launch(M.z_from_r, s);
+    run_ulv_merged(M, s);                                     // z = M^{-1} r
+    { std::vector<DotProb> v = M.d_rz; dots_merged(v, s); }
+    { std::vector<VecProb> v = M.v_upd; vec_merged(v, s); }
+    copy_launch(M.rz_from_rzn, s);
+    for (auto& a : I) {
+      if (!a.active) continue;
+      bool restarted = false;
+      for (int c = 0; c < a.nrhs; ++c)
+        if (a.hdone[c] == 2) { a.hdone[c] = 0; restarted = true; }
+      if (restarted)
+        SPD_CUDA(cudaMemcpyAsync(pl.dn(a), a.hdone.data(), a.nrhs * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+    }
+  }
+  // final true residuals, outputs
+  for (int k = 0; k < count; ++k) {
+    Inst& a = I[k];
+    std::vector<double> trel;
+    true_residual(a, trel);
+    bool conv = true;
+    for (int c = 0; c < a.nrhs; ++c) {
+      if (iters_out && iters_out[k]) iters_out[k][c] = a.hit[c];
+      if (relres_out && relres_out[k]) relres_out[k][c] = trel[c];
+      conv = conv && trel[c] <= tol;
+    }
+    const int64_t* perm = a.h2->td.perm.p;
+    if (!is_device_pointer(a.X)) {
+      DevBuf<double> tmp((size_t)a.ld * a.nrhs);
+      if (a.ld > a.n)
+        SPD_CUDA(cudaMemcpyAsync(tmp.p, a.X, (size_t)a.ld * a.nrhs * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+      permute_from_sorted(a.x.p, tmp.p, a.ld, a.n, a.nrhs, perm, s);
+      SPD_CUDA(cudaMemcpyAsync(a.X, tmp.p, (size_t)a.ld * a.nrhs * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      SPD_CUDA(cudaStreamSynchronize(s));
+    } else {
+      permute_from_sorted(a.x.p, a.X, a.ld, a.n, a.nrhs, perm, s);
+    }
+    if (status) status[k] = conv ? SPDHSS_OK : SPDHSS_NO_CONVERGENCE;
+  }
+  SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace spd
