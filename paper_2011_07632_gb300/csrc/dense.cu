@@ -398,6 +398,17 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
       }
       vt.swap(nt);
     }
+    // longest K first, so that the long tiles do not form the tail of the launch
+    {
+      std::vector<int> kt(lprobs.size(), 0);
+      for (int q = 0; q < (int)lprobs.size(); ++q)
+        for (int g = lprobs[q].seg0; g < lprobs[q].seg1; ++g) kt[q] += lsegs[g].K;
+      auto klen = [&](const int4& t) {
+        return t.w > 0 ? kparts[t.w - 1].y - kparts[t.w - 1].x : kt[t.x];
+      };
+      std::stable_sort(vt.begin(), vt.end(),
+                       [&](const int4& x, const int4& y) { return klen(x) > klen(y); });
+    }
     vnb.push_back(v);
     vbeg.push_back((int64_t)tiles.size());
     tiles.insert(tiles.end(), vt.begin(), vt.end());
@@ -1467,6 +1478,21 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
     merge_ctx().m->submit(pivot ? "geqp3" : "geqrf", std::move(d));
     return -1;
   }
+  // the largest factorizations first (CTAs start in index order), so that they do not
+  // form the tail of the launch
+  DevBuf<QrProb> sorted;
+  const QrProb* dprobs = b.d.p;
+  if (b.size() > 1) {
+    std::vector<QrProb> h = b.h;
+    auto cost = [](const QrProb& q) {
+      const double k = std::min(q.kmax, std::min(q.m, q.n));
+      return (double)q.m * q.n * k;
+    };
+    std::stable_sort(h.begin(), h.end(),
+                     [&](const QrProb& x, const QrProb& y) { return cost(x) > cost(y); });
+    sorted.upload(h, s);
+    dprobs = sorted.p;
+  }
   if (pivot) {
     int mmax = 1, nmax = 1;
     for (const auto& p : b.h) { mmax = std::max(mmax, p.m); nmax = std::max(nmax, p.n); }
@@ -1497,11 +1523,11 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
       ProfScope ps(b.tag ? b.tag : "geqp3", s);
       // lanes per column: rows per lane at least 8 where the columns are short
       if (mmax <= 64)
-        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<8>, (const QrProb*)b.d.p, mmax, nmax));
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<8>, dprobs, mmax, nmax));
       else if (mmax <= 128)
-        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<16>, (const QrProb*)b.d.p, mmax, nmax));
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<16>, dprobs, mmax, nmax));
       else
-        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<32>, (const QrProb*)b.d.p, mmax, nmax));
+        SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<32>, dprobs, mmax, nmax));
       SPD_LAUNCHED();
       return ps.slot;
     }
@@ -1529,7 +1555,7 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
   {
     ProfScope ps(b.tag ? b.tag : (pivot ? "geqp3" : "geqrf"), s);
     slot = ps.slot;
-    SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, (const QrProb*)b.d.p, pivot));
+    SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, dprobs, pivot));
     SPD_LAUNCHED();
   }
   return slot;

@@ -171,7 +171,10 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
       proxy_launch(pb, h->kfn, dim, s);
       qb.tag = "geqp3_h2_id";
       qb.upload(s);
-      const int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
+      // cluster size: by the widest matrix, and wide enough that small batches still put
+      // about two CTAs on every SM (the columns of a matrix are split over its cluster)
+      int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
+      while (cl < 8 && (int64_t)nb * cl < 2 * 152 && maxm >= 32 * cl) cl *= 2;
       const int pslot = geqp3_launch(qb, 1, cl, np, s);
       std::vector<int> hrk = rk.download(s);
       if (pslot >= 0) {
