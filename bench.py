@@ -284,6 +284,19 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     return out
 
 
+def replica_throughput(total_ms, steps, world, dist=None, device=None):
+    """Whole-job throughput of `world` independent replicas that each ran `steps` steps in
+    `total_ms` of their own device time: the job lasts as long as the slowest rank (max over
+    ranks), and its value is all ranks' steps over that time.  Returns (job ms, steps/s)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return total_ms, (steps * world) / (total_ms / 1e3)
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -345,14 +358,8 @@ def run_gpu(args):
     prof = native.profile_report()
     native.lib().spdhss_profile(0)
     times = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(times))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms, value = replica_throughput(float(sum(times)), args.steps, world, dist, dev)
     torch.cuda.synchronize()
-    value = (args.steps * world) / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None

@@ -1,0 +1,61 @@
+"""The multi-GPU bench path is replicas only (independent instances per rank, no data-path
+collective): the job time is the slowest rank's and the value counts every rank's steps.
+Checked here with two gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r took 100 (r + 1) ms for its 4 steps
+    ms, value = bench.replica_throughput(100.0 * (rank + 1), 4, world, dist, "cpu")
+    out[rank] = (ms, value)
+    dist.destroy_process_group()
+
+
+def test_two_replicas_max_time_and_total_steps():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    for r in range(world):
+        ms, value = res[r]
+        assert ms == pytest.approx(200.0)          # the slowest rank
+        assert value == pytest.approx(8 / 0.2)     # 2 ranks x 4 steps in 0.2 s
+
+
+def test_single_replica_needs_no_collective():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.replica_throughput(250.0, 5, 1) == (250.0, pytest.approx(20.0))
+
+
+def test_replicas_draw_different_inputs():
+    from paper_2011_07632_gb300 import inputs
+    a = inputs.uniform_cube(64, 3, 0 + 0)
+    b = inputs.uniform_cube(64, 3, 0 + 1)
+    assert not (a == b).all()
