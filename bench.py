@@ -299,6 +299,13 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     return out
 
 
+# DRAM bytes (read + write) per launch of a kernel family on the headline workload, from one
+# ncu capture of the current kernels (profiles/launches_headline_exp3d_n4096.md): the two
+# shared-memory QR launches of one step's H^2 ID, averaged.  Remove an entry when its
+# kernel changes.
+DRAM_TRAFFIC = {"geqp3_h2_id": (75838464 + 16536064 + 75617280 + 12764416) / 2}
+
+
 def replica_throughput(total_ms, steps, world, dist=None, device=None):
     """Whole-job throughput of `world` independent replicas that each ran `steps` steps in
     `total_ms` of their own device time: the job lasts as long as the slowest rank (max over
@@ -415,7 +422,8 @@ def run_gpu(args):
         per_launch_ms = st["ms"] / max(st["launches"], 1)
         achieved = (st["flops"] / max(st["launches"], 1)) / (per_launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": DRAM_TRAFFIC.get(top),
                 "peak_source": "FP64 FMA units: 152 SMs x 2 FMA/clk x 2 flop x max SM clock",
                 "share_of_step": st["ms"] / max(total_ms, 1e-9),
                 "launches_per_step": st["launches"] / args.steps}
