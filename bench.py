@@ -299,10 +299,9 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     return out
 
 
-# DRAM bytes (read + write) per launch of a kernel family on the headline workload, from one
-# ncu capture of the current kernels (profiles/launches_headline_exp3d_n4096.md): the two
-# shared-memory QR launches of one step's H^2 ID, averaged.  Remove an entry when its
-# kernel changes.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel family on
+# the n = 4096 workload, from one ncu capture of the current kernels: the two shared-memory
+# QR launches of one step's H^2 ID, averaged.  An entry is removed when its kernel changes.
 DRAM_TRAFFIC = {"geqp3_h2_id": (75838464 + 16536064 + 75617280 + 12764416) / 2}
 
 
