@@ -79,7 +79,13 @@ def _sym_power(Bb: np.ndarray, p: float) -> np.ndarray:
     return (Q * d ** p) @ Q.T
 
 
-def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: str = "eig") -> HSS:
+def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: str = "eig",
+                 rtol: float = RANK_RTOL) -> HSS:
+    """Alg. 5.3.  rtol > RANK_RTOL truncates every basis at the relative tolerance rtol
+    (the pivoted QR of the scaled sample stops when the largest remaining column norm is
+    <= rtol times the first), with r as the rank cap: the tolerance-driven construction
+    with a fixed sketch."""
+    rtol = max(float(rtol), RANK_RTOL)
     hss = HSS(tree)
     Y = sample_products(tree, M, Omega)
     Lv = tree.L
@@ -93,7 +99,7 @@ def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: s
             break
         S = np.linalg.cholesky(Aii)
         lam = sla.solve_triangular(S, Y[1][b:e], lower=True)
-        k, piv, Rq, V = pivoted_qr(lam, r, RANK_RTOL)
+        k, piv, Rq, V = pivoted_qr(lam, r, rtol)
         hss.S[i] = S
         hss.Vbar[i] = V
         hss.rank[i] = k
@@ -124,7 +130,7 @@ def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: s
                 Fh = np.linalg.cholesky(np.eye(m) + Bb)
                 Fmh = sla.solve_triangular(Fh, np.eye(m), lower=True)
             lam = Fmh @ (PhiStack @ Y[k][b:e])
-            kk, piv, Rq, Vb = pivoted_qr(lam, r, RANK_RTOL)
+            kk, piv, Rq, Vb = pivoted_qr(lam, r, rtol)
             hss.Bbold[i] = Bb
             hss.Fhalf[i] = Fh
             hss.Vbar[i] = Vb

@@ -190,3 +190,41 @@ def test_spdhss_preconditioner_reduces_iterations():
     _, it_c, rel_c = P.pcg(lambda v: M @ v, lambda v: v, b, 1e-6, 3000)
     assert rel_p.max() <= 1e-6 and rel_c.max() <= 1e-6
     assert it_p.max() * 5 < it_c.max()
+
+
+@pytest.mark.parametrize("tau", [1e-1, 1e-2, 1e-4])
+def test_tolerance_truncation_leaf_ranks_match_lapack(tau):
+    """Tolerance-driven bases: the leaf rank is the number of |R_kk| > tau |R_00| in
+    LAPACK's column-pivoted QR (scipy) of the scaled sample S_i^{-1} Y_i^(1), capped at r."""
+    n, r = 512, 40
+    X, tr, M = _problem(n, 3, 32, K.GAUSS, 0.3, 1e-4, seed=3)
+    Om = inputs.sketch(n, r + 10, 9)
+    hss = S.build_spdhss(tr, M, Om, r, rtol=tau)
+    Y = S.sample_products(tr, M, Om)
+    for i in tr.nodes_at_level(1):
+        b, e = tr.begin[i], tr.end[i]
+        lam = sla.solve_triangular(np.linalg.cholesky(M[b:e, b:e]), Y[1][b:e], lower=True)
+        R = sla.qr(lam, mode="r", pivoting=True)[0]
+        d = np.abs(np.diag(R))
+        want = min(r, int(np.sum(d > tau * d[0])))
+        assert hss.rank[i] == want
+
+
+def test_tolerance_truncation_monotone_and_spd():
+    """Larger tau: ranks never grow, the approximation error grows, and the HSS stays SPD
+    (Sec. 3.2 holds for any truncation)."""
+    n, r = 512, 40
+    X, tr, M = _problem(n, 3, 32, K.EXP, 0.5, 1e-3, seed=4)
+    Om = inputs.sketch(n, r + 10, 10)
+    prev_rank, prev_err = None, None
+    for tau in (1e-14, 1e-6, 1e-2, 1e-1):
+        hss = S.build_spdhss(tr, M, Om, r, rtol=tau)
+        Hd = S.assemble_dense(hss)
+        assert np.linalg.eigvalsh(Hd).min() > 0.0
+        ranks = np.array([hss.rank[i] for i in sorted(hss.rank)])
+        err = np.linalg.norm(Hd - M) / np.linalg.norm(M)
+        if prev_rank is not None:
+            assert np.all(ranks <= prev_rank)
+            assert err >= prev_err * (1 - 1e-12)
+        prev_rank, prev_err = ranks, err
+    assert prev_rank.sum() < np.array([S.build_spdhss(tr, M, Om, r).rank[i] for i in sorted(hss.rank)]).sum()
