@@ -128,6 +128,15 @@ spdhss_status h2_destroy(h2_handle h2);
 spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
                            uint64_t seed, void* stream, hss_handle* out);
 
+/* Tolerance-driven variant of spdhss_build: every basis is truncated at the relative
+ * tolerance `tol` (the column-pivoted QR of the scaled sample stops when the largest
+ * remaining column norm is <= tol times the first), `rank` being the cap; tol = 0 is
+ * spdhss_build.  The sketch keeps rank + oversample columns (no adaptive growth).  The
+ * result is SPD for every tol (Sec. 3.2).  EINVAL unless 0 <= tol < 1. */
+spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversample,
+                               const double* omega, uint64_t seed, void* stream,
+                               hss_handle* out);
+
 /* Y = H X with the HSS approximation H (same layout rules as h2_matmul). */
 spdhss_status hss_matmul(hss_handle hss, const double* X, double* Y, int nrhs, int64_t ld,
                          void* stream);

@@ -324,9 +324,11 @@ spdhss_status h2_destroy(h2_handle h) {
 
 extern "C" {
 
-spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
-                           uint64_t seed, void* stream, hss_handle* out) {
+spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversample,
+                               const double* omega, uint64_t seed, void* stream,
+                               hss_handle* out) {
   return spd::guarded("spdhss_build", [&] {
+    SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
     spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -335,9 +337,14 @@ spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double*
     SPD_REQUIRE(oversample >= 0, "oversample must be >= 0");
     SPD_REQUIRE(omega == nullptr || spd::is_device_pointer(omega), "omega must be a device pointer");
     std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-    spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream);
+    spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream, tol);
     *out = hs.release();
   });
+}
+
+spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
+                           uint64_t seed, void* stream, hss_handle* out) {
+  return spdhss_build_tol(h2, rank, 0.0, oversample, omega, seed, stream, out);
 }
 
 spdhss_status hss_matmul(hss_handle hs, const double* X, double* Y, int nrhs, int64_t ld,
@@ -555,7 +562,7 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
       std::unique_ptr<spdhss_h2_s> h =
           h2_build_one(points[i], n[i], dim[i], kernel[i], leaf_size[i], tol[i], s);
       std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-      spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], nullptr, seed[i], s);
+      spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], nullptr, seed[i], s, 0.0);
       std::unique_ptr<spdhss_ulv_s> u(new spdhss_ulv_s());
       ulv_factor_impl(u.get(), hs.get(), s);
       ulv_out[i] = u.release();

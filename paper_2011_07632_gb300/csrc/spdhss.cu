@@ -99,7 +99,7 @@ void check_info(DevBuf<int>& info, const char* what, int64_t base, cudaStream_t 
 }  // namespace
 
 void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
-                       const double* omega, uint64_t seed, cudaStream_t s) {
+                       const double* omega, uint64_t seed, cudaStream_t s, double rtol) {
   const TreeHost& T = h2->th;
   const int64_t n = T.n;
   const int D = T.D;
@@ -302,7 +302,7 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         }
         QrProb q;
         q.A = Q.p + qo[a]; q.lda = std::max(m, 1); q.m = m; q.n = sc;
-        q.kmax = std::min(r, std::min(m, sc)); q.rtol = 1e-14;
+        q.kmax = std::min(r, std::min(m, sc)); q.rtol = std::max(rtol, 1e-14);
         q.piv = piv.p + a * sc; q.tau = tau.p + mo[a]; q.rank = rkd.p + a;
         q.norms = norms.p + 2 * a * sc;
         q.downdate = 0;   // sketches are close to full rank: every norm would be recomputed

@@ -89,3 +89,23 @@ def test_device_sketch_statistics():
     e_dev = rel(gpu_dense(api.HSS(h, 50, 10, seed=3), n), A)
     e_host = rel(gpu_dense(api.HSS(h, 50, 10, omega=inputs.sketch(n, 60, 2)), n), A)
     assert e_dev < 3 * e_host and e_host < 3 * e_dev
+
+
+@pytest.mark.parametrize("tau", [1e-1, 1e-2, 1e-5])
+def test_tolerance_truncated_hss_matches_oracle(tau):
+    """Tolerance-driven bases (spdhss_build_tol): the same truncation as the oracle's on
+    the same matrix and sketch, and the result stays SPD."""
+    api = need_gpu()
+    n, dim, leaf, kind, ell, sigma, tol, r = 1500, 3, 40, "exp", 0.5, 1e-3, 1e-8, 40
+    X = inputs.uniform_cube(n, dim, 3)
+    Om = inputs.sketch(n, r + 10, 4)
+    h = api.H2(X, kind, ell, sigma, leaf, tol)
+    hs = api.HSS(h, r, 10, omega=Om, tol=tau)
+    Hg = gpu_dense(hs, n)
+    tr = OT.build_tree(X, leaf)
+    M = OH.dense(OH.build_h2(tr, X, OK.NAMES[kind], ell, sigma, tol))
+    hss = OS.build_spdhss(tr, M, Om[tr.perm], r, rtol=tau)
+    Ho = unsort(OS.assemble_dense(hss), tr.perm)
+    assert rel(Hg, Ho) < 1e-10
+    assert hs.info()["max_rank"] == max(hss.rank.values())
+    assert np.linalg.eigvalsh(0.5 * (Hg + Hg.T)).min() > 0.0
