@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: this many Poisson-arriving mixed requests, served one at "
                          "a time and then concurrently; prints a serving JSON line")
+    ap.add_argument("--tol-sweep", action="store_true",
+                    help="tolerance-driven SPD-HSS: PCG iterations and times for bases "
+                         "truncated at 1e-1 and 1e-2 (rank cap 400) over growing n")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched level sweep: this many independent instances built and solved "
                          "with merged launches, then one at a time; prints a batching JSON line")
@@ -606,8 +609,44 @@ def run_batch(count):
         "dtype": "f64", "data": "synthetic"}))
 
 
+def run_tol_sweep():
+    """Exp kernel on uniform points in the unit cube (shift 1e-2, leaf 64, H^2 tol 1e-8):
+    bases truncated at a relative tolerance (rank cap 400) instead of a fixed rank; PCG
+    iterations to relres 1e-6 as n grows."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    rows = []
+    for n in (4096, 16384, 65536):
+        pts = torch.from_numpy(inputs.uniform_cube(n, 3, 0)).cuda()
+        b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
+        h = api.H2(pts, "exp", 1.0, 1e-2, 64, 1e-8)
+        for tau in (1e-1, 1e-2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs = api.HSS(h, 400, 10, seed=2, tol=tau)
+            u = api.ULV(hs)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            rows.append({"n": n, "tol": tau, "max_rank": hs.info()["max_rank"],
+                         "pcg_iters": int(it.max()), "relres": float(rr.max()),
+                         "build_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3})
+            u.close(); hs.close()
+        h.close()
+    print(json.dumps({"metric": "PCG iterations with tolerance-truncated SPD-HSS bases",
+                      "workload": "exp3d_shift1e-2_n4096-65536", "rows": rows,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def main():
     args = parse()
+    if args.tol_sweep:
+        run_tol_sweep()
+        return
     if args.batch:
         run_batch(args.batch)
         return
