@@ -58,8 +58,8 @@ def parse():
                     help="serving mode: this many Poisson-arriving mixed requests, served one at "
                          "a time and then concurrently; prints a serving JSON line")
     ap.add_argument("--tol-sweep", action="store_true",
-                    help="tolerance-driven SPD-HSS: PCG iterations and times for bases "
-                         "truncated at 1e-1 and 1e-2 (rank cap 400) over growing n")
+                    help="tolerance-driven SPD-HSS on the paper's Matern ball/sphere "
+                         "workload: PCG iterations and matvec errors at tau 1e-1 and 1e-2")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched level sweep: this many independent instances built and solved "
                          "with merged launches, then one at a time; prints a batching JSON line")
@@ -610,35 +610,46 @@ def run_batch(count):
 
 
 def run_tol_sweep():
-    """Exp kernel on uniform points in the unit cube (shift 1e-2, leaf 64, H^2 tol 1e-8):
-    bases truncated at a relative tolerance (rank cap 400) instead of a fixed rank; PCG
-    iterations to relres 1e-6 as n grows."""
+    """The paper's relative-tolerance experiment (Matern-3/2 with l = 0.25, i.e. length scale
+    4, shift 1e-2, ball and sphere point sets of constant density): bases truncated at
+    tau = 1e-1 and 1e-2 (rank caps 200 and 600, oversampling 10), leaf boxes of up to 400
+    points, H^2 tolerance 1e-8; PCG iterations to relres 1e-6 and the average relative error
+    of the SPD-HSS product against the H^2 product over 4 random vectors."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2011_07632_gb300 import api, inputs
     rows = []
-    for n in (4096, 16384, 65536):
-        pts = torch.from_numpy(inputs.uniform_cube(n, 3, 0)).cuda()
-        b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
-        h = api.H2(pts, "exp", 1.0, 1e-2, 64, 1e-8)
-        for tau in (1e-1, 1e-2):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hs = api.HSS(h, 400, 10, seed=2, tol=tau)
-            u = api.ULV(hs)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            rows.append({"n": n, "tol": tau, "max_rank": hs.info()["max_rank"],
-                         "pcg_iters": int(it.max()), "relres": float(rr.max()),
-                         "build_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3})
-            u.close(); hs.close()
-        h.close()
+    for pset in ("ball", "sphere"):
+        for n in (40000, 80000, 160000):
+            X = inputs.ball(n, 0) if pset == "ball" else inputs.sphere(n, 0)
+            pts = torch.from_numpy(X).cuda()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
+            xr = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 4, 3))).cuda()
+            h = api.H2(pts, "matern32", 4.0, 1e-2, 400, 1e-8)
+            yh = h.matmul(xr)
+            for tau, cap in ((1e-1, 200), (1e-2, 600)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                hs = api.HSS(h, cap, 10, seed=2, tol=tau)
+                u = api.ULV(hs)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                ys = hs.matmul(xr)
+                err = float(((ys - yh).norm(dim=0) / yh.norm(dim=0)).mean())
+                rows.append({"points": pset, "n": n, "tol": tau, "rank_cap": cap,
+                             "max_rank": hs.info()["max_rank"], "pcg_iters": int(it.max()),
+                             "relres": float(rr.max()), "matvec_err": err,
+                             "build_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3})
+                u.close(); hs.close()
+            h.close()
+            del pts, b, xr, yh
+            torch.cuda.empty_cache()
     print(json.dumps({"metric": "PCG iterations with tolerance-truncated SPD-HSS bases",
-                      "workload": "exp3d_shift1e-2_n4096-65536", "rows": rows,
+                      "workload": "matern32_l0.25_ball_sphere_n40k-160k", "rows": rows,
                       "dtype": "f64", "data": "synthetic"}))
 
 
