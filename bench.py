@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--tol-sweep", action="store_true",
                     help="tolerance-driven SPD-HSS on the paper's Matern ball/sphere "
                          "workload: PCG iterations and matvec errors at tau 1e-1 and 1e-2")
+    ap.add_argument("--rank-sweep", action="store_true",
+                    help="fixed ranks 100 and 200 on the paper's Matern ball/sphere workload")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched level sweep: this many independent instances built and solved "
                          "with merged launches, then one at a time; prints a batching JSON line")
@@ -609,6 +611,33 @@ def run_batch(count):
         "dtype": "f64", "data": "synthetic"}))
 
 
+def run_rank_sweep():
+    """The paper's fixed-rank runs on the same Matern (l = 0.25) ball/sphere workload:
+    r = 100 and 200, oversampling 10, PCG iterations to relres 1e-6."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    rows = []
+    for pset in ("ball", "sphere"):
+        for n in (40000, 80000):
+            X = inputs.ball(n, 0) if pset == "ball" else inputs.sphere(n, 0)
+            pts = torch.from_numpy(X).cuda()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
+            h = api.H2(pts, "matern32", 4.0, 1e-2, 400, 1e-8)
+            for r in (100, 200):
+                hs = api.HSS(h, r, 10, seed=2)
+                u = api.ULV(hs)
+                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
+                rows.append({"points": pset, "n": n, "rank": r, "pcg_iters": int(it.max()),
+                             "relres": float(rr.max())})
+                u.close(); hs.close()
+            h.close()
+    print(json.dumps({"metric": "PCG iterations with fixed-rank SPD-HSS",
+                      "workload": "matern32_l0.25_ball_sphere_n40k-80k", "rows": rows,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def run_tol_sweep():
     """The paper's relative-tolerance experiment (Matern-3/2 with l = 0.25, i.e. length scale
     4, shift 1e-2, ball and sphere point sets of constant density): bases truncated at
@@ -657,6 +686,9 @@ def main():
     args = parse()
     if args.tol_sweep:
         run_tol_sweep()
+        return
+    if args.rank_sweep:
+        run_rank_sweep()
         return
     if args.batch:
         run_batch(args.batch)
