@@ -483,43 +483,8 @@ template struct GemmBatchT<double>;
 template struct GemmBatchT<float>;
 
 // ---------------------------------------------------------------------------------------
-// Cholesky, one CTA per matrix, right-looking in global memory
+// Cholesky
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_potrf(const PotrfProb* __restrict__ probs, int* info) {
-  const PotrfProb P = probs[blockIdx.x];
-  double* A = P.A;
-  const int64_t ld = P.lda;
-  const int n = P.n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __shared__ double s_d;
-  __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = A[j + j * ld];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = 1;
-        if (atomicCAS(P.info ? P.info : info, 0, P.tag + 1) == 0) (P.info ? P.info : info)[1] = P.col0 + j;
-      }
-      s_d = sqrt(d);
-    }
-    __syncthreads();
-    if (s_fail) return;
-    const double d = s_d;
-    const double inv = 1.0 / d;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + j * ld] *= inv;
-    if (threadIdx.x == 0) A[j + j * ld] = d;
-    __syncthreads();
-    for (int c = j + 1 + warp; c < n; c += nw) {
-      const double ljc = A[c + j * ld];
-      for (int i = c + lane; i < n; i += 32) A[i + c * ld] -= A[i + j * ld] * ljc;
-    }
-    __syncthreads();
-  }
-  for (int c = warp; c < n; c += nw)
-    for (int i = lane; i < c; i += 32) A[i + c * ld] = 0.0;
-}
 
 // Blocked right-looking Cholesky, one CTA per matrix, 32 x 32 tiles: one warp factors the
 // diagonal tile in shared memory, every thread solves panel rows against it, and the
