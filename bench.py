@@ -613,7 +613,8 @@ def run_batch(count):
 
 def run_rank_sweep():
     """The paper's fixed-rank runs on the same Matern (l = 0.25) ball/sphere workload:
-    r = 100 and 200, oversampling 10, PCG iterations to relres 1e-6."""
+    r = 100 and 200, oversampling 10, and r = 0 (the block-Jacobi preconditioner of the
+    paper's comparisons); PCG iterations to relres 1e-6."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -625,10 +626,10 @@ def run_rank_sweep():
             pts = torch.from_numpy(X).cuda()
             b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
             h = api.H2(pts, "matern32", 4.0, 1e-2, 400, 1e-8)
-            for r in (100, 200):
+            for r in (0, 100, 200):
                 hs = api.HSS(h, r, 10, seed=2)
                 u = api.ULV(hs)
-                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
+                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6, maxit=3000)
                 rows.append({"points": pset, "n": n, "rank": r, "pcg_iters": int(it.max()),
                              "relres": float(rr.max())})
                 u.close(); hs.close()

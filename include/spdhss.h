@@ -117,7 +117,8 @@ spdhss_status h2_destroy(h2_handle h2);
 
 /* ---- SPD HSS construction (Alg. 5.3 with Alg. 5.1 and Alg. 5.2) ----------------------
  * Builds the SPD HSS approximation {A_ii, U_i, R_i, B_ij} of the H^2 matrix with rank cap
- * `rank` (r) and oversampling `oversample` (p, the paper uses 10).  The Gaussian sketch
+ * `rank` (r) and oversampling `oversample` (p, the paper uses 10); rank 0 gives the block
+ * diagonal of the leaf blocks (the block-Jacobi preconditioner).  The Gaussian sketch
  * Omega is n x (r+p):
  *   omega   DEVICE pointer, column-major, leading dimension n, original point order; or
  *           NULL, in which case Omega is drawn on the device from `seed`.

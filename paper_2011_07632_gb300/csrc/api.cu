@@ -333,7 +333,7 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     SPD_REQUIRE(h2 != nullptr, "NULL H2 handle");
-    SPD_REQUIRE(rank >= 1, "rank must be >= 1");
+    SPD_REQUIRE(rank >= 0, "rank must be >= 0");
     SPD_REQUIRE(oversample >= 0, "oversample must be >= 0");
     SPD_REQUIRE(omega == nullptr || spd::is_device_pointer(omega), "omega must be a device pointer");
     std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());

@@ -109,3 +109,25 @@ def test_tolerance_truncated_hss_matches_oracle(tau):
     assert rel(Hg, Ho) < 1e-10
     assert hs.info()["max_rank"] == max(hss.rank.values())
     assert np.linalg.eigvalsh(0.5 * (Hg + Hg.T)).min() > 0.0
+
+
+def test_rank_zero_gives_block_jacobi():
+    """rank 0: the GPU SPD-HSS is the block diagonal of the leaf blocks and its ULV solve is
+    the block-Jacobi solve."""
+    api = need_gpu()
+    n, leaf = 1200, 50
+    X = inputs.uniform_cube(n, 3, 5)
+    h = api.H2(X, "matern32", 0.3, 1e-2, leaf, 1e-8)
+    hs = api.HSS(h, 0, 10, seed=1)
+    Hg = gpu_dense(hs, n)
+    tr = OT.build_tree(X, leaf)
+    M = OK.dense_matrix(OK.NAMES["matern32"], 0.3, 1e-2, X[tr.perm])
+    B = np.zeros_like(M)
+    for i in tr.nodes_at_level(1):
+        b, e = tr.begin[i], tr.end[i]
+        B[b:e, b:e] = M[b:e, b:e]
+    assert rel(Hg, unsort(B, tr.perm)) < 1e-13
+    u = api.ULV(hs)
+    rhs = inputs.rhs(n, 2, 6)
+    x = u.solve(rhs).cpu().numpy()
+    assert rel(Hg @ x, rhs) < 1e-11

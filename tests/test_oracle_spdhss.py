@@ -228,3 +228,15 @@ def test_tolerance_truncation_monotone_and_spd():
             assert err >= prev_err * (1 - 1e-12)
         prev_rank, prev_err = ranks, err
     assert prev_rank.sum() < np.array([S.build_spdhss(tr, M, Om, r).rank[i] for i in sorted(hss.rank)]).sum()
+
+
+def test_rank_zero_is_block_jacobi():
+    """r = 0: every basis is empty and the SPD-HSS matrix is the block diagonal of the leaf
+    blocks, the block-Jacobi preconditioner of the paper's comparisons, exactly."""
+    X, tr, M = _problem(400, 3, 16, K.EXP, 0.5, 1e-2, seed=1)
+    hss = S.build_spdhss(tr, M, inputs.sketch(400, 10, 3), 0)
+    B = np.zeros_like(M)
+    for i in tr.nodes_at_level(1):
+        b, e = tr.begin[i], tr.end[i]
+        B[b:e, b:e] = M[b:e, b:e]
+    assert np.array_equal(S.assemble_dense(hss), B)
