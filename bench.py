@@ -62,6 +62,9 @@ def parse():
                          "workload: PCG iterations and matvec errors at tau 1e-1 and 1e-2")
     ap.add_argument("--rank-sweep", action="store_true",
                     help="fixed ranks 100 and 200 on the paper's Matern ball/sphere workload")
+    ap.add_argument("--kernel-sweep", action="store_true",
+                    help="block Jacobi and SPD-HSS r=100 over the Matern parameter l on the "
+                         "paper's 320,000-point ball")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched level sweep: this many independent instances built and solved "
                          "with merged launches, then one at a time; prints a batching JSON line")
@@ -618,7 +621,8 @@ def run_batch(count):
 def run_rank_sweep():
     """The paper's fixed-rank runs on the same Matern (l = 0.25) ball/sphere workload:
     r = 100 and 200, oversampling 10, and r = 0 (the block-Jacobi preconditioner of the
-    paper's comparisons); PCG iterations to relres 1e-6."""
+    paper's comparisons); the paper's PCG setting: right-hand side uniform on [-0.5, 0.5],
+    relres 1e-4."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -628,12 +632,12 @@ def run_rank_sweep():
         for n in (40000, 80000):
             X = inputs.ball(n, 0) if pset == "ball" else inputs.sphere(n, 0)
             pts = torch.from_numpy(X).cuda()
-            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(n, 1, 1))).cuda()
             h = api.H2(pts, "matern32", 4.0, 1e-2, 400, 1e-8)
             for r in (0, 100, 200):
                 hs = api.HSS(h, r, 10, seed=2)
                 u = api.ULV(hs)
-                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6, maxit=3000)
+                x, it, rr = api.pcg_solve(h, u, b, tol=1e-4, maxit=3000)
                 rows.append({"points": pset, "n": n, "rank": r, "pcg_iters": int(it.max()),
                              "relres": float(rr.max())})
                 u.close(); hs.close()
@@ -643,12 +647,41 @@ def run_rank_sweep():
                       "dtype": "f64", "data": "synthetic"}))
 
 
+def run_kernel_sweep():
+    """The paper's parameter sweep: Matern-3/2 kernel matrices sigma I + K_l on 320,000
+    points in a ball (constant density), l from 0.001 to 1 (length scale 1/l), sigma 1e-2,
+    leaf boxes of up to 400 points; block Jacobi (rank 0) and SPD-HSS with r = 100; PCG to
+    relres 1e-4 with a right-hand side uniform on [-0.5, 0.5]."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    n = 320000
+    pts = torch.from_numpy(inputs.ball(n, 0)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(n, 1, 1))).cuda()
+    rows = []
+    for l in (0.001, 0.01, 0.1, 1.0):
+        h = api.H2(pts, "matern32", 1.0 / l, 1e-2, 400, 1e-8)
+        for r in (0, 100):
+            hs = api.HSS(h, r, 10, seed=2)
+            u = api.ULV(hs)
+            x, it, rr = api.pcg_solve(h, u, b, tol=1e-4, maxit=3000)
+            rows.append({"l": l, "rank": r, "pcg_iters": int(it.max()), "relres": float(rr.max())})
+            u.close(); hs.close()
+        h.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "PCG iterations over the Matern length scale",
+                      "workload": "matern32_ball_n320k_l0.001-1", "rows": rows,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def run_tol_sweep():
     """The paper's relative-tolerance experiment (Matern-3/2 with l = 0.25, i.e. length scale
     4, shift 1e-2, ball and sphere point sets of constant density): bases truncated at
     tau = 1e-1 and 1e-2 (rank caps 200 and 600, oversampling 10), leaf boxes of up to 400
-    points, H^2 tolerance 1e-8; PCG iterations to relres 1e-6 and the average relative error
-    of the SPD-HSS product against the H^2 product over 4 random vectors."""
+    points, H^2 tolerance 1e-8; PCG iterations to relres 1e-4 with a right-hand side uniform
+    on [-0.5, 0.5] (the paper's setting) and the average relative error of the SPD-HSS
+    product against the H^2 product over 4 random vectors."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -658,7 +691,7 @@ def run_tol_sweep():
         for n in (40000, 80000, 160000):
             X = inputs.ball(n, 0) if pset == "ball" else inputs.sphere(n, 0)
             pts = torch.from_numpy(X).cuda()
-            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, 1))).cuda()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(n, 1, 1))).cuda()
             xr = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 4, 3))).cuda()
             h = api.H2(pts, "matern32", 4.0, 1e-2, 400, 1e-8)
             yh = h.matmul(xr)
@@ -669,7 +702,7 @@ def run_tol_sweep():
                 u = api.ULV(hs)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
-                x, it, rr = api.pcg_solve(h, u, b, tol=1e-6)
+                x, it, rr = api.pcg_solve(h, u, b, tol=1e-4)
                 torch.cuda.synchronize()
                 t2 = time.perf_counter()
                 ys = hs.matmul(xr)
@@ -694,6 +727,9 @@ def main():
         return
     if args.rank_sweep:
         run_rank_sweep()
+        return
+    if args.kernel_sweep:
+        run_kernel_sweep()
         return
     if args.batch:
         run_batch(args.batch)

@@ -41,6 +41,12 @@ def sphere(n: int, seed: int = 0) -> np.ndarray:
     return v * rad
 
 
+def rhs_uniform(n: int, nrhs: int, seed: int = 1) -> np.ndarray:
+    """Right-hand sides with entries uniform on [-0.5, 0.5] (the paper's experiments),
+    column-major (n, nrhs) float64 in Fortran order."""
+    return np.asfortranarray(_gen(seed, 6).random((n, nrhs)) - 0.5)
+
+
 def rhs(n: int, nrhs: int, seed: int = 1) -> np.ndarray:
     """Right-hand sides, entries N(0,1), column-major (n, nrhs) float64 in Fortran order."""
     return np.asfortranarray(_gen(seed, 3).standard_normal((n, nrhs)))
