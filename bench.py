@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--kernel-sweep", action="store_true",
                     help="block Jacobi and SPD-HSS r=100 over the Matern parameter l on the "
                          "paper's 320,000-point ball")
+    ap.add_argument("--paper-table", action="store_true",
+                    help="the paper's timing-table workload (320,000 points in a ball, three "
+                         "kernels, r = 100 and 200) on one GPU")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched level sweep: this many independent instances built and solved "
                          "with merged launches, then one at a time; prints a batching JSON line")
@@ -675,6 +678,59 @@ def run_kernel_sweep():
                       "dtype": "f64", "data": "synthetic"}))
 
 
+def run_paper_table():
+    """The paper's timing table setting: 320,000 points in a ball of radius (3N/4pi)^(1/3),
+    shift 1e-2, H^2 tolerance 1e-8, leaf boxes of up to 400 points, oversampling 10; the
+    Matern-3/2 kernel with l = 0.025, the Gaussian with l = 0.01 and the IMQ with l = 1
+    (the paper's l; here length scales 40, 10 and 1); SPD-HSS with r = 100 and 200; PCG to
+    relres 1e-4 with a right-hand side uniform on [-0.5, 0.5].  Times with CUDA events."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    n = 320000
+    pts = torch.from_numpy(inputs.ball(n, 0)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(n, 1, 1))).cuda()
+
+    def timed(fn, reps=1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = None
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / reps
+
+    rows = []
+    for kern, ell, lp in (("matern32", 40.0, 0.025), ("gauss", 10.0, 0.01), ("imq", 1.0, 1.0)):
+        h, t_h2 = timed(lambda: api.H2(pts, kern, ell, 1e-2, 400, 1e-8))
+        h.matmul(b)
+        _, t_mv = timed(lambda: h.matmul(b), reps=5)
+        info = h.info()
+        row = {"kernel": kern, "paper_l": lp, "h2_build_s": t_h2 / 1e3, "h2_matvec_s": t_mv / 1e3,
+               "h2_gb": info["stored_bytes"] / 1e9}
+        for r in (100, 200):
+            def build():
+                hs = api.HSS(h, r, 10, seed=2)
+                return hs, api.ULV(hs)
+            (hs, u), t_b = timed(build)
+            u.solve(b)
+            _, t_s = timed(lambda: u.solve(b), reps=5)
+            x, it, rr = api.pcg_solve(h, u, b, tol=1e-4, maxit=3000)
+            row[f"r{r}"] = {"build_incl_ulv_s": t_b / 1e3, "apply_s": t_s / 1e3,
+                            "hss_gb": hs.info()["stored_bytes"] / 1e9, "pcg_iters": int(it.max())}
+            u.close(); hs.close()
+        rows.append(row)
+        h.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "the paper's timing table on one GB300",
+                      "workload": "ball_n320k_matern_gauss_imq", "rows": rows,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def run_tol_sweep():
     """The paper's relative-tolerance experiment (Matern-3/2 with l = 0.25, i.e. length scale
     4, shift 1e-2, ball and sphere point sets of constant density): bases truncated at
@@ -730,6 +786,9 @@ def main():
         return
     if args.kernel_sweep:
         run_kernel_sweep()
+        return
+    if args.paper_table:
+        run_paper_table()
         return
     if args.batch:
         run_batch(args.batch)
