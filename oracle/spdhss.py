@@ -58,6 +58,23 @@ class HSS:
         return {(i, j): b for (i, j), b in self.B.items() if t.parent[i] == t.parent[j]}
 
 
+def build_spdhss_adaptive(tree: Tree, M: np.ndarray, Omega: np.ndarray, rank_cap: int,
+                          p: int, rtol: float, r0: int = 64) -> HSS:
+    """Tolerance-driven construction with a growing sketch (the extension remarked after
+    Alg. 5.3: add vectors to Omega until the truncation at rtol is no longer limited by the
+    sketch).  Omega holds at least rank_cap + p columns; an attempt with rank cap r uses its
+    first r + p.  Starting from r = min(rank_cap, r0), the cap doubles until every rank is
+    below the cap of the attempt (the p extra columns then oversample every kept rank) or
+    the cap reaches rank_cap."""
+    r = min(rank_cap, r0)
+    while True:
+        hss = build_spdhss(tree, M, Omega[:, :r + p], r, rtol=rtol)
+        if max(hss.rank.values(), default=0) < r or r >= rank_cap:
+            hss.sketch_rank = r
+            return hss
+        r = min(2 * r, rank_cap)
+
+
 def sample_products(tree: Tree, M: np.ndarray, Omega: np.ndarray):
     """Y^(k) = (M - blkdiag_k(M)) Omega for k = 1 .. L-1 (Eq. Yk), literally."""
     Y = {}

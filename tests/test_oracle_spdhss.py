@@ -240,3 +240,22 @@ def test_rank_zero_is_block_jacobi():
         b, e = tr.begin[i], tr.end[i]
         B[b:e, b:e] = M[b:e, b:e]
     assert np.array_equal(S.assemble_dense(hss), B)
+
+
+def test_adaptive_sketch_grows_until_ranks_fit():
+    """Tolerance-driven construction with a growing sketch: the sketch doubles from 8
+    columns (+ p) until every basis rank is below the attempt's cap; the result is the
+    construction with that sketch, whose ranks are all below it."""
+    n, p = 512, 10
+    X, tr, M = _problem(n, 3, 64, K.MATERN32, 0.3, 1e-2, seed=6)
+    Om = inputs.sketch(n, 200 + p, 11)
+    hss = S.build_spdhss_adaptive(tr, M, Om, 200, p, 1e-3, r0=8)
+    r = hss.sketch_rank
+    assert r > 8 and r in (16, 32, 64, 128, 200)
+    assert max(hss.rank.values()) < r
+    ref = S.build_spdhss(tr, M, Om[:, :r + p], r, rtol=1e-3)
+    assert ref.rank == hss.rank
+    # the previous attempt was limited by its sketch
+    rp = 128 if r == 200 else r // 2
+    prev = S.build_spdhss(tr, M, Om[:, :rp + p], rp, rtol=1e-3)
+    assert max(prev.rank.values()) == rp
