@@ -131,9 +131,13 @@ spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double*
 
 /* Tolerance-driven variant of spdhss_build: every basis is truncated at the relative
  * tolerance `tol` (the column-pivoted QR of the scaled sample stops when the largest
- * remaining column norm is <= tol times the first), `rank` being the cap; tol = 0 is
- * spdhss_build.  The sketch keeps rank + oversample columns (no adaptive growth).  The
- * result is SPD for every tol (Sec. 3.2).  EINVAL unless 0 <= tol < 1. */
+ * remaining column norm is <= tol times the first), `rank` being the largest rank allowed;
+ * tol = 0 is spdhss_build.  The sketch grows: an attempt with rank cap r uses the first
+ * r + oversample sketch columns (of omega, which then holds rank + oversample columns, or
+ * of the device sketch, whose columns do not depend on its width); starting from
+ * r = min(rank, 64), r doubles until every rank is below r or r reaches `rank` (each
+ * attempt is a full construction).  The result is SPD for every tol (Sec. 3.2).  EINVAL
+ * unless 0 <= tol < 1. */
 spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversample,
                                const double* omega, uint64_t seed, void* stream,
                                hss_handle* out);

@@ -336,9 +336,26 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
     SPD_REQUIRE(rank >= 0, "rank must be >= 0");
     SPD_REQUIRE(oversample >= 0, "oversample must be >= 0");
     SPD_REQUIRE(omega == nullptr || spd::is_device_pointer(omega), "omega must be a device pointer");
-    std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-    spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream, tol);
-    *out = hs.release();
+    if (tol <= 0.0) {
+      std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
+      spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream, tol);
+      *out = hs.release();
+      return;
+    }
+    // growing sketch: an attempt with cap r uses the first r + oversample sketch columns;
+    // the cap doubles from 64 until every rank is below it or it reaches `rank`
+    int r = std::min(rank, 64);
+    while (true) {
+      std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
+      spd::spdhss_build_impl(hs.get(), h2, r, oversample, omega, seed, (cudaStream_t)stream, tol);
+      int mr = 0;
+      for (int v : hs->rk) mr = std::max(mr, v);
+      if (mr < r || r >= rank) {
+        *out = hs.release();
+        return;
+      }
+      r = std::min(2 * r, rank);
+    }
   });
 }
 

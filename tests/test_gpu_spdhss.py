@@ -131,3 +131,23 @@ def test_rank_zero_gives_block_jacobi():
     rhs = inputs.rhs(n, 2, 6)
     x = u.solve(rhs).cpu().numpy()
     assert rel(Hg @ x, rhs) < 1e-11
+
+
+def test_tolerance_driven_sketch_growth_matches_oracle():
+    """spdhss_build_tol grows the sketch (first r + p columns, r doubling from 64) until the
+    ranks fit: the same attempts and the same result as the oracle's growing construction."""
+    api = need_gpu()
+    n, dim, leaf, kind, ell, sigma, tol, cap, p = 3000, 3, 100, "matern32", 0.3, 1e-2, 1e-8, 300, 10
+    tau = 1e-3                            # ranks up to 159: the sketch grows 64 -> 128 -> 256
+    X = inputs.uniform_cube(n, dim, 7)
+    Om = inputs.sketch(n, cap + p, 8)
+    h = api.H2(X, kind, ell, sigma, leaf, tol)
+    hs = api.HSS(h, cap, p, omega=Om, tol=tau)
+    Hg = gpu_dense(hs, n)
+    tr = OT.build_tree(X, leaf)
+    M = OH.dense(OH.build_h2(tr, X, OK.NAMES[kind], ell, sigma, tol))
+    ho = OS.build_spdhss_adaptive(tr, M, Om[tr.perm], cap, p, tau, r0=64)
+    assert 64 < ho.sketch_rank < cap      # the sketch grew and stopped below the cap
+    Ho = unsort(OS.assemble_dense(ho), tr.perm)
+    assert rel(Hg, Ho) < 1e-10
+    assert hs.info()["max_rank"] == max(ho.rank.values())
