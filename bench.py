@@ -734,7 +734,8 @@ def run_paper_table():
 def run_tol_sweep():
     """The paper's relative-tolerance experiment (Matern-3/2 with l = 0.25, i.e. length scale
     4, shift 1e-2, ball and sphere point sets of constant density): bases truncated at
-    tau = 1e-1 and 1e-2 (rank caps 200 and 600, oversampling 10), leaf boxes of up to 400
+    tau = 1e-1 and 1e-2 (largest ranks 200 and 600, the sketch growing from 64 + 10 columns
+    as needed, oversampling 10), leaf boxes of up to 400
     points, H^2 tolerance 1e-8; PCG iterations to relres 1e-4 with a right-hand side uniform
     on [-0.5, 0.5] (the paper's setting) and the average relative error of the SPD-HSS
     product against the H^2 product over 4 random vectors."""
