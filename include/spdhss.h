@@ -49,17 +49,26 @@ typedef enum {
 
 /* Kernel functions of Sec. 6, with a length scale ell that divides the distance r:
  * EXP exp(-r/ell); GAUSS exp(-r^2/ell^2); MATERN32 (1+sqrt3 r/ell) exp(-sqrt3 r/ell);
- * IMQ 1/sqrt(1 + r^2/ell^2).  K(x,x) = 1.  The matrix is A = shift*I + K(X,X). */
+ * IMQ 1/sqrt(1 + r^2/ell^2).  K(x,x) = 1.  The matrix is A = shift*I + K(X,X).
+ * RPY is the Rotne-Prager-Yamakawa tensor of Sec. 6 for 3D points, ell = the particle
+ * radius a (r = x - y):
+ *   r = 0: (1/a) I;   |r| >= 2a: 3/(4|r|)(I + rr^T/|r|^2) + 3a^2/(2|r|^3)(I/3 - rr^T/|r|^2);
+ *   |r| < 2a: (1/a)[(1 - 9|r|/(32a)) I + 3|r|/(32a) rr^T/|r|^2]
+ * (the overlap branch read with 1/a on both terms, the form continuous at |r| = 2a).  Its
+ * matrix has THREE unknowns per point: with n points it is 3n x 3n, row 3p + c being
+ * component c of point p, and every "n" below (block vector rows, h2_info[0], the
+ * exported permutation and index ranges, skeleton indices) counts unknowns, 3n. */
 typedef enum {
   SPDHSS_K_EXP = 0,
   SPDHSS_K_GAUSS = 1,
   SPDHSS_K_MATERN32 = 2,
-  SPDHSS_K_IMQ = 3
+  SPDHSS_K_IMQ = 3,
+  SPDHSS_K_RPY = 4
 } spdhss_kernel_kind;
 
 typedef struct {
   int kind;       /* spdhss_kernel_kind */
-  double ell;     /* length scale, > 0 */
+  double ell;     /* length scale (RPY: particle radius a), > 0 */
   double shift;   /* diagonal shift sigma >= 0 (Sec. 6.2) */
 } spdhss_kernel_desc;
 
@@ -73,7 +82,8 @@ typedef struct spdhss_ulv_s* ulv_handle;
  * Type-3 far pairs of Sec. 5.2.2) and a proxy-point H^2 representation whose
  * interpolative decompositions stop at relative pivot size `tol` (the paper uses 1e-8).
  *   points   n x dim row-major, HOST or DEVICE pointer (detected), read only.
- *   n >= 1, dim in {2, 3}, leaf_size >= 1, tol >= 0 (0 keeps full rank: exact H^2).
+ *   n >= 1 points, dim in {2, 3} (3 for RPY), leaf_size >= 1 points, tol >= 0 (0 keeps
+ *   full rank: exact H^2).  For RPY every proxy point carries the three components.
  *   out      receives a new handle; destroy with h2_destroy.
  * Errors: EINVAL for bad sizes, ENOMEM, ECUDA. */
 spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,

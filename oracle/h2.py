@@ -18,6 +18,10 @@ the reading used here:
   column-pivoted QR of K(P, X_cand), stopped when |R_kk| <= tol |R_00|;
   U = Pi [I; (R_11^{-1} R_12)^T], skeleton = candidates in pivot order;
 * coupling B_ij = K(X_skel_i, X_skel_j) for Type-3 pairs (no shift: off-diagonal blocks).
+* a vector-valued kernel (RPY, three unknowns per point) works on unknowns throughout:
+  the tree counts unknowns (tree.expand_dofs), every proxy point gives one row per
+  component (row 3t + c: component c of proxy point t), and the decomposition picks
+  skeleton unknowns.
 """
 from __future__ import annotations
 
@@ -84,7 +88,8 @@ class H2:
     kind: int
     ell: float
     sigma: float
-    Xs: np.ndarray          # points in sorted (tree) order
+    Xs: np.ndarray          # points in sorted (tree) order (of every unknown for RPY)
+    cs: np.ndarray          # component of every sorted unknown (None: scalar kernel)
     skel: list              # per node: indices into Xs (pivot order)
     U: list                 # per node: leaf basis (|I_i| x k_i) or transfer R_i (sum k_c x k_i)
     B: dict                 # (i, j) -> K(X_skel_i, X_skel_j) for Type-3 pairs
@@ -95,7 +100,11 @@ class H2:
 
 def build_h2(tree: Tree, X: np.ndarray, kind: int, ell: float, sigma: float, tol: float) -> H2:
     """Proxy-point H^2 (bottom-up ID of every node of depth >= 1)."""
-    Xs = np.asarray(X, dtype=np.float64)[tree.perm]
+    X = np.asarray(X, dtype=np.float64)
+    k_u = tree.dofs
+    Xs = X[tree.perm // k_u]
+    cs = tree.perm % k_u if k_u > 1 else None
+    sub = (lambda idx: cs[idx]) if k_u > 1 else (lambda idx: None)
     nn = tree.num_nodes
     skel = [np.zeros(0, np.int64) for _ in range(nn)]
     U = [np.zeros((0, 0)) for _ in range(nn)]
@@ -110,7 +119,10 @@ def build_h2(tree: Tree, X: np.ndarray, kind: int, ell: float, sigma: float, tol
                 skel[i] = np.zeros(0, np.int64)
                 U[i] = np.zeros((len(cand), 0))
                 continue
-            M = K.kernel_block(kind, ell, P, Xs[cand])          # |P| x |cand|
+            cP = None
+            if k_u > 1:
+                P, cP = np.repeat(P, k_u, axis=0), np.tile(np.arange(k_u), len(P))
+            M = K.kernel_block(kind, ell, P, Xs[cand], cP, sub(cand))   # |P| x |cand|
             # column-pivoted QR by LAPACK (dgeqp3), truncated at |R_kk| <= tol |R_00|
             R, piv = sla.qr(M, mode="r", pivoting=True)
             d = np.abs(np.diag(R))
@@ -125,8 +137,9 @@ def build_h2(tree: Tree, X: np.ndarray, kind: int, ell: float, sigma: float, tol
     B = {}
     for i in range(nn):
         for j in tree.far(i):
-            B[(i, int(j))] = K.kernel_block(kind, ell, Xs[skel[i]], Xs[skel[int(j)]])
-    return H2(tree, kind, ell, sigma, Xs, skel, U, B)
+            si, sj = skel[i], skel[int(j)]
+            B[(i, int(j))] = K.kernel_block(kind, ell, Xs[si], Xs[sj], sub(si), sub(sj))
+    return H2(tree, kind, ell, sigma, Xs, cs, skel, U, B)
 
 
 def explicit_basis(h2: H2, i: int) -> np.ndarray:
@@ -155,7 +168,9 @@ def dense(h2: H2) -> np.ndarray:
     for i in tree.nodes_at_depth(tree.D):
         for j in tree.near(i):
             bi, ei, bj, ej = tree.begin[i], tree.end[i], tree.begin[j], tree.end[j]
-            A[bi:ei, bj:ej] = K.kernel_block(h2.kind, h2.ell, h2.Xs[bi:ei], h2.Xs[bj:ej])
+            ci = h2.cs[bi:ei] if h2.cs is not None else None
+            cj = h2.cs[bj:ej] if h2.cs is not None else None
+            A[bi:ei, bj:ej] = K.kernel_block(h2.kind, h2.ell, h2.Xs[bi:ei], h2.Xs[bj:ej], ci, cj)
     ub = {}
     for (i, j), Bij in h2.B.items():
         for v in (i, j):

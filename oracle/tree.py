@@ -23,6 +23,7 @@ HSS level k (k = 1 leaves ... L root) is depth D + 1 - k.
 """
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -89,6 +90,7 @@ class Tree:
     far_off: np.ndarray
     far_idx: np.ndarray
     D: int = 0                  # depth of the leaf level
+    dofs: int = 1               # unknowns per point (n, perm, begin, end count unknowns)
 
     @property
     def num_nodes(self) -> int:
@@ -267,3 +269,14 @@ def _build_lists(tree: Tree) -> None:
         idx = np.array([v for x in lists for v in x], dtype=np.int64)
         setattr(tree, name + "_off", off)
         setattr(tree, name + "_idx", idx)
+
+
+def expand_dofs(tree: Tree, k: int) -> Tree:
+    """The same tree over k unknowns per point (a vector-valued kernel): unknown k*p + c is
+    component c of point p, in sorted and in original order alike, so every index range
+    and the permutation scale by k and the components of a point stay together."""
+    if k == 1:
+        return tree
+    perm = (tree.perm[:, None] * k + np.arange(k)[None, :]).reshape(-1)
+    return dataclasses.replace(tree, n=tree.n * k, perm=perm, begin=tree.begin * k,
+                               end=tree.end * k, dofs=k)

@@ -46,12 +46,14 @@ class H2:
             points = torch.from_numpy(np.ascontiguousarray(points, dtype=np.float64))
         points = points.to(torch.float64).contiguous()
         n, dim = points.shape
-        self.n, self.dim = int(n), int(dim)
+        # matrix size: three unknowns per point for the RPY tensor kernel
+        self.npoints, self.dim = int(n), int(dim)
+        self.n = self.npoints * N.DOFS.get(kernel, 1)
         self.kernel, self.ell, self.shift = kernel, float(ell), float(shift)
         self.leaf_size, self.tol = int(leaf_size), float(tol)
         kd = N.KernelDesc(N.KERNELS[kernel], float(ell), float(shift))
         h = ctypes.c_void_p()
-        N.check(N.lib().h2_build(_ptr(points), self.n, self.dim, kd, int(leaf_size), float(tol),
+        N.check(N.lib().h2_build(_ptr(points), self.npoints, self.dim, kd, int(leaf_size), float(tol),
                                  _stream(stream), ctypes.byref(h)))
         self._h = h
 
@@ -269,7 +271,8 @@ def build_batched(instances, stream=None):
         if st[k] != N.OK:
             out.append(None)
             continue
-        h = _wrap(H2, h2o[k], n=int(n[k]), dim=int(dim[k]), kernel=inst["kernel"],
+        h = _wrap(H2, h2o[k], n=int(n[k]) * N.DOFS.get(inst["kernel"], 1), npoints=int(n[k]),
+                  dim=int(dim[k]), kernel=inst["kernel"],
                   ell=float(inst["ell"]), shift=float(inst["shift"]),
                   leaf_size=int(inst["leaf_size"]), tol=float(inst["tol"]))
         hs = _wrap(HSS, hso[k], h2=h, rank=int(inst["rank"]),

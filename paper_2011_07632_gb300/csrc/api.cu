@@ -185,11 +185,12 @@ static std::unique_ptr<spdhss_h2_s> h2_build_one(const double* points, int64_t n
                                                  spdhss_kernel_desc kernel, int leaf_size,
                                                  double tol, cudaStream_t s) {
   SPD_REQUIRE(points != nullptr, "points is NULL");
-  SPD_REQUIRE(n >= 1 && n < (1LL << 40), "n out of range");
+  SPD_REQUIRE(n >= 1 && n < (1LL << 38), "n out of range");
   SPD_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
   SPD_REQUIRE(leaf_size >= 1, "leaf_size must be >= 1");
   SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
-  SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 3, "unknown kernel kind");
+  SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 4, "unknown kernel kind");
+  SPD_REQUIRE(kernel.kind != SPDHSS_K_RPY || dim == 3, "the RPY kernel needs dim 3");
   SPD_REQUIRE(kernel.ell > 0.0, "kernel length scale must be > 0");
   SPD_REQUIRE(kernel.shift >= 0.0, "shift must be >= 0");
   std::unique_ptr<spdhss_h2_s> h(new spdhss_h2_s());

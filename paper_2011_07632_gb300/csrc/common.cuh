@@ -185,6 +185,38 @@ __device__ __forceinline__ float kernel_r2_k(float r2, float inv_ell) {
   return rsqrtf(1.0f + r2 * (inv_ell * inv_ell));
 }
 
+// ---- the Rotne-Prager-Yamakawa tensor (Sec. 6), particle radius a ----------------------
+// A vector-valued kernel: the matrix has 3 unknowns per point, and its entry for the
+// unknowns (p, ci) and (q, cj) is the (ci, cj) entry of the 3 x 3 tensor K(x_p, x_q),
+// r = x_p - x_q:
+//   r = 0:        (1/a) I
+//   |r| >= 2a:    3/(4|r|) (I + rr^T/|r|^2) + 3a^2/(2|r|^3) (I/3 - rr^T/|r|^2)
+//   |r| <  2a:    (1/a) [ (1 - 9|r|/(32a)) I + 3|r|/(32a) rr^T/|r|^2 ]
+// (the overlap branch with 1/a on both terms: the form continuous at |r| = 2a).  Such a
+// handle stores each point three times in sorted order (unknown 3p + c is component c of
+// point p) with one more coordinate row holding the component c.
+constexpr int kRpyDofs = 3;
+__host__ __device__ inline int kernel_dofs(int kind) { return kind == SPDHSS_K_RPY ? kRpyDofs : 1; }
+
+template <class T>
+__device__ __forceinline__ T rpy_entry(T d0, T d1, T d2, int ci, int cj, T inv_a) {
+  const T r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  const T I = (ci == cj) ? T(1) : T(0);
+  if (r2 == T(0)) return I * inv_a;
+  const T di = ci == 0 ? d0 : (ci == 1 ? d1 : d2);
+  const T dj = cj == 0 ? d0 : (cj == 1 ? d1 : d2);
+  const T r = sqrt(r2);
+  const T rr = di * dj / r2;
+  const T a = T(1) / inv_a;
+  if (r >= T(2) * a) {
+    const T inv_r = T(1) / r;
+    return T(0.75) * inv_r * (I + rr) +
+           T(1.5) * a * a * (inv_r * inv_r * inv_r) * (I * T(1.0 / 3.0) - rr);
+  }
+  const T t = r * inv_a * T(1.0 / 32.0);
+  return inv_a * ((T(1) - T(9) * t) * I + T(3) * t * rr);
+}
+
 // Points are stored structure-of-arrays: coordinate a of point p at x[a * ldx + p].
 __device__ __forceinline__ double sqdist3(const double* __restrict__ x, int64_t ldx, int dim,
                                           int64_t p, double y0, double y1, double y2) {

@@ -83,10 +83,15 @@ static bool has_far_field(const TreeHost& T, int64_t i) {
 void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, int leaf_size,
                    cudaStream_t s) {
   build_tree(d_points, n, dim, leaf_size, s, h->th, h->td);
+  // a vector-valued kernel: from here on the tree counts unknowns, and every proxy point
+  // carries one row per component
+  expand_dofs(kernel_dofs(h->kfn.kind), s, h->th, h->td);
+  n = h->th.n;
   const TreeHost& T = h->th;
   const int64_t NN = T.nn();
   const int D = T.D;
-  const int np = proxy_count(dim);
+  const int crow = dim + (T.dofs > 1 ? 1 : 0);   // coordinate rows (+ component row)
+  const int np = proxy_count(dim) * T.dofs;
   const double hg = T.w / (double)(1LL << T.B);
 
   std::vector<int> rank(NN, 0), mrows(NN, 0);
@@ -154,7 +159,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
           p.xc = h->td.xs.p; p.ldxc = n; p.c0 = T.begin[i];
         } else {
           const int64_t cb = T.child_begin[i] - T.depth_off[t + 1];
-          p.xc = sx[t + 1].p; p.ldxc = (int64_t)sx[t + 1].n / dim; p.c0 = soff[t + 1][cb];
+          p.xc = sx[t + 1].p; p.ldxc = (int64_t)sx[t + 1].n / crow; p.c0 = soff[t + 1][cb];
         }
         p.cols = mrows[i];
         p.out = G.p + goff[b];
@@ -243,16 +248,16 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
       for (int64_t v : skel_local[o + k]) sidx.push_back(v);
     }
     const int64_t Kt = soff[t][nn];
-    sx[t].alloc((size_t)std::max<int64_t>(Kt, 1) * dim);
+    sx[t].alloc((size_t)std::max<int64_t>(Kt, 1) * crow);
     if (Kt > 0) {
       DevBuf<int64_t> di;
       di.upload(sidx, s);
-      k_gather_coords<<<ceil_div(Kt, 256), 256, 0, s>>>(h->td.xs.p, n, dim, di.p, Kt, sx[t].p);
+      k_gather_coords<<<ceil_div(Kt, 256), 256, 0, s>>>(h->td.xs.p, n, crow, di.p, Kt, sx[t].p);
       SPD_LAUNCHED();
       SPD_CUDA(cudaStreamSynchronize(s));
     }
-    // sx[t].n is used as the leading dimension holder: dim * Kt entries
-    if (Kt == 0) sx[t].n = dim;
+    // sx[t].n is used as the leading dimension holder: crow * Kt entries
+    if (Kt == 0) sx[t].n = crow;
   }
 
   // global skeleton arrays (node-major) and bases
@@ -289,11 +294,11 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
   SPD_CUDA(cudaStreamSynchronize(s));
   upool.clear();
   const int64_t K = h->Ktot;
-  h->skel_x.alloc((size_t)std::max<int64_t>(K, 1) * dim);
+  h->skel_x.alloc((size_t)std::max<int64_t>(K, 1) * crow);
   if (K > 0) {
     DevBuf<int64_t> di;
     di.upload(h->skel_idx, s);
-    k_gather_coords<<<ceil_div(K, 256), 256, 0, s>>>(h->td.xs.p, n, dim, di.p, K, h->skel_x.p);
+    k_gather_coords<<<ceil_div(K, 256), 256, 0, s>>>(h->td.xs.p, n, crow, di.p, K, h->skel_x.p);
     SPD_LAUNCHED();
     SPD_CUDA(cudaStreamSynchronize(s));
   }

@@ -97,10 +97,10 @@ struct spdhss_h2_s {
   double tol = 0;
   spd::TreeHost th;
   spd::TreeDev td;
-  // skeletons (sorted-order point indices, pivot order), node-major
+  // skeletons (sorted-order unknown indices, pivot order), node-major
   std::vector<int64_t> skel_off, skel_idx;
   int64_t Ktot = 0;
-  spd::DevBuf<double> skel_x;        // dim x Ktot, structure of arrays
+  spd::DevBuf<double> skel_x;        // (dim + component row if vector-valued) x Ktot, SoA
   // bases: leaf U_i (|I_i| x k_i) or transfer R_i (sum k_c x k_i), column-major
   std::vector<int64_t> U_off;
   std::vector<int> U_rows;

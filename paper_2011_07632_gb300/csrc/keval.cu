@@ -21,12 +21,20 @@ __global__ void __launch_bounds__(256) k_tiles(const TileProb* __restrict__ prob
     const int i = i0 + (e & 31), j = j0 + (e >> 5);
     if (i >= P.rows || j >= P.cols) continue;
     const int64_t pr = P.r0 + i, pc = P.c0 + j;
-    double r2 = 0.0;
-    for (int a = 0; a < dim; ++a) {
-      const double d = P.xr[a * P.ldxr + pr] - P.xc[a * P.ldxc + pc];
-      r2 += d * d;
+    double v;
+    if (kf.kind == SPDHSS_K_RPY) {
+      // component rows: index dim (= 3) of both point arrays
+      v = rpy_entry<double>(P.xr[pr] - P.xc[pc], P.xr[P.ldxr + pr] - P.xc[P.ldxc + pc],
+                            P.xr[2 * P.ldxr + pr] - P.xc[2 * P.ldxc + pc],
+                            (int)P.xr[3 * P.ldxr + pr], (int)P.xc[3 * P.ldxc + pc], kf.inv_ell);
+    } else {
+      double r2 = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        const double d = P.xr[a * P.ldxr + pr] - P.xc[a * P.ldxc + pc];
+        r2 += d * d;
+      }
+      v = kernel_r2(kf, r2);
     }
-    double v = kernel_r2(kf, r2);
     if (P.xr == P.xc && pr == pc) v += P.diag_add;
     P.out[i + (int64_t)j * P.ldo] = v;
   }
@@ -99,12 +107,14 @@ __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ pro
   const ProxyProb P = probs[w.x];
   const KernelFn kf = P.dim ? P.kf : kf_;
   const int dim = P.dim ? P.dim : dim_;
-  const int np = proxy_count(dim);
+  // a vector-valued kernel: row i is component i % kd of proxy point i / kd
+  const int kd = kernel_dofs(kf.kind);
+  const int np = proxy_count(dim) * kd;
   const int i0 = w.y, j0 = w.z;
   __shared__ double sy[3][64];
   if (threadIdx.x < 64 && i0 + threadIdx.x < np) {
     double y[3] = {0, 0, 0};
-    proxy_point(P, dim, i0 + threadIdx.x, y);
+    proxy_point(P, dim, (i0 + threadIdx.x) / kd, y);
     for (int a = 0; a < 3; ++a) sy[a][threadIdx.x] = y[a];
   }
   __syncthreads();
@@ -113,12 +123,20 @@ __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ pro
     const int i = i0 + ii;
     if (i >= np || j >= P.cols) continue;
     const int64_t pc = P.c0 + j;
-    double r2 = 0.0;
-    for (int a = 0; a < dim; ++a) {
-      const double d = sy[a][ii] - P.xc[a * P.ldxc + pc];
-      r2 += d * d;
+    double v;
+    if (kd > 1) {
+      v = rpy_entry<double>(sy[0][ii] - P.xc[pc], sy[1][ii] - P.xc[P.ldxc + pc],
+                            sy[2][ii] - P.xc[2 * P.ldxc + pc], i % kd,
+                            (int)P.xc[3 * P.ldxc + pc], kf.inv_ell);
+    } else {
+      double r2 = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        const double d = sy[a][ii] - P.xc[a * P.ldxc + pc];
+        r2 += d * d;
+      }
+      v = kernel_r2(kf, r2);
     }
-    P.out[i + (int64_t)j * P.ldo] = kernel_r2(kf, r2);
+    P.out[i + (int64_t)j * P.ldo] = v;
   }
 }
 
@@ -138,7 +156,9 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
   }
   std::vector<int4> work;
   for (int p = 0; p < (int)b.size(); ++p)
-    for (int i0 = 0, np = proxy_count(b.h[p].dim ? b.h[p].dim : dim); i0 < np; i0 += 64)
+    for (int i0 = 0, np = proxy_count(b.h[p].dim ? b.h[p].dim : dim) *
+                          kernel_dofs(b.h[p].dim ? b.h[p].kf.kind : k.kind);
+         i0 < np; i0 += 64)
       for (int j0 = 0; j0 < b.h[p].cols; j0 += 32) work.push_back(make_int4(p, i0, j0, 0));
   if (work.empty()) return;
   DevBuf<int4> dw;
@@ -165,12 +185,14 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restri
                                                     int dim_) {
   // source points staged per chunk; the staging area is reused for the final reduction
   constexpr int CH = NC >= 16 ? 192 : (NC >= 8 ? 256 : 512);
-  constexpr int STAGE = CH * (3 + NC);
+  constexpr bool RPY = KIND == SPDHSS_K_RPY;
+  constexpr int NX = RPY ? 4 : 3;   // staged coordinate rows (+ the component row)
+  constexpr int STAGE = CH * (NX + NC);
   constexpr int RED = NC * 256;
   __shared__ T smem[STAGE > RED ? STAGE : RED];
   T (*red)[256] = reinterpret_cast<T (*)[256]>(smem);
   T (*sx)[CH] = reinterpret_cast<T (*)[CH]>(smem);
-  T (*sv)[CH] = reinterpret_cast<T (*)[CH]>(smem + 3 * CH);
+  T (*sv)[CH] = reinterpret_cast<T (*)[CH]>(smem + NX * CH);
   const int2 w = work[blockIdx.x];
   const NearProbT<T> P = probs[w.x];
   const bool own = P.xs != nullptr;
@@ -190,10 +212,12 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restri
     const int p = t % m, g = t / m;
     const int64_t gp = P.row0 + rb + p;
     T y0 = 0, y1 = 0, y2 = 0;
+    int yc = 0;
     if (g < G) {
       y0 = (T)xs[gp];
       y1 = (T)xs[ldx + gp];
       if (dim == 3) y2 = (T)xs[2 * ldx + gp];
+      if (RPY) yc = (int)xs[3 * ldx + gp];
     }
     T acc[NC];
 #pragma unroll
@@ -213,6 +237,7 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restri
             sx[0][cnt + e] = (T)xs[gq];
             sx[1][cnt + e] = (T)xs[ldx + gq];
             sx[2][cnt + e] = (dim == 3) ? (T)xs[2 * ldx + gq] : (T)0;
+            if (RPY) sx[NX - 1][cnt + e] = (T)xs[3 * ldx + gq];
 #pragma unroll
             for (int c = 0; c < NC; ++c)
               sv[c][cnt + e] = (c < ncb) ? xin[q + e + (int64_t)c * S.ldx] : (T)0;
@@ -225,7 +250,15 @@ __global__ void __launch_bounds__(256) k_near_small(const NearProbT<T>* __restri
         if (t == 0) { s_seg = sg; s_q = q; }
       }
       if (g < G) {
-        if (dim == 3) {
+        if (RPY) {
+#pragma unroll 4
+          for (int q = g; q < cnt; q += G) {
+            const T kv = rpy_entry<T>(y0 - sx[0][q], y1 - sx[1][q], y2 - sx[2][q], yc,
+                                      (int)sx[NX - 1][q], inv_ell);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = kv * sv[c][q] + acc[c];
+          }
+        } else if (dim == 3) {
 #pragma unroll 4
           for (int q = g; q < cnt; q += G) {
             const T d0 = y0 - sx[0][q], d1 = y1 - sx[1][q], d2 = y2 - sx[2][q];
@@ -304,7 +337,8 @@ __device__ __forceinline__ void near_pairs(const NearProb& P, const NearSeg* __r
     for (int q0 = 0; q0 < S.cols; q0 += 32) {
       const int nq = min(32, S.cols - q0);
       if (t < 32 && t < nq)
-        for (int a = 0; a < dim; ++a) cx[a][t] = xs[a * ldx + S.col0 + q0 + t];
+        for (int a = 0; a < (KIND == SPDHSS_K_RPY ? 4 : dim); ++a)
+          cx[a][t] = xs[a * ldx + S.col0 + q0 + t];
       for (int e = t; e < 32 * 64; e += 256) {
         const int qq = e % 32, cc = e / 32;
         double v = 0.0;
@@ -316,12 +350,18 @@ __device__ __forceinline__ void near_pairs(const NearProb& P, const NearSeg* __r
         const int rr = e & 31, qq = e >> 5;
         double v = 0.0;
         if (rr < nr && qq < nq) {
-          double r2 = 0.0;
-          for (int a = 0; a < dim; ++a) {
-            const double d = rx[a][rr] - cx[a][qq];
-            r2 += d * d;
+          if (KIND == SPDHSS_K_RPY) {
+            v = rpy_entry<double>(rx[0][rr] - cx[0][qq], rx[1][rr] - cx[1][qq],
+                                  rx[2][rr] - cx[2][qq], (int)rx[3][rr], (int)cx[3][qq],
+                                  kf.inv_ell);
+          } else {
+            double r2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+              const double d = rx[a][rr] - cx[a][qq];
+              r2 += d * d;
+            }
+            v = kernel_r2_k<KIND>(r2, kf.inv_ell);
           }
-          v = kernel_r2_k<KIND>(r2, kf.inv_ell);
           if (S.self && (P.row0 + rb + rr) == (S.col0 + q0 + qq)) v += kf.shift;
         }
         Kt[qq][rr] = v;
@@ -353,8 +393,8 @@ __global__ void __launch_bounds__(256) k_near_pairs(const NearProb* __restrict__
                                                     int dim_) {
   __shared__ double Kt[32][33];
   __shared__ double Xt[32][65];
-  __shared__ double rx[3][32];
-  __shared__ double cx[3][32];
+  __shared__ double rx[4][32];   // coordinates (+ the component row of a vector kernel)
+  __shared__ double cx[4][32];
   const int2 w = work[blockIdx.x];
   const NearProb P = probs[w.x];
   const bool own = P.xs != nullptr;
@@ -368,7 +408,8 @@ __global__ void __launch_bounds__(256) k_near_pairs(const NearProb* __restrict__
   for (int rb = 0; rb < P.rows; rb += 32) {
     const int nr = min(32, P.rows - rb);
     if (threadIdx.x < nr)
-      for (int a = 0; a < dim; ++a) rx[a][threadIdx.x] = xs[a * ldx + P.row0 + rb + threadIdx.x];
+      for (int a = 0; a < (KIND == SPDHSS_K_RPY ? 4 : dim); ++a)
+        rx[a][threadIdx.x] = xs[a * ldx + P.row0 + rb + threadIdx.x];
     __syncthreads();
     const int ppt = (nr * ncb + 255) / 256;
     if (ppt <= 1) near_pairs<1, KIND>(P, segs, col0, ncb, rb, nr, kf, xs, ldx, dim, Kt, Xt, rx, cx);
@@ -539,6 +580,7 @@ void NearBatchT<T>::launch(const KernelFn& k, const double* xs, int64_t ldx, int
     case SPDHSS_K_EXP: k_near_small<T, NC, SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
     case SPDHSS_K_GAUSS: k_near_small<T, NC, SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
     case SPDHSS_K_MATERN32: k_near_small<T, NC, SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
+    case SPDHSS_K_RPY: k_near_small<T, NC, SPDHSS_K_RPY><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
     default: k_near_small<T, NC, SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break; \
   }
   switch (cb) {
@@ -553,6 +595,7 @@ void NearBatchT<T>::launch(const KernelFn& k, const double* xs, int64_t ldx, int
           case SPDHSS_K_EXP: k_near_pairs<SPDHSS_K_EXP><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
           case SPDHSS_K_GAUSS: k_near_pairs<SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
           case SPDHSS_K_MATERN32: k_near_pairs<SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
+          case SPDHSS_K_RPY: k_near_pairs<SPDHSS_K_RPY><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
           default: k_near_pairs<SPDHSS_K_IMQ><<<g, 256, 0, s>>>(pr, sg, wk, k, xs, ldx, dim); break;
         }
       } else {

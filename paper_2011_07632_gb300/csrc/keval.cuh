@@ -39,7 +39,8 @@ struct ProxyProb {
   const double* xc;
   int64_t ldxc, c0;
   int cols;
-  double* out;     // proxy_count(dim) x cols, column-major
+  double* out;     // proxy_count(dim) * kernel_dofs(kind) x cols, column-major (row i:
+                   // component i % kernel_dofs of proxy point i / kernel_dofs)
   int64_t ldo;
   KernelFn kf{};   // kernel and dimension of this problem (dim 0: the launch's)
   int dim = 0;

@@ -247,6 +247,39 @@ __global__ void k_gather_soa(const double* __restrict__ xin, const int64_t* __re
   for (int a = 0; a < dim; ++a) xout[a * n + p] = xin[a * n + o];
 }
 
+// unknowns of a vector-valued kernel: sorted unknown k*p + c is component c of sorted
+// point p, original unknown k*perm[p] + c; coordinates repeated, row `dim` holds c
+__global__ void k_expand_dofs(const double* __restrict__ xs, const int64_t* __restrict__ perm,
+                              int64_t n, int dim, int k, double* __restrict__ xd,
+                              int64_t* __restrict__ pd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t p = e / k;
+  const int c = (int)(e - p * k);
+  const int64_t N = n * k;
+  for (int a = 0; a < dim; ++a) xd[a * N + e] = xs[a * n + p];
+  xd[dim * N + e] = (double)c;
+  pd[e] = perm[p] * k + c;
+}
+
+void expand_dofs(int k, cudaStream_t s, TreeHost& th, TreeDev& td) {
+  if (k <= 1) return;
+  const int64_t n = th.n, N = n * k;
+  DevBuf<double> xd((size_t)(th.dim + 1) * N);
+  DevBuf<int64_t> pd(N);
+  k_expand_dofs<<<ceil_div(N, 256), 256, 0, s>>>(td.xs.p, td.perm.p, n, th.dim, k, xd.p, pd.p);
+  SPD_LAUNCHED();
+  SPD_CUDA(cudaStreamSynchronize(s));
+  td.xs = std::move(xd);
+  td.perm = std::move(pd);
+  th.n = N;
+  th.dofs = k;
+  for (auto& v : th.begin) v *= k;
+  for (auto& v : th.end) v *= k;
+  td.begin.upload(th.begin, s);
+  td.end.upload(th.end, s);
+}
+
 // ---------------------------------------------------------------------------------------
 // tree level by level
 // ---------------------------------------------------------------------------------------

@@ -7,8 +7,9 @@ namespace spd {
 
 // Host mirror of the tree (small: O(number of nodes + list entries)).
 struct TreeHost {
-  int64_t n = 0;
+  int64_t n = 0;                    // unknowns (points x dofs)
   int dim = 0;
+  int dofs = 1;                     // unknowns per point (3 for a vector-valued kernel)
   int leaf_size = 0;
   int B = 0;                        // bits per dimension of the finest grid
   int D = 0;                        // depth of the leaf level
@@ -40,6 +41,11 @@ struct TreeDev {
 // Builds the tree from device points (row-major n x dim).
 void build_tree(const double* d_points, int64_t n, int dim, int leaf_size, cudaStream_t s,
                 TreeHost& th, TreeDev& td);
+
+// Turns a point tree into a tree of k unknowns per point (k > 1): n, the permutation and
+// every index range count unknowns, unknown k*p + c being component c of point p; the
+// sorted coordinates gain a row (index dim) holding c.  No-op for k = 1.
+void expand_dofs(int k, cudaStream_t s, TreeHost& th, TreeDev& td);
 
 // Device exclusive scan of int64 values (in place); returns the total.
 int64_t exclusive_scan_i64(int64_t* d, int64_t n, cudaStream_t s);

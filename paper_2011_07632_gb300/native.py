@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "libspdhss.so")
 OK, EINVAL, ENOMEM, NOT_SPD, NO_CONVERGENCE, NUMERIC, TIMEOUT, ECUDA = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "NOT_SPD", 4: "NO_CONVERGENCE",
                 5: "NUMERIC", 6: "TIMEOUT", 7: "ECUDA"}
-KERNELS = {"exp": 0, "gauss": 1, "matern32": 2, "imq": 3}
+KERNELS = {"exp": 0, "gauss": 1, "matern32": 2, "imq": 3, "rpy": 4}
+DOFS = {"rpy": 3}   # unknowns per point of a vector-valued kernel
 
 
 class SpdhssError(RuntimeError):
