@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--tol-sweep", action="store_true",
                     help="tolerance-driven SPD-HSS on the paper's Matern ball/sphere "
                          "workload: PCG iterations and matvec errors at tau 1e-1 and 1e-2")
+    ap.add_argument("--rpy-sweep", type=str, default=None, metavar="N1,N2,...",
+                    help="the paper's RPY iteration runs at these particle counts")
     ap.add_argument("--rank-sweep", action="store_true",
                     help="fixed ranks 100 and 200 on the paper's Matern ball/sphere workload")
     ap.add_argument("--kernel-sweep", action="store_true",
@@ -650,6 +652,57 @@ def run_rank_sweep():
                       "dtype": "f64", "data": "synthetic"}))
 
 
+def run_rpy_sweep(sizes):
+    """The paper's RPY runs: particles of radius a = 0.29 and 0.42 (volume fractions about
+    0.1 and 0.3 at the unit density of the ball of radius (3N/4pi)^(1/3); the sphere of
+    radius (N/4pi)^(1/2) has unit surface density), 3N unknowns, no shift, H^2 tolerance
+    1e-8, leaf boxes of up to 400 particles; no preconditioner, block Jacobi (rank 0) and
+    SPD-HSS with r = 100 and 200 (oversampling 10); PCG to relres 1e-4 with a right-hand
+    side uniform on [-0.5, 0.5]; also the H^2 and SPD-HSS construction times."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs
+    rows = []
+    for pset in ("ball", "sphere"):
+        for n in sizes:
+            X = inputs.ball(n, 0) if pset == "ball" else inputs.sphere(n, 0)
+            pts = torch.from_numpy(X).cuda()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(3 * n, 1, 1))).cuda()
+            for a in (0.29, 0.42):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = api.H2(pts, "rpy", a, 0.0, 400, 1e-8)
+                torch.cuda.synchronize()
+                t_h2 = time.perf_counter() - t0
+                row = {"points": pset, "n": n, "unknowns": 3 * n, "a": a,
+                       "h2_build_s": round(t_h2, 3), "h2_max_rank": h.info()["max_rank"]}
+                if n <= 40000:
+                    x, it, rr = api.pcg_solve(h, None, b, tol=1e-4, maxit=3000)
+                    row["none"] = int(it.max())
+                for r in (0, 100, 200):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    hs = api.HSS(h, r, 10, seed=2)
+                    u = api.ULV(hs)
+                    torch.cuda.synchronize()
+                    t_b = time.perf_counter() - t0
+                    x, it, rr = api.pcg_solve(h, u, b, tol=1e-4, maxit=3000)
+                    key = "bj" if r == 0 else "r%d" % r
+                    row[key] = int(it.max())
+                    if r:
+                        row[key + "_build_s"] = round(t_b, 3)
+                    assert float(rr.max()) <= 1e-4
+                    u.close(); hs.close()
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+                h.close()
+                torch.cuda.empty_cache()
+    print(json.dumps({"metric": "PCG iterations for RPY kernel matrices",
+                      "workload": "rpy_a0.29-0.42_ball_sphere", "rows": rows,
+                      "dtype": "f64", "data": "synthetic"}))
+
+
 def run_kernel_sweep():
     """The paper's parameter sweep: Matern-3/2 kernel matrices sigma I + K_l on 320,000
     points in a ball (constant density), l from 0.001 to 1 (length scale 1/l), sigma 1e-2,
@@ -781,6 +834,9 @@ def main():
     args = parse()
     if args.tol_sweep:
         run_tol_sweep()
+        return
+    if args.rpy_sweep:
+        run_rpy_sweep([int(v) for v in args.rpy_sweep.split(",")])
         return
     if args.rank_sweep:
         run_rank_sweep()

@@ -199,7 +199,8 @@ spdhss_status ulv_solve_noalloc(ulv_handle ulv, const double* B, double* X, int 
  * Solves A X = B with the H^2 matrix A and the ULV-factored SPD HSS preconditioner, from
  * X_0 = 0, every column independently, until the relative residual of every column is
  * <= relres_tol (recursive residual, confirmed by a recomputed true residual) or maxit
- * iterations.
+ * iterations.  ulv = NULL runs unpreconditioned CG (the baseline of the paper's
+ * iteration tables); so does pcg_solve_mixed.
  *   B, X          n x nrhs column-major, leading dimension ld, original order; HOST or
  *                 DEVICE pointers (detected; host data is staged through the device).
  *   iters_out     HOST int[nrhs] or NULL: iterations taken per column.

@@ -204,7 +204,8 @@ class ULV:
 def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=None,
               raise_on_no_convergence: bool = False, mixed: bool = False):
     """PCG (Sec. 6.2): returns (X (n, nrhs), iterations per column, true relres per column).
-    mixed=True uses the FP32 product with A inside the iteration (pcg_solve_mixed).
+    mixed=True uses the FP32 product with A inside the iteration (pcg_solve_mixed);
+    ulv=None runs unpreconditioned CG.
 
     B may be a CUDA tensor (device path) or a CPU tensor / numpy array (host buffers: the
     library stages them through the device and X comes back on the host)."""
@@ -217,7 +218,8 @@ def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=
     it = (ctypes.c_int * nrhs)()
     rr = (ctypes.c_double * nrhs)()
     fn = N.lib().pcg_solve_mixed if mixed else N.lib().pcg_solve
-    st = fn(h2._h, ulv._h, _ptr(Bc), _ptr(Xc), nrhs, h2.n, float(tol), int(maxit), it, rr,
+    st = fn(h2._h, ulv._h if ulv is not None else None, _ptr(Bc), _ptr(Xc), nrhs, h2.n,
+            float(tol), int(maxit), it, rr,
             _stream(stream))
     if st != N.OK and not (st == N.NO_CONVERGENCE and not raise_on_no_convergence):
         N.check(st)

@@ -450,8 +450,8 @@ spdhss_status pcg_solve(h2_handle h2, ulv_handle u, const double* B, double* X, 
                         double* relres_out, void* stream) {
   spdhss_status st = spd::guarded("pcg_solve", [&] {
     spd::StreamScope ss((cudaStream_t)stream);
-    SPD_REQUIRE(h2 && u && B && X, "NULL argument");
-    SPD_REQUIRE(u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
+    SPD_REQUIRE(h2 && B && X, "NULL argument");
+    SPD_REQUIRE(!u || u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
     SPD_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     SPD_REQUIRE(ld >= h2->th.n, "ld must be >= n");
     SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
@@ -484,8 +484,8 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle u, const double* B, doubl
                               double* relres_out, void* stream) {
   return spd::guarded("pcg_solve_mixed", [&] {
     spd::StreamScope ss((cudaStream_t)stream);
-    SPD_REQUIRE(h2 && u && B && X, "NULL argument");
-    SPD_REQUIRE(u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
+    SPD_REQUIRE(h2 && B && X, "NULL argument");
+    SPD_REQUIRE(!u || u->hs->h2 == h2, "the ULV factorization belongs to another H2 matrix");
     SPD_REQUIRE(nrhs >= 1 && nrhs <= 16, "nrhs must be in [1, 16]");
     SPD_REQUIRE(ld >= h2->th.n, "ld must be >= n");
     SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");

@@ -254,11 +254,14 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   };
   H2Plan& PA = get_plan(nrhs);
   H2Plan& PR = get_plan(-nrhs);   // second plan (negative key) for residual checks
-  UlvPlan& PU = ulv_plan(u, nrhs, s);
+  // no factorization: plain CG (z = r)
+  UlvPlan* PU = u ? &ulv_plan(u, nrhs, s) : nullptr;
   double* p = PA.xs.p;
   double* q = PA.ys.p;
   H2PlanF* PF = precision ? &h2_plan_f(h2, nrhs, s) : nullptr;
-  double* z = PU.bw[0].p;
+  DevBuf<double> zown;
+  if (!PU) zown.alloc(nc);
+  double* z = PU ? PU->bw[0].p : zown.p;
   DevBuf<double> bs(nc), x(nc), r(nc), part((size_t)DOT_BLOCKS * nrhs), sc((size_t)4 * nrhs);
   DevBuf<int> done(nrhs);
   double* rz = sc.p;
@@ -291,7 +294,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   for (int c = 0; c < nrhs; ++c) hdone[c] = 0;
   // z = M^{-1} r, p = z, rz = r.z
   copy_vec(z, r.p, nc, s);
-  ulv_solve_sorted(u, PU, s);
+  if (PU) ulv_solve_sorted(u, *PU, s);
   copy_vec(p, z, nc, s);
   dots(r.p, z, n, nrhs, part.p, rz, s);
   std::vector<double> hrr(nrhs);
@@ -357,7 +360,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       copy_vec(r.p, PR.ys.p, nc, s);
     }
     copy_vec(z, r.p, nc, s);
-    ulv_solve_sorted(u, PU, s);                   // z = M^{-1} r
+    if (PU) ulv_solve_sorted(u, *PU, s);          // z = M^{-1} r
     dots(r.p, z, n, nrhs, part.p, rzn, s);
     update_p(p, z, n, nrhs, rzn, rz, done.p, s);
     copy_vec(rz, rzn, nrhs, s);

@@ -119,3 +119,22 @@ def test_rpy_large_sampled_rows():
     Xu, cu = OK.unknowns(OK.RPY, X)
     ye = np.vstack([OK.kernel_block(OK.RPY, 0.29, Xu[[q]], Xu, cu[[q]], cu) @ x for q in rows])
     assert np.abs(y[rows] - ye).max() / np.abs(ye).max() < 1e-7
+
+
+def test_unpreconditioned_cg_matches_oracle():
+    """ulv = None: plain CG on the H^2 matrix, against the oracle's iteration with the
+    identity preconditioner."""
+    api = need_gpu()
+    X = inputs.ball(900, 8)
+    h = api.H2(X, "rpy", 0.42, 0.0, 64, 1e-8)
+    b = inputs.rhs_uniform(h.n, 2, 3)
+    x, its, rr = api.pcg_solve(h, None, b, tol=1e-6)
+    assert np.all(rr <= 1e-6)
+    o = OT.expand_dofs(OT.build_tree(X, 64), 3)
+    Mo = _unsort(OH.dense(OH.build_h2(o, X, OK.RPY, 0.42, 0.0, 1e-8)), o.perm)
+    xo, ito, _ = OP.pcg(lambda v: Mo @ v, lambda v: v.copy(), b, 1e-6, 3000)
+    # plain CG over ~170 iterations (kappa ~ 2800) loses orthogonality at a rate set by
+    # rounding: the same iteration takes 166/169 steps in extended precision and 175/179
+    # in numpy FP64, so the counts agree to a few percent, not to one step
+    assert np.all(np.abs(its - ito) <= np.maximum(1, 0.05 * ito))
+    assert rel(x, xo) < 1e-5
