@@ -121,3 +121,21 @@ def test_regular_grid_interaction_counts():
     assert max(counts_far) == 189
     # depth 1: all 8 cells are mutually adjacent: no Type-3 pair
     assert all(len(tr.far(i)) == 0 for i in tr.nodes_at_depth(1))
+
+
+def test_expand_dofs_keeps_particles_together():
+    """Three unknowns per point: the permutation of unknowns is a permutation, every node
+    range covers whole particles, and sorted unknown 3s + c is component c of the point
+    the point tree puts at position s."""
+    X = inputs.uniform_cube(500, 3, 11)
+    t = T.build_tree(X, 16)
+    u = T.expand_dofs(t, 3)
+    assert u.n == 1500 and u.dofs == 3
+    assert np.array_equal(np.sort(u.perm), np.arange(1500))
+    assert np.array_equal(u.perm[0::3] // 3, t.perm) and np.all(u.perm % 3 == np.tile([0, 1, 2], 500))
+    assert np.array_equal(u.begin, 3 * t.begin) and np.array_equal(u.end, 3 * t.end)
+    for d in range(u.D + 1):
+        nodes = list(u.nodes_at_depth(d))
+        assert u.begin[nodes[0]] == 0 and u.end[nodes[-1]] == 1500
+        assert np.array_equal(u.end[nodes[:-1]], u.begin[nodes[1:]])
+    assert T.expand_dofs(t, 1) is t
