@@ -34,13 +34,18 @@ class Request:
     rank: int = 50
     oversample: int = 10
     seed: int = 0
-    rhs: Sequence[np.ndarray] = ()  # blocks (n, nrhs) solved with the same resident state
+    rhs: Sequence[np.ndarray] = ()  # blocks (unknowns, nrhs) solved with the same resident state
     relres: float = 1e-6
     maxit: int = 3000
 
     @property
     def n(self) -> int:
         return int(self.points.shape[0])
+
+    @property
+    def unknowns(self) -> int:
+        """Matrix size: three unknowns per point for the RPY tensor kernel."""
+        return self.n * (3 if self.kernel == "rpy" else 1)
 
 
 @dataclasses.dataclass
@@ -63,11 +68,13 @@ class Result:
 def footprint_bytes(req: Request) -> int:
     """Upper estimate of the device memory of one request: H^2 generators (couplings of up
     to ~190 far neighbours per leaf at leaf-sized ranks), SPD-HSS and ULV factors, the
-    sampling buffers of the construction, and the solve vectors."""
-    n, L, r = req.n, req.leaf_size, req.rank
+    sampling buffers of the construction, and the solve vectors.  Sizes count unknowns
+    (a leaf of L points holds 3L unknowns for the RPY kernel, and its ranks scale alike)."""
+    k = req.unknowns // max(req.n, 1)
+    n, L, r = req.unknowns, req.leaf_size * k, req.rank
     s = r + req.oversample
     nrhs = max((b.shape[1] if b.ndim == 2 else 1) for b in req.rhs) if len(req.rhs) else 1
-    h2 = 8 * n * (190 * min(L, 64) + 64)
+    h2 = 8 * n * (190 * min(L, 64 * k) + 64)
     hss = 8 * n * (6 * r + 4 * s + 2 * L)
     vec = 8 * n * (8 * s + 16 * nrhs)
     return int(h2 + hss + vec + (64 << 20))

@@ -83,3 +83,12 @@ def test_synthetic_stream_shape():
     assert all(1000 <= r.n <= 4000 for r in reqs)
     assert all(1 <= r.rhs[0].shape[1] <= 16 for r in reqs)
     assert serve.footprint_bytes(reqs[0]) > 0
+
+
+def test_footprint_counts_unknowns():
+    """An RPY request (three unknowns per point) is sized by its 3n unknowns."""
+    X = np.zeros((5000, 3))
+    scalar = serve.Request(rid=0, arrival=0.0, points=X, kernel="exp", leaf_size=64)
+    rpy = serve.Request(rid=1, arrival=0.0, points=X, kernel="rpy", leaf_size=64)
+    assert scalar.unknowns == 5000 and rpy.unknowns == 15000
+    assert serve.footprint_bytes(rpy) >= 3 * (serve.footprint_bytes(scalar) - (64 << 20))
