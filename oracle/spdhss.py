@@ -158,6 +158,93 @@ def build_spdhss(tree: Tree, M: np.ndarray, Omega: np.ndarray, r: int, factor: s
     return hss
 
 
+def _principal_basis(C: np.ndarray, r: int):
+    """Orthonormal V with col(V) in col(C) minimizing ||C - V V^T C||_F over r columns:
+    the leading left singular vectors (Eckart-Young); singular values <= RANK_RTOL times
+    the largest count as zero."""
+    if C.shape[0] == 0 or C.shape[1] == 0:
+        return 0, np.zeros((C.shape[0], 0))
+    Uc, sv, _ = np.linalg.svd(C, full_matrices=False)
+    k = int(min(r, np.sum(sv > RANK_RTOL * sv[0]))) if sv[0] > 0 else 0
+    return k, Uc[:, :k]
+
+
+def build_spdhss_deterministic(tree: Tree, M: np.ndarray, r: int, keep: bool = False) -> HSS:
+    """Alg. 4.1 as printed, without sketching: the leaf bases V_i minimize
+    ||C_ii^c - V_i V_i^T C_ii^c||_F for the explicitly scaled block row
+    C_ij = S_i^{-1} A_ij S_j^{-T} (j != i in lvl(1)), and above the leaves Vbar_i minimizes
+    ||E_ii^c - Vbar_i Vbar_i^T E_ii^c||_F (Eq. minimization) for
+    E_ij = (I + bold B_ii)^{-1/2} bold B_ij (I + bold B_jj)^{-1/2}, j != i in lvl(k), both
+    by a truncated SVD.  B_ij, R_i, U_i as in build_spdhss.  It measures what the sketch of
+    Sec. 5.2.1 costs in accuracy; keep=True stores every C_ii^c / E_ii^c in hss.target."""
+    hss = HSS(tree)
+    hss.target = {}
+    Lv = tree.L
+    leaves = list(tree.nodes_at_level(1)) if Lv > 1 else [0]
+    for i in leaves:
+        b, e = tree.begin[i], tree.end[i]
+        hss.D[i] = M[b:e, b:e].copy()
+        if Lv > 1:
+            hss.S[i] = np.linalg.cholesky(hss.D[i])
+    if Lv == 1:
+        return hss
+    for i in leaves:
+        b, e = tree.begin[i], tree.end[i]
+        blocks = []
+        for j in leaves:
+            if j == i:
+                continue
+            bj, ej = tree.begin[j], tree.end[j]
+            Cij = sla.solve_triangular(hss.S[i], M[b:e, bj:ej], lower=True)
+            blocks.append(sla.solve_triangular(hss.S[j], Cij.T, lower=True).T)   # C_ij S_j^{-T}
+        C = np.hstack(blocks) if blocks else np.zeros((e - b, 0))
+        k, V = _principal_basis(C, r)
+        if keep:
+            hss.target[i] = C
+        hss.Vbar[i] = V
+        hss.rank[i] = k
+        hss.Phi[i] = sla.solve_triangular(hss.S[i], V, lower=True, trans="T").T
+        hss.U[i] = hss.S[i] @ V
+    _all_pairs_B(hss, M, 1)
+    for k in range(2, Lv):
+        nodes = [int(i) for i in tree.nodes_at_level(k)]
+        off, Fh, Fmh = {}, {}, {}
+        for i in nodes:
+            kids = [int(c) for c in tree.children(i)]
+            off[i] = (kids, np.concatenate([[0], np.cumsum([hss.rank[c] for c in kids])]).astype(int))
+        def bold(i, j):
+            ki, oi = off[i]
+            kj, oj = off[j]
+            Bb = np.zeros((oi[-1], oj[-1]))
+            for a, ca in enumerate(ki):
+                for bb, cb in enumerate(kj):
+                    if ca != cb:
+                        Bb[oi[a]:oi[a + 1], oj[bb]:oj[bb + 1]] = hss.B[(ca, cb)]
+            return Bb
+        for i in nodes:
+            Bb = bold(i, i)
+            hss.Bbold[i] = Bb
+            Fh[i], Fmh[i] = _sym_power(Bb, 0.5), _sym_power(Bb, -0.5)
+        for i in nodes:
+            blocks = [Fmh[i] @ bold(i, j) @ Fmh[j] for j in nodes if j != i]
+            E = np.hstack(blocks) if blocks else np.zeros((off[i][1][-1], 0))
+            kk, Vb = _principal_basis(E, r)
+            if keep:
+                hss.target[i] = E
+            kids, oi = off[i]
+            b, e = tree.begin[i], tree.end[i]
+            PhiStack = np.zeros((oi[-1], e - b))
+            for a, c in enumerate(kids):
+                PhiStack[oi[a]:oi[a + 1], tree.begin[c] - b:tree.end[c] - b] = hss.Phi[c]
+            hss.Fhalf[i] = Fh[i]
+            hss.Vbar[i] = Vb
+            hss.rank[i] = kk
+            hss.Phi[i] = Vb.T @ Fmh[i] @ PhiStack
+            hss.R[i] = Fh[i] @ Vb
+        _all_pairs_B(hss, M, k)
+    return hss
+
+
 def _all_pairs_B(hss: HSS, M: np.ndarray, k: int) -> None:
     """B_ij = Phi_i M_ij Phi_j^T for every i != j in lvl(k) (Eq. bij_hss)."""
     tree = hss.tree
