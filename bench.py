@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--rank", type=int, default=WORKLOAD["rank"])
-    ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    # --problem-size: the same option under a name that torchrun's parser does not take for
+    # an abbreviation of its own --nnodes / --nproc-per-node
+    ap.add_argument("--n", "--problem-size", dest="n", type=int, default=WORKLOAD["n"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-at-scale", action="store_true")

@@ -59,3 +59,21 @@ def test_replicas_draw_different_inputs():
     a = inputs.uniform_cube(64, 3, 0 + 0)
     b = inputs.uniform_cube(64, 3, 0 + 1)
     assert not (a == b).all()
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """bench.py --impl reference launched like the GPU arm with two ranks (gloo on the CPU):
+    rank 0 alone times the oracle and prints one JSON line; the other rank exits 0."""
+    import json
+    import subprocess
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--problem-size", "300"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
