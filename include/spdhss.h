@@ -97,7 +97,8 @@ spdhss_status h2_matmul(h2_handle h2, const double* X, double* Y, int nrhs, int6
                         void* stream);
 
 /* Sizes of the tree and the H^2 data, written to the HOST array info[16]:
- *  [0] n  [1] dim  [2] number of tree nodes  [3] D (depth of the leaf level; HSS levels
+ *  [0] n (unknowns: 3 x points for RPY)  [1] dim  [2] number of tree nodes  [3] D (depth
+ *  of the leaf level; HSS levels
  *  L = D + 1)  [4] entries of all near lists  [5] entries of all far lists
  *  [6] total skeleton size (sum of H^2 ranks)  [7] bytes of stored H^2 generators
  *  (bases, transfers, couplings)  [8] near-field kernel entries per matvec
@@ -107,9 +108,9 @@ spdhss_status h2_info(h2_handle h2, int64_t* info);
 
 /* Export of the cluster tree for parity checks; every pointer is a HOST array sized from
  * h2_info (nn = info[2], nnear = info[4], nfar = info[5]); any pointer may be NULL.
- *   perm[n]           sorted position -> original point index
+ *   perm[n]           sorted position -> original index (of the unknown, for RPY)
  *   depth_off[D+2]    nodes of depth t are [depth_off[t], depth_off[t+1])
- *   begin[nn], end[nn]  point range in sorted order
+ *   begin[nn], end[nn]  range of sorted positions (unknowns for RPY: 3 x the points')
  *   parent[nn]        -1 for the root
  *   cell_lo[nn*dim], cell_hi[nn*dim]  integer cell on the finest grid, row-major
  *   near_off[nn+1], near_idx[nnear], far_off[nn+1], far_idx[nfar]  CSR lists */
@@ -120,7 +121,7 @@ spdhss_status h2_export_tree(h2_handle h2, int64_t* perm, int64_t* depth_off, in
 
 /* Export of the H^2 skeletons (HOST arrays): skel_off[nn+1] (node i owns
  * skel_idx[skel_off[i] .. skel_off[i+1]-1]), skel_idx[info[6]] = sorted-order point
- * indices in pivot order.  Either pointer may be NULL. */
+ * (for RPY: unknown) indices in pivot order.  Either pointer may be NULL. */
 spdhss_status h2_export_skeletons(h2_handle h2, int64_t* skel_off, int64_t* skel_idx);
 
 spdhss_status h2_destroy(h2_handle h2);
