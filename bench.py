@@ -321,6 +321,21 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
 DRAM_TRAFFIC = {"geqp3_h2_id": (75838464 + 16536064 + 75617280 + 12764416) / 2}
 
 
+def family_table(prof, fp64_peak):
+    """Per kernel family of the timed steps (library event timing): total ms, launches and,
+    where the family records its algorithmic FP64 flops, the achieved TFLOP/s and its
+    fraction of the FP64 peak; largest time first."""
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        row = {"ms": round(v["ms"], 3), "launches": v["launches"]}
+        if v.get("flops", 0.0) > 0.0 and v["ms"] > 0.0:
+            tf = v["flops"] / (v["ms"] / 1e3) / 1e12
+            row["tflops"] = round(tf, 4)
+            row["fp64_frac"] = round(tf / fp64_peak, 4)
+        out[k] = row
+    return out
+
+
 def replica_throughput(total_ms, steps, world, dist=None, device=None):
     """Whole-job throughput of `world` independent replicas that each ran `steps` steps in
     `total_ms` of their own device time: the job lasts as long as the slowest rank (max over
@@ -463,8 +478,7 @@ def run_gpu(args):
         "hss": hinfo,
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
         "at_scale": at_scale,
-        "clocks": clk.summary(), "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
-                                              for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "clocks": clk.summary(), "kernels": family_table(prof, fp64_peak),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -77,3 +77,14 @@ def test_reference_arm_under_torchrun_prints_once():
     line = lines[0]
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_family_table_reports_fp64_fraction():
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"a": {"ms": 10.0, "launches": 2, "flops": 6.0e9},
+            "b": {"ms": 30.0, "launches": 3, "flops": 0.0}}
+    t = bench.family_table(prof, 1.2)
+    assert list(t) == ["b", "a"]
+    assert t["a"]["tflops"] == pytest.approx(0.6) and t["a"]["fp64_frac"] == pytest.approx(0.5)
+    assert "tflops" not in t["b"] and t["b"]["launches"] == 3
