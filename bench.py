@@ -316,9 +316,34 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel family on
-# the n = 4096 workload, from one ncu capture of the current kernels: the two shared-memory
-# QR launches of one step's H^2 ID, averaged.  An entry is removed when its kernel changes.
-DRAM_TRAFFIC = {"geqp3_h2_id": (75838464 + 16536064 + 75617280 + 12764416) / 2}
+# the n = 4096 workload, from one ncu capture.  Each entry names the source files of the
+# family's kernels and a fingerprint of their text at the time of the capture: when the
+# files have changed since, the bench reports the traffic as null (stale capture).
+DRAM_TRAFFIC = {}
+
+
+def source_fingerprint(files):
+    """First 16 hex digits of the SHA-256 of the given package source files, in order."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2011_07632_gb300", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def measured_traffic(family):
+    """Per-launch DRAM bytes of a family from the capture table, or None when there is no
+    capture or the kernels' sources changed after it."""
+    e = DRAM_TRAFFIC.get(family)
+    if not e:
+        return None
+    try:
+        if source_fingerprint(e["sources"]) != e["sha16"]:
+            return None
+    except OSError:
+        return None
+    return e["bytes"]
 
 
 def family_table(prof, fp64_peak):
@@ -457,7 +482,7 @@ def run_gpu(args):
         achieved = (st["flops"] / max(st["launches"], 1)) / (per_launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": DRAM_TRAFFIC.get(top),
+                "traffic": measured_traffic(top),
                 "peak_source": "FP64 FMA units: 152 SMs x 2 FMA/clk x 2 flop x max SM clock",
                 "share_of_step": st["ms"] / max(total_ms, 1e-9),
                 "launches_per_step": st["launches"] / args.steps}

@@ -163,14 +163,19 @@ spdhss_status hss_info(hss_handle hss, int64_t* info);
 
 spdhss_status hss_destroy(hss_handle hss);
 
-/* ---- ULV factorization and solve ---------------------------------------------------
+/* ---- ULV factorization and solve (Sec. 1 and Sec. 6) -----------------------------------
+ * The paper factors the SPD HSS matrix with the ULV factorization it cites (Sec. 1; the
+ * reported construction times include it, Sec. 6) and applies the factors as the PCG
+ * preconditioner; it does not spell out the steps.
  * ulv_factor: symmetric ULV of the SPD HSS matrix (orthogonal compression of every
  * basis, Cholesky elimination of the complement, Schur update, dense Cholesky at the
- * root).  Errors: NOT_SPD if a pivot is not positive. */
+ * root).  Every Cholesky exists in exact arithmetic because the SPD HSS matrix is SPD
+ * (Sec. 3.2).  Errors: NOT_SPD if a pivot is not positive, ENOMEM, ECUDA. */
 spdhss_status ulv_factor(hss_handle hss, void* stream, ulv_handle* out);
 
-/* X = H^{-1} B.  B, X device, n x nrhs column-major, leading dimension ld, original
- * order; B and X may be the same array. */
+/* X = H^{-1} B: the forward and backward sweeps of the ULV factors (the preconditioner
+ * apply of Sec. 6).  B, X device, n x nrhs column-major, leading dimension ld, original
+ * order; B and X may be the same array.  Errors: EINVAL, ENOMEM, ECUDA. */
 spdhss_status ulv_solve(ulv_handle ulv, const double* B, double* X, int nrhs, int64_t ld,
                         void* stream);
 
@@ -180,19 +185,27 @@ spdhss_status ulv_destroy(ulv_handle ulv);
  * application whose device memory is all reserved by its own allocator, or a latency-
  * critical path that cannot accept the device-wide synchronization of cudaMalloc and
  * cudaFree).  The paper has no counterpart: this is a property of the library, not of the
- * method.  The call allocates nothing: it works in two fixed device arrays that are part of
- * the library image (48 MiB of level buffers, 8 MiB of launch descriptors), held by every
- * GPU that loads the library until the process exits.
+ * method.  The call allocates no device memory: it works in two fixed device arrays that
+ * are part of the library image (48 MiB of level buffers, 8 MiB of launch descriptors),
+ * held by every GPU that loads them until the process exits.
  *   B, X     DEVICE pointers, n x nrhs column-major, leading dimension ld >= n, original
  *            point order; B and X may be the same array.
  *   Limit:   the level buffers need about (n + sum of the block sizes above the leaves) x
  *            nrhs doubles (roughly 2 to 3 x n x nrhs); a call that needs more than 6 Mi
  *            doubles, or more than 8 MiB of descriptors, returns EINVAL and does nothing.
- *   The first call on a device looks up the arrays' device addresses (once per device, with
- *   that device current); make that first call before any stream capture.
+ *   Loading: the library's device code is loaded lazily, and loading the two arrays takes
+ *            their 56 MiB from the device.  ulv_factor, which allocates anyway, loads them
+ *            on its device and looks up their addresses (once per device, with that device
+ *            current), so that this call allocates nothing.  Only a call on a device where
+ *            no ulv_factor has run loads them itself; make that first call before any
+ *            stream capture.
+ *   Descriptors: built on the host once per (handle, nrhs) and kept, unchanged, by the
+ *            handle until ulv_destroy; every call copies them into the descriptor array
+ *            (a host-to-device copy of a few KB to a few MB on `stream`).
  *   Every call shares the two arrays and leaves its data there; nothing needs to start at
  *   zero.  Calls whose work overlaps on the GPU (different streams) race on the arrays:
- *   serialize them, e.g. on one stream. */
+ *   serialize them, e.g. on one stream.
+ * Errors: EINVAL (NULL pointer, nrhs < 1, ld < n, sizes over the arrays), ECUDA. */
 spdhss_status ulv_solve_noalloc(ulv_handle ulv, const double* B, double* X, int nrhs,
                                 int64_t ld, void* stream);
 

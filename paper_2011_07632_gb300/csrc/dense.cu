@@ -947,8 +947,10 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------------------
 // Householder QR with column pivoting; a cluster of C CTAs shares one matrix, CTA q owning
-// the column positions p with p % C == q.  Pivot norms are recomputed from the updated
-// trailing rows at every step; ties go to the lowest position.
+// the column positions p with p % C == q.  Pivot norms are downdated after every step and
+// recomputed from the trailing rows when the downdate loses accuracy (qr_downdate below),
+// or recomputed at every step when the problem asks for it (downdate = 0); ties go to the
+// lowest position.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void argmax_merge(double& v, int& p, double v2, int p2) {
   if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }

@@ -27,6 +27,8 @@ __global__ void k_triu(const double* const* __restrict__ src, const int64_t* __r
 }
 
 void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
+  // the allocation-free solve's arrays are loaded here, where allocating is allowed
+  ulv_noalloc_prepare_device();
   const spdhss_h2_s* h2 = hs->h2;
   const TreeHost& T = h2->th;
   const int64_t n = T.n;

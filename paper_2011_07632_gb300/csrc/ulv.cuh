@@ -22,6 +22,12 @@ struct UlvPlan {
   GemmBatch root_f, root_b;                  // t = L^{-1} b ; b = L^{-T} t
 };
 
+// State of the allocation-free solve for one column count (ulv_noalloc.cu).
+struct NoallocPlan;
+// Looks up the allocation-free solve's device arrays on the current device (once per
+// device); loading them is the one allocation they need, so ulv_factor makes it.
+void ulv_noalloc_prepare_device();
+
 }  // namespace spd
 
 struct spdhss_ulv_s {
@@ -37,6 +43,7 @@ struct spdhss_ulv_s {
   std::vector<int64_t> Foff;
   spd::DevBuf<double> Fbuf, Bbuf, rootF, rootB;
   std::map<int, std::unique_ptr<spd::UlvPlan>> plans;
+  std::map<int, std::shared_ptr<spd::NoallocPlan>> noalloc_plans;   // ulv_solve_noalloc
   size_t stored_bytes() const { return Dbuf.bytes() + Wbuf.bytes() + taub.bytes() + Ubuf.bytes() + root.bytes(); }
 };
 
@@ -45,4 +52,6 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s);
 UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s);
 // in place on plan.bw[0] (sorted order, n x ncol, ld n)
 void ulv_solve_sorted(const spdhss_ulv_s* u, const UlvPlan& p, cudaStream_t s);
+void ulv_solve_noalloc_impl(spdhss_ulv_s* u, const double* B, double* X, int ncol, int64_t ld,
+                            cudaStream_t s);
 }  // namespace spd

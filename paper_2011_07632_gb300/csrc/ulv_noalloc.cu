@@ -6,16 +6,29 @@
 // buffers and launch descriptors on first use per column count; this variant instead
 // works in two fixed file-scope device arrays: one for the level buffers (48 MiB) and one
 // for the launch descriptors (8 MiB).  They are part of the library's device image, so
-// every GPU that loads the library holds them until the process exits.
+// every GPU that loads them holds them until the process exits.
 //
-// Their device addresses are looked up once per device (cudaGetSymbolAddress, with that
-// device current) by the first call made on it.  Every call shares the two arrays and
-// leaves its data in them; the solve writes every element it later reads (the right-hand
-// side into the leaf-level buffer, the reduced parts into every block above), so nothing
-// has to start at zero.  Two calls whose work overlaps on the GPU (different streams)
-// race on the arrays.
+// The library's modules are loaded lazily: the module holding the two arrays is loaded
+// (its 56 MiB taken from the device) the first time their addresses are looked up.  That
+// look-up (cudaGetSymbolAddress, with the device current) is made once per device by
+// ulv_factor, which allocates anyway, so that the solve itself allocates nothing; a solve
+// on a device where no factorization has run makes the look-up itself.
+//
+// The descriptors of one column count depend only on the handle and the device's arrays:
+// they are built once per (handle, column count) into a host image that the handle keeps
+// unchanged until it is destroyed, and every call copies that image into the descriptor
+// array.  Every call shares the two arrays and leaves its data in them; the solve writes
+// every element it later reads (the right-hand side into the leaf-level buffer, the
+// reduced parts into every block above), so nothing has to start at zero.  Two calls
+// whose work overlaps on the GPU (different streams) race on the arrays.
+//
+// The sweeps are those of the ULV solve in the reflector-and-substitution form: each
+// node's stored Householder reflectors (Wbuf, taub) and its complement Cholesky factor
+// (Dbuf) are applied directly, where ulv_solve multiplies by the explicit per-node solve
+// matrices made from the same factors.  Both are exact forms of the same solve.
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "ulv.cuh"
@@ -59,6 +72,12 @@ DeviceArrays arrays_for_current_device() {
   return a;
 }
 
+}  // namespace
+
+void ulv_noalloc_prepare_device() { (void)arrays_for_current_device(); }
+
+namespace {
+
 // Host image of the descriptor array: typed blocks at 256-byte aligned offsets.
 struct Stage {
   std::vector<unsigned char> bytes;
@@ -81,17 +100,29 @@ struct LevelOps {
 
 }  // namespace
 
-void ulv_solve_noalloc_impl(const spdhss_ulv_s* u, const double* B, double* X, int ncol,
-                            int64_t ld, cudaStream_t s) {
-  const DeviceArrays dev = arrays_for_current_device();
+// Everything one column count needs: the host image of the descriptors (never modified
+// once built), the offsets of its blocks and the level buffers' layout in the scratch.
+struct NoallocPlan {
+  Stage st;
+  std::vector<LevelOps> ops;
+  std::vector<int64_t> boff;
+  size_t orf = 0, orb = 0, orw = 0;
+  int64_t nrw = 0;
+  double* scratch = nullptr;
+};
+
+// The plan of one column count for the current device (EINVAL when it exceeds the arrays).
+static std::shared_ptr<NoallocPlan> noalloc_plan(const spdhss_ulv_s* u, int ncol,
+                                                 const DeviceArrays& dev) {
   const TreeHost& T = u->hs->h2->th;
   const int64_t n = T.n;
   const int L = u->L, D = u->D;
   const int nlev = std::max(L - 1, 0);
-  const int64_t* perm = u->hs->h2->td.perm.p;
-
+  std::shared_ptr<NoallocPlan> plan = std::make_shared<NoallocPlan>();
+  plan->scratch = dev.scratch;
   // ---- level buffers inside the scratch array --------------------------------------
-  std::vector<int64_t> ldk(nlev + 1, 0), boff(nlev + 2, 0);
+  std::vector<int64_t> ldk(nlev + 1, 0);
+  std::vector<int64_t>& boff = plan->boff;
   std::vector<int64_t> moff(T.nn(), 0);
   if (D == 0) {
     ldk.assign(1, n);
@@ -121,9 +152,9 @@ void ulv_solve_noalloc_impl(const spdhss_ulv_s* u, const double* B, double* X, i
   auto bw = [&](int k) { return dev.scratch + boff[k]; };
 
   // ---- descriptors (host image, then one copy into the descriptor array) ----------------
-  static thread_local Stage st;
-  st.bytes.clear();
-  std::vector<LevelOps> ops(nlev);
+  Stage& st = plan->st;
+  std::vector<LevelOps>& ops = plan->ops;
+  ops.assign(nlev, LevelOps());
   for (int k = 1; k <= nlev; ++k) {
     const int t = D + 1 - k;
     const int64_t ldb = ldk[k - 1], ldn = ldk[k];
@@ -200,7 +231,10 @@ void ulv_solve_noalloc_impl(const spdhss_ulv_s* u, const double* B, double* X, i
     rb.push_back(TrsmProb{u->root.p, mr, top, ldtop, mr, ncol, 1, 1});
     for (int c = 0; c < ncol; ++c) rw.push_back(make_int2(0, c));
   }
-  const size_t orf = st.put(rf), orb = st.put(rb), orw = st.put(rw);
+  plan->orf = st.put(rf);
+  plan->orb = st.put(rb);
+  plan->orw = st.put(rw);
+  plan->nrw = (int64_t)rw.size();
   if (st.bytes.size() > kDescBytes) {
     char msg[200];
     std::snprintf(msg, sizeof(msg),
@@ -208,11 +242,31 @@ void ulv_solve_noalloc_impl(const spdhss_ulv_s* u, const double* B, double* X, i
                   "holds %zu (8 MiB); use fewer columns or ulv_solve", st.bytes.size(), kDescBytes);
     throw Error(SPDHSS_EINVAL, msg);
   }
-  if (!st.bytes.empty())
-    SPD_CUDA(cudaMemcpyAsync(dev.desc, st.bytes.data(), st.bytes.size(), cudaMemcpyHostToDevice, s));
-  auto D_ = [&](size_t off) { return (const void*)(dev.desc + off); };
+  return plan;
+}
 
-  // ---- the solve: same sweeps as ulv_solve -----------------------------------------------
+void ulv_solve_noalloc_impl(spdhss_ulv_s* u, const double* B, double* X, int ncol, int64_t ld,
+                            cudaStream_t s) {
+  const DeviceArrays dev = arrays_for_current_device();
+  const int64_t n = u->hs->h2->th.n;
+  const int nlev = std::max(u->L - 1, 0);
+  const int D = u->D;
+  const int64_t* perm = u->hs->h2->td.perm.p;
+  std::shared_ptr<NoallocPlan>& slot = u->noalloc_plans[ncol];
+  if (!slot || slot->scratch != dev.scratch) slot = noalloc_plan(u, ncol, dev);
+  const NoallocPlan& P = *slot;
+  const std::vector<LevelOps>& ops = P.ops;
+  auto bw = [&](int k) { return dev.scratch + P.boff[k]; };
+  // the plan's descriptor image, unchanged since it was built, into the descriptor array
+  if (!P.st.bytes.empty())
+    SPD_CUDA(cudaMemcpyAsync(dev.desc, P.st.bytes.data(), P.st.bytes.size(),
+                             cudaMemcpyHostToDevice, s));
+  auto D_ = [&](size_t off) { return (const void*)(dev.desc + off); };
+  const size_t orf = P.orf, orb = P.orb, orw = P.orw;
+  const int64_t nrw = P.nrw;
+  (void)D;
+
+  // ---- the solve: ULV sweeps up the levels, root solves, sweeps down ------------------
   permute_to_sorted(B, ld, bw(0), n, ncol, perm, s);
   for (int k = 0; k < nlev; ++k) {
     const LevelOps& o = ops[k];
@@ -222,8 +276,8 @@ void ulv_solve_noalloc_impl(const spdhss_ulv_s* u, const double* B, double* X, i
                     o.nft, o.nbf, s);
     copy_launch_raw((const CopyProb*)D_(o.up), o.ncp, o.cmax, s);
   }
-  trsm_launch_raw((const TrsmProb*)D_(orf), (const int2*)D_(orw), (int64_t)rw.size(), s);
-  trsm_launch_raw((const TrsmProb*)D_(orb), (const int2*)D_(orw), (int64_t)rw.size(), s);
+  trsm_launch_raw((const TrsmProb*)D_(orf), (const int2*)D_(orw), nrw, s);
+  trsm_launch_raw((const TrsmProb*)D_(orb), (const int2*)D_(orw), nrw, s);
   for (int k = nlev - 1; k >= 0; --k) {
     const LevelOps& o = ops[k];
     copy_launch_raw((const CopyProb*)D_(o.dn), o.ncp, o.cmax, s);

@@ -44,6 +44,12 @@ def test_noalloc_matches_ulv_solve_twice(n, leaf, r):
         assert rel(got, ref) < 1e-12
 
 
+def _raw(native, torch, u, Bc, Xc, nrhs, n):
+    return native.lib().ulv_solve_noalloc(u._h, ctypes.c_void_p(Bc.data_ptr()),
+                                          ctypes.c_void_p(Xc.data_ptr()), nrhs, n,
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
 def test_noalloc_allocates_nothing_and_rejects_oversize():
     api = need_gpu()
     import torch
@@ -52,28 +58,60 @@ def test_noalloc_allocates_nothing_and_rejects_oversize():
     X = inputs.uniform_cube(n, 3, 5)
     h = api.H2(X, "exp", 1.0, 1e-2, 64, 1e-8)
     hs = api.HSS(h, 20, 10, seed=2)
-    u = api.ULV(hs)
+    u = api.ULV(hs)          # the factorization loads the fixed arrays on this device
     B = inputs.rhs(n, 2, 1)
-    st, _ = _call_noalloc(native, torch, u, B, 2, n)      # first call: per-device set-up
-    assert st == native.OK
-    torch.cuda.synchronize()
     Bc = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
     Xc = torch.empty_like(Bc)
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
+    # the first call (a fresh process: the first on this device) and the ones after it
     for _ in range(3):
-        s = native.lib().ulv_solve_noalloc(u._h, ctypes.c_void_p(Bc.data_ptr()),
-                                           ctypes.c_void_p(Xc.data_ptr()), 2, n,
-                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-        assert s == native.OK
+        assert _raw(native, torch, u, Bc, Xc, 2, n) == native.OK
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
     # more columns than the fixed level buffers hold: a clear EINVAL, nothing done
     big = 2500
     Bb = torch.zeros((big, n), dtype=torch.float64, device="cuda")
     Xb = torch.zeros_like(Bb)
-    s = native.lib().ulv_solve_noalloc(u._h, ctypes.c_void_p(Bb.data_ptr()),
-                                       ctypes.c_void_p(Xb.data_ptr()), big, n,
-                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert s == native.EINVAL
+    assert _raw(native, torch, u, Bb, Xb, big, n) == native.EINVAL
     assert b"48 MiB" in native.lib().spdhss_last_error()
+
+
+def test_noalloc_in_place():
+    """B and X the same array: the result equals ulv_solve's."""
+    api = need_gpu()
+    import torch
+    from paper_2011_07632_gb300 import native
+    n = 2500
+    X = inputs.uniform_cube(n, 2, 6)
+    h = api.H2(X, "gauss", 0.1, 1e-3, 64, 1e-8)
+    hs = api.HSS(h, 25, 10, seed=3)
+    u = api.ULV(hs)
+    B = inputs.rhs(n, 4, 2)
+    ref = u.solve(B).cpu().numpy()
+    Bc = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    assert _raw(native, torch, u, Bc, Bc, 4, n) == native.OK
+    torch.cuda.synchronize()
+    assert rel(Bc.t().cpu().numpy(), ref) < 1e-12
+
+
+def test_noalloc_rejects_too_many_descriptors():
+    """Many small leaves: the launch descriptors (one work item per node and column) outgrow
+    their 8 MiB array before the level buffers outgrow theirs."""
+    api = need_gpu()
+    import torch
+    from paper_2011_07632_gb300 import native
+    n = 2000
+    X = inputs.uniform_cube(n, 3, 7)
+    h = api.H2(X, "exp", 1.0, 1e-2, 4, 1e-8)
+    hs = api.HSS(h, 2, 4, seed=5)
+    u = api.ULV(hs)
+    msg = None
+    for nrhs in (32, 64, 128, 256, 512, 1024):
+        Bc = torch.zeros((nrhs, n), dtype=torch.float64, device="cuda")
+        st = _raw(native, torch, u, Bc, Bc, nrhs, n)
+        if st != native.OK:
+            assert st == native.EINVAL
+            msg = native.lib().spdhss_last_error()
+            break
+    assert msg is not None and b"8 MiB" in msg, msg
