@@ -248,13 +248,17 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
  * copies) takes the nodes of all instances at the same step, so the GPU sees one launch
  * per step instead of one per step and instance.  Instances at different steps (other
  * depths, other iteration counts) form separate launches; an instance that fails leaves
- * the sweep without stopping the others.  Results agree with the one-instance calls up to
- * floating-point summation order (kernel variants are chosen for the merged launch).
+ * the sweep without stopping the others.  Every instance's results are bit-identical to
+ * those of the one-instance calls: each kernel's per-problem arithmetic (variant, split of
+ * a sum over CTAs, lanes per column) is fixed by that problem and its own instance, never
+ * by the other instances sharing a launch.
  * All work runs on `stream`.  Arrays are HOST arrays of `count` entries.
  *
  * spdhss_build_batched: for instance i, h2_build(points[i], n[i], dim[i], kernel[i],
- *   leaf_size[i], tol[i]) -> spdhss_build(rank[i], oversample[i], omega NULL, seed[i]) ->
- *   ulv_factor.  points[i]: n[i] x dim[i] column-major, HOST or DEVICE.  Outputs: HOST
+ *   leaf_size[i], tol[i]) -> spdhss_build(rank[i], oversample[i], omega[i], seed[i]) ->
+ *   ulv_factor.  points[i]: n[i] x dim[i] column-major, HOST or DEVICE.  omega: NULL, or a
+ *   HOST array of `count` entries, each NULL (the sketch drawn from seed[i]) or a DEVICE
+ *   n[i] x (rank[i] + oversample[i]) column-major sketch as spdhss_build's.  Outputs: HOST
  *   arrays of handles (NULL entry where that instance failed) and status[i] per instance
  *   (may be NULL).  Returns OK when every instance succeeded, else the first failing
  *   instance's status (spdhss_last_error names it).  The caller destroys the handles.
@@ -266,7 +270,8 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
 spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
-                                   const int* oversample, const uint64_t* seed, void* stream,
+                                   const int* oversample, const uint64_t* seed,
+                                   const double* const* omega, void* stream,
                                    h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
                                    spdhss_status* status);
 spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,

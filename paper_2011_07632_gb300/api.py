@@ -240,7 +240,8 @@ def build_batched(instances, stream=None):
     instances, with the batched kernel launches of all instances merged step by step.
 
     instances: list of dicts with keys points ((n, dim) array or tensor), kernel, ell,
-    shift, leaf_size, tol, rank, oversample (default 10), seed (default 0).
+    shift, leaf_size, tol, rank, oversample (default 10), seed (default 0), omega (optional
+    (n, rank + oversample) sketch, else drawn on the device from seed).
     Returns (list of (H2, HSS, ULV) or None per instance, per-instance status codes,
     (merged launches, hand-overs))."""
     m = len(instances)
@@ -262,10 +263,20 @@ def build_batched(instances, stream=None):
     rank = (ctypes.c_int * m)(*[int(i["rank"]) for i in instances])
     over = (ctypes.c_int * m)(*[int(i.get("oversample", 10)) for i in instances])
     seed = (ctypes.c_uint64 * m)(*[int(i.get("seed", 0)) for i in instances])
+    oms = []
+    for k, inst in enumerate(instances):
+        om = inst.get("omega")
+        if om is not None:
+            om = _colmajor(om)
+            assert om.shape == (int(inst["rank"]) + int(inst.get("oversample", 10)),
+                                int(pts[k].shape[0]))
+        oms.append(om)
+    keep.extend(o for o in oms if o is not None)
+    omp = (ctypes.c_void_p * m)(*[o.data_ptr() if o is not None else None for o in oms])
     h2o, hso, ulo = (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)()
     st = (ctypes.c_int * m)()
     rc = N.lib().spdhss_build_batched(m, ptr, _i64(n), dim, kd, leaf, tol, rank, over, seed,
-                                      _stream(stream), h2o, hso, ulo, st)
+                                      omp, _stream(stream), h2o, hso, ulo, st)
     if rc != N.OK and all(v == N.OK for v in st):
         N.check(rc)
     out = []

@@ -558,7 +558,8 @@ extern "C" {
 spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
-                                   const int* oversample, const uint64_t* seed, void* stream,
+                                   const int* oversample, const uint64_t* seed,
+                                   const double* const* omega, void* stream,
                                    h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
                                    spdhss_status* status) {
   std::vector<spdhss_status> st;
@@ -580,7 +581,8 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
       std::unique_ptr<spdhss_h2_s> h =
           h2_build_one(points[i], n[i], dim[i], kernel[i], leaf_size[i], tol[i], s);
       std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-      spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], nullptr, seed[i], s, 0.0);
+      spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], omega ? omega[i] : nullptr,
+                        seed[i], s, 0.0);
       std::unique_ptr<spdhss_ulv_s> u(new spdhss_ulv_s());
       ulv_factor_impl(u.get(), hs.get(), s);
       ulv_out[i] = u.release();

@@ -377,14 +377,20 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
         for (int n0 = 0; n0 < lprobs[p].N; n0 += tn) vt.push_back(make_int4(p, m0, n0, 0));
     }
     if (vt.empty()) continue;
-    // matrix-vector-like products on too few tiles to fill the GPU: split the K range of
-    // each tile over several CTAs (partial sums, added in order by k_gemm_kreduce)
-    if (v >= 1 && v <= 4 && (int64_t)vt.size() < 2 * 152) {
-      const int want = (int)std::min<int64_t>(16, ceil_div(4 * 152, (int64_t)vt.size()));
+    // matrix-vector-like products of few tiles: split the K range of each tile over
+    // several CTAs (partial sums, added in order by k_gemm_kreduce).  The split of a
+    // problem depends on that problem alone (its tile count and K), never on the other
+    // problems of the launch, so that a product gives the same bits whichever launch it is
+    // part of (one instance alone, or many merged).
+    if (v >= 1 && v <= 4) {
       std::vector<int4> nt;
       for (const int4& t : vt) {
         int K = 0;
         for (int g = lprobs[t.x].seg0; g < lprobs[t.x].seg1; ++g) K += lsegs[g].K;
+        const int64_t ptiles = ceil_div((int64_t)lprobs[t.x].M, (int64_t)tm);
+        const int want = ptiles >= 2 * 152
+                             ? 1
+                             : (int)std::min<int64_t>(16, ceil_div((int64_t)4 * 152, ptiles));
         const int kp = std::min(want, (K + 127) / 128);
         if (kp <= 1) { nt.push_back(t); continue; }
         reds.push_back(make_int4(t.x, t.y, t.z, slot));
@@ -864,19 +870,34 @@ __global__ void __launch_bounds__(256) k_trsm_blk(const TrsmProb* __restrict__ p
 
 static constexpr size_t kTrsmMaxSmem = 200 * 1024;
 
-// work list and variant: blocked kernel (variant = columns per CTA: 1, 2, 4 or 8) when every
-// problem's columns fit shared memory; the column-per-warp kernel otherwise (variant 0)
-static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_t* smem) {
+// Work list and variant.  A problem whose n rows of one column fit shared memory goes to
+// the blocked kernel, any other to the column-per-warp kernel: the choice depends on the
+// problem alone, so that its result is the same in any launch it is part of (the two
+// kernels order their operations differently; the blocked kernel's columns per CTA do
+// not change any column's arithmetic).  Work items of the blocked kernel come first
+// (*nblk of them), variant = its columns per CTA (1, 2, 4 or 8).
+static bool trsm_fits_blocked(int n) {
+  return (size_t)n * sizeof(double) + TRB * 33 * sizeof(double) <= kTrsmMaxSmem;
+}
+
+static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_t* smem,
+                                   int64_t* nblk) {
   int maxn = 0, maxc = 0;
-  for (const auto& p : b.h) { maxn = std::max(maxn, p.n); maxc = std::max(maxc, p.ncol); }
-  const int cw = maxc <= 1 ? 1 : (maxc <= 2 ? 2 : (maxc <= 4 ? 4 : 8));
-  const size_t need = (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double);
-  *variant = (need <= kTrsmMaxSmem) ? cw : 0;
-  *smem = *variant ? need : 0;
+  for (const auto& p : b.h)
+    if (p.n > 0 && trsm_fits_blocked(p.n)) { maxn = std::max(maxn, p.n); maxc = std::max(maxc, p.ncol); }
+  int cw = maxc <= 1 ? 1 : (maxc <= 2 ? 2 : (maxc <= 4 ? 4 : 8));
+  while (cw > 1 && (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double) > kTrsmMaxSmem)
+    cw /= 2;
+  *variant = cw;
+  *smem = (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double);
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
-    if (b.h[p].n > 0)
-      for (int c = 0; c < b.h[p].ncol; c += (*variant ? *variant : 1)) work.push_back(make_int2(p, c));
+    if (b.h[p].n > 0 && trsm_fits_blocked(b.h[p].n))
+      for (int c = 0; c < b.h[p].ncol; c += cw) work.push_back(make_int2(p, c));
+  *nblk = (int64_t)work.size();
+  for (int p = 0; p < (int)b.size(); ++p)
+    if (b.h[p].n > 0 && !trsm_fits_blocked(b.h[p].n))
+      for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
   return work;
 }
 
@@ -890,23 +911,25 @@ static void trsm_blk_go(const TrsmProb* probs, const int2* work, int64_t nwork, 
   k_trsm_blk<C><<<(unsigned)nwork, 256, smem, s>>>(probs, work);
 }
 
-static void trsm_go(const TrsmProb* probs, const int2* work, int64_t nwork, int variant,
-                    size_t smem, cudaStream_t s) {
-  if (variant) {
+static void trsm_go(const TrsmProb* probs, const int2* work, int64_t nwork, int64_t nblk,
+                    int variant, size_t smem, cudaStream_t s) {
+  if (nblk > 0) {
     switch (variant) {
-      case 1: trsm_blk_go<1>(probs, work, nwork, smem, s); break;
-      case 2: trsm_blk_go<2>(probs, work, nwork, smem, s); break;
-      case 4: trsm_blk_go<4>(probs, work, nwork, smem, s); break;
-      default: trsm_blk_go<8>(probs, work, nwork, smem, s); break;
+      case 1: trsm_blk_go<1>(probs, work, nblk, smem, s); break;
+      case 2: trsm_blk_go<2>(probs, work, nblk, smem, s); break;
+      case 4: trsm_blk_go<4>(probs, work, nblk, smem, s); break;
+      default: trsm_blk_go<8>(probs, work, nblk, smem, s); break;
     }
-  } else {
-    k_trsm<<<ceil_div(nwork, 8), 256, 0, s>>>(probs, work, nwork);
+    SPD_LAUNCHED();
   }
-  SPD_LAUNCHED();
+  if (nwork > nblk) {
+    k_trsm<<<ceil_div(nwork - nblk, 8), 256, 0, s>>>(probs, work + nblk, nwork - nblk);
+    SPD_LAUNCHED();
+  }
 }
 
 void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
-  std::vector<int2> w = trsm_work(b, &b.variant, &b.smem);
+  std::vector<int2> w = trsm_work(b, &b.variant, &b.smem, &b.nfirst);
   b.work.upload(w, s);
   b.nwork = (int64_t)w.size();
 }
@@ -929,18 +952,19 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
     ProfScope ps(b.tag ? b.tag : "trsm", s, f);
-    trsm_go(b.d.p, b.work.p, b.nwork, b.variant, b.smem, s);
+    trsm_go(b.d.p, b.work.p, b.nwork, b.nfirst, b.variant, b.smem, s);
     return;
   }
   int variant;
   size_t smem;
-  std::vector<int2> work = trsm_work(b, &variant, &smem);
+  int64_t nblk;
+  std::vector<int2> work = trsm_work(b, &variant, &smem, &nblk);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);
   {
     ProfScope ps(b.tag ? b.tag : "trsm", s, f);
-    trsm_go(b.d.p, dw.p, (int64_t)work.size(), variant, smem, s);
+    trsm_go(b.d.p, dw.p, (int64_t)work.size(), nblk, variant, smem, s);
   }
   SPD_CUDA(cudaStreamSynchronize(s));
 }
@@ -979,22 +1003,17 @@ __device__ __forceinline__ int qr_downdate(double rjp, double& vn1, double vn2) 
   return 0;
 }
 
-// v^T col over rows [0, len) by one warp: four independent partial sums (rows l, l + 32,
-// l + 64, l + 96 of every 128), so that four loads are in flight per lane
-__device__ __forceinline__ double warp_dot4(const double* __restrict__ v,
-                                            const double* __restrict__ col, int len, int lane) {
-  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
-  int i = lane;
-  for (; i + 96 < len; i += 128) {
-    w0 = fma(v[i], col[i], w0);
-    w1 = fma(v[i + 32], col[i + 32], w1);
-    w2 = fma(v[i + 64], col[i + 64], w2);
-    w3 = fma(v[i + 96], col[i + 96], w3);
-  }
-  for (; i < len; i += 32) w0 = fma(v[i], col[i], w0);
-  return warp_sum((w0 + w1) + (w2 + w3));
+template <int LPC>
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+  for (int o = LPC / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 
+// Columns in global memory.  Every reduction has the shape and order of k_geqp3_smem with
+// the same LPC (lanes per column), so the two kernels give bit-identical factorizations
+// and the choice between them (and of the cluster size) does not change any result.
+template <int LPC>
 __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs, int pivot) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -1120,42 +1139,61 @@ __global__ void __launch_bounds__(256) k_geqp3(const QrProb* __restrict__ probs,
       s_v[i] = (i == 0) ? 1.0 : A[j + i + (int64_t)j * ld];
     __syncthreads();
     {
-      int t = 0;
-      for (int p = first_owned(j + 1); p < n; p += C, ++t) {
-        if (t % nw != warp) continue;
+      // LPC lanes per column, G = 32 / LPC columns per warp at a time (as k_geqp3_smem)
+      constexpr int G = 32 / LPC;
+      const int g = lane / LPC, sl = lane % LPC;
+      const unsigned FULL = 0xffffffffu;
+      const int p0 = first_owned(j + 1);
+      const int cnt = (p0 < n) ? (n - p0 + C - 1) / C : 0;
+      for (int t0 = warp * G; t0 < cnt; t0 += nw * G) {
+        const int t = t0 + g;
+        const bool act = t < cnt;
+        const int p = p0 + (act ? t : 0) * C;
         double* col = A + j + (int64_t)p * ld;
-        if (tau != 0.0) {
-          const double w = warp_dot4(s_v, col, len, lane) * tau;
+        double w = 0.0;
+        if (act && tau != 0.0) {
+          double w0 = 0.0, w1 = 0.0;
+          int i = sl;
+          for (; i + LPC < len; i += 2 * LPC) {
+            w0 = fma(s_v[i], col[i], w0);
+            w1 = fma(s_v[i + LPC], col[i + LPC], w1);
+          }
+          if (i < len) w0 = fma(s_v[i], col[i], w0);
+          w = w0 + w1;
+        }
+        w = group_sum<LPC>(w) * tau;
+        double sq = 0.0;
+        if (act && tau != 0.0) {
           if (pivot && !P.downdate) {   // update and recompute the norm in one pass
-            double s = 0.0;
-            for (int i = lane; i < len; i += 32) {
+            for (int i = sl; i < len; i += LPC) {
               const double a = col[i] - w * s_v[i];
               col[i] = a;
-              if (i > 0) s += a * a;
+              if (i > 0) sq += a * a;
             }
-            s = warp_sum(s);
-            if (lane == 0) P.norms[p] = sqrt(s);
-            continue;
-          }
+          } else {
 #pragma unroll 4
-          for (int i = lane; i < len; i += 32) col[i] -= w * s_v[i];
+            for (int i = sl; i < len; i += LPC) col[i] -= w * s_v[i];
+          }
         }
-        if (pivot) {
-          int rc = 1;
+        if (!pivot) continue;
+        int rc = 1;
+        if (P.downdate || tau == 0.0) {
           if (P.downdate) {
-            if (lane == 0) {
+            rc = 0;
+            if (act && sl == 0) {
               double v1 = P.norms[p];
               rc = qr_downdate(col[0], v1, P.norms[n + p]);
               P.norms[p] = v1;
             }
-            rc = __shfl_sync(0xffffffffu, rc, 0);
+            rc = __shfl_sync(FULL, rc, g * LPC);
           }
-          if (rc) {
-            double s = 0.0;
-            for (int i = 1 + lane; i < len; i += 32) s += col[i] * col[i];
-            s = warp_sum(s);
-            if (lane == 0) { P.norms[p] = sqrt(s); P.norms[n + p] = P.norms[p]; }
-          }
+          if (act && rc)
+            for (int i = 1 + sl; i < len; i += LPC) sq += col[i] * col[i];
+        }
+        sq = group_sum<LPC>(sq);
+        if (act && sl == 0 && rc) {
+          P.norms[p] = sqrt(sq);
+          if (P.downdate) P.norms[n + p] = P.norms[p];
         }
       }
     }
@@ -1194,13 +1232,6 @@ __host__ __device__ inline QrSmemLayout qr_smem_layout(int m, int n, int C) {
   L.v = (L.col2pos + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
   L.total = L.v + (size_t)L.ldm * sizeof(double);
   return L;
-}
-
-template <int LPC>
-__device__ __forceinline__ double group_sum(double x) {
-#pragma unroll
-  for (int o = LPC / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
 }
 
 template <int LPC>
@@ -1433,8 +1464,37 @@ struct DeferredQr : Deferred {
   }
 };
 
+// lanes per column of a problem: rows per lane at least 8 where the columns are short.  A
+// function of the problem alone: the factorization's arithmetic depends on it and on
+// nothing else of the launch.
+static int qr_lpc(int m) { return m <= 64 ? 8 : (m <= 128 ? 16 : 32); }
+
+static int geqp3_launch_lpc(const Batch<QrProb>& b, int pivot, int cluster, int max_m, int lpc,
+                            cudaStream_t s);
+
 int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cudaStream_t s) {
   if (b.empty()) { merge_skip(); return -1; }
+  if (!merging()) {
+    int slot = -1;
+    for (int lpc : {8, 16, 32}) {
+      Batch<QrProb> sub;
+      sub.tag = b.tag;
+      int mm = 1;
+      for (const auto& q : b.h)
+        if (qr_lpc(q.m) == lpc) { sub.push(q); mm = std::max(mm, q.m); }
+      if (sub.empty()) continue;
+      if (sub.size() == b.size()) return geqp3_launch_lpc(b, pivot, cluster, max_m, lpc, s);
+      sub.upload(s);
+      const int sl = geqp3_launch_lpc(sub, pivot, cluster, std::min(max_m, mm), lpc, s);
+      if (slot < 0) slot = sl;
+    }
+    return slot;
+  }
+  return geqp3_launch_lpc(b, pivot, cluster, max_m, 0, s);
+}
+
+static int geqp3_launch_lpc(const Batch<QrProb>& b, int pivot, int cluster, int max_m, int lpc,
+                            cudaStream_t s) {
   if (merging()) {
     std::unique_ptr<DeferredQr> d(new DeferredQr());
     d->h = b.h;
@@ -1488,10 +1548,9 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       ProfScope ps(b.tag ? b.tag : "geqp3", s);
-      // lanes per column: rows per lane at least 8 where the columns are short
-      if (mmax <= 64)
+      if (lpc == 8)
         SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<8>, dprobs, mmax, nmax));
-      else if (mmax <= 128)
+      else if (lpc == 16)
         SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<16>, dprobs, mmax, nmax));
       else
         SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3_smem<32>, dprobs, mmax, nmax));
@@ -1504,7 +1563,9 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
   SPD_REQUIRE(smem <= 200 * 1024, "geqp3: matrix too tall for the shared-memory reflector");
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_geqp3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+    cudaFuncSetAttribute(k_geqp3<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+    cudaFuncSetAttribute(k_geqp3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+    cudaFuncSetAttribute(k_geqp3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
   });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(b.size() * cluster), 1, 1);
@@ -1522,7 +1583,9 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
   {
     ProfScope ps(b.tag ? b.tag : (pivot ? "geqp3" : "geqrf"), s);
     slot = ps.slot;
-    SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3, dprobs, pivot));
+    if (lpc == 8) SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3<8>, dprobs, pivot));
+    else if (lpc == 16) SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3<16>, dprobs, pivot));
+    else SPD_CUDA(cudaLaunchKernelEx(&cfg, k_geqp3<32>, dprobs, pivot));
     SPD_LAUNCHED();
   }
   return slot;
@@ -1607,41 +1670,58 @@ __global__ void __launch_bounds__(256) k_hh_apply_r(const HhApplyProb* __restric
   }
 }
 
-// registers per lane for the rows of the tallest matrix (0: too tall, generic kernel)
+// A problem of at most 512 rows goes to the register kernel, a taller one to the generic
+// kernel: the choice depends on the problem alone (the two kernels sum in different
+// orders; the register kernel's rows per lane do not change a column's arithmetic, the
+// extra registers holding zeros).  EPT: registers per lane for the tallest register problem.
+constexpr int kHhRegRows = 512;
+
 static int hh_ept(const Batch<HhApplyProb>& b) {
   int mx = 1;
-  for (const auto& p : b.h) mx = std::max(mx, p.m);
+  for (const auto& p : b.h)
+    if (p.m <= kHhRegRows) mx = std::max(mx, p.m);
   const int e = (mx + 31) / 32;
-  return e <= 1 ? 1 : (e <= 2 ? 2 : (e <= 4 ? 4 : (e <= 8 ? 8 : (e <= 16 ? 16 : 0))));
+  return e <= 1 ? 1 : (e <= 2 ? 2 : (e <= 4 ? 4 : (e <= 8 ? 8 : 16)));
 }
 
 // FP64 issue is 2 FMA per clock per SM on this part: with few columns the warps are spread
 // one or two per CTA so that they land on different SMs.
-static void hh_go(const HhApplyProb* probs, const int2* work, int64_t nw, int ept, int trans,
-                  cudaStream_t s) {
-  const int wpb = nw >= 8 * 152 ? 8 : (nw >= 2 * 152 ? 2 : 1);   // warps per CTA
-  const unsigned g = (unsigned)ceil_div(nw, wpb);
-  const int bs = 32 * wpb;
-  switch (ept) {
-    case 1: k_hh_apply_r<1><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
-    case 2: k_hh_apply_r<2><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
-    case 4: k_hh_apply_r<4><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
-    case 8: k_hh_apply_r<8><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
-    case 16: k_hh_apply_r<16><<<g, bs, 0, s>>>(probs, work, nw, trans); break;
-    default: k_hh_apply<<<(unsigned)ceil_div(nw, 8), 256, 0, s>>>(probs, work, nw, trans); break;
+static void hh_go(const HhApplyProb* probs, const int2* work, int64_t nw, int64_t nreg, int ept,
+                  int trans, cudaStream_t s) {
+  if (nreg > 0) {
+    const int wpb = nreg >= 8 * 152 ? 8 : (nreg >= 2 * 152 ? 2 : 1);   // warps per CTA
+    const unsigned g = (unsigned)ceil_div(nreg, wpb);
+    const int bs = 32 * wpb;
+    switch (ept) {
+      case 1: k_hh_apply_r<1><<<g, bs, 0, s>>>(probs, work, nreg, trans); break;
+      case 2: k_hh_apply_r<2><<<g, bs, 0, s>>>(probs, work, nreg, trans); break;
+      case 4: k_hh_apply_r<4><<<g, bs, 0, s>>>(probs, work, nreg, trans); break;
+      case 8: k_hh_apply_r<8><<<g, bs, 0, s>>>(probs, work, nreg, trans); break;
+      default: k_hh_apply_r<16><<<g, bs, 0, s>>>(probs, work, nreg, trans); break;
+    }
+    SPD_LAUNCHED();
   }
-  SPD_LAUNCHED();
+  if (nw > nreg) {
+    k_hh_apply<<<(unsigned)ceil_div(nw - nreg, 8), 256, 0, s>>>(probs, work + nreg, nw - nreg, trans);
+    SPD_LAUNCHED();
+  }
 }
 
-static std::vector<int2> hh_work(const Batch<HhApplyProb>& b) {
+// (problem, column) items: the register kernel's problems first (*nreg items)
+static std::vector<int2> hh_work(const Batch<HhApplyProb>& b, int64_t* nreg) {
   std::vector<int2> work;
   for (int p = 0; p < (int)b.size(); ++p)
-    for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+    if (b.h[p].m <= kHhRegRows)
+      for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
+  *nreg = (int64_t)work.size();
+  for (int p = 0; p < (int)b.size(); ++p)
+    if (b.h[p].m > kHhRegRows)
+      for (int c = 0; c < b.h[p].ncol; ++c) work.push_back(make_int2(p, c));
   return work;
 }
 
 void householder_prepare(Batch<HhApplyProb>& b, cudaStream_t s) {
-  std::vector<int2> w = hh_work(b);
+  std::vector<int2> w = hh_work(b, &b.nfirst);
   b.work.upload(w, s);
   b.nwork = (int64_t)w.size();
   b.variant = hh_ept(b);
@@ -1664,17 +1744,18 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
   if (b.nwork >= 0) {
     if (b.nwork == 0) return;
     ProfScope ps(b.tag ? b.tag : "householder", s);
-    hh_go(b.d.p, b.work.p, b.nwork, b.variant, trans, s);
+    hh_go(b.d.p, b.work.p, b.nwork, b.nfirst, b.variant, trans, s);
     return;
   }
-  std::vector<int2> work = hh_work(b);
+  int64_t nreg = 0;
+  std::vector<int2> work = hh_work(b, &nreg);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);
   const int64_t nw = (int64_t)work.size();
   {
     ProfScope ps(b.tag ? b.tag : "householder", s);
-    hh_go(b.d.p, dw.p, nw, hh_ept(b), trans, s);
+    hh_go(b.d.p, dw.p, nw, nreg, hh_ept(b), trans, s);
   }
   SPD_CUDA(cudaStreamSynchronize(s));
 }

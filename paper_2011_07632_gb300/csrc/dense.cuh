@@ -96,6 +96,7 @@ struct Batch {
   const char* tag = nullptr;   // profiler label of the call site
   int variant = 0;        // kernel variant chosen when the work list was prepared
   size_t smem = 0;        // dynamic shared memory of that variant
+  int64_t nfirst = 0;     // work items [0, nfirst) go to the first of two kernels
   void upload(cudaStream_t s) { d.upload(h, s); }
   size_t size() const { return h.size(); }
   bool empty() const { return h.empty(); }

@@ -761,9 +761,12 @@ void RowCoupBatchT<T>::upload(cudaStream_t s) {
   int64_t nparts = 0, total = 0;
   for (const auto& P : probs)
     for (int g = P.ch0; g < P.ch1; ++g) total += (int64_t)P.M * chunks[g].K;
-  const int64_t item = std::min(kRowItemMax, std::max(kRowItemMin, total / (152 * 16)));
+  const int64_t item0 = std::min(kRowItemMax, std::max(kRowItemMin, total / (152 * 16)));
+  for (auto& P : probs)
+    if (P.item == 0) P.item = item0;
   for (int p = 0; p < (int)probs.size(); ++p) {
     const RowCoupProbT<T>& P = probs[p];
+    const int64_t item = P.item;
     int64_t kt = 0;
     for (int g = P.ch0; g < P.ch1; ++g) kt += chunks[g].K;
     flops += 2.0 * P.M * (double)kt * P.ncol;

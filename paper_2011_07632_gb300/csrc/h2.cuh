@@ -27,6 +27,9 @@ struct RowCoupProbT {
   const T* A;        // k_i x (sum k_j), ld k_i
   int ch0, ch1;      // chunk range
   int beta = 0;      // 1: add to C instead of overwriting it
+  // coupling entries per CTA chosen when the problem's own batch was first uploaded (0:
+  // not yet); kept so that the problem is summed the same way in merged launches
+  int64_t item = 0;
 };
 template <class T>
 struct RowCoupChunkT {

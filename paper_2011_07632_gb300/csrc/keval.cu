@@ -1,5 +1,6 @@
 // Kernel-matrix evaluation kernels (see keval.cuh).
 #include <algorithm>
+#include <map>
 #include <type_traits>
 
 #include "keval.cuh"
@@ -441,9 +442,17 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   work.clear();
   int mx = 1;
   for (const auto& p : probs) mx = std::max(mx, p.ncol);
-  // few columns: thread-per-row kernel (cb = -NC); otherwise shared-memory kernel tiles
+  // few columns: thread-per-row kernel (cb = -NC); otherwise shared-memory kernel tiles.
+  // Problems that carry the choice of their first upload keep it (all of one launch
+  // share it: merged launches are grouped by it).
   if (mx <= 16) cb = -(mx <= 1 ? 1 : (mx <= 2 ? 2 : (mx <= 4 ? 4 : (mx <= 8 ? 8 : 16))));
   else cb = 64;
+  for (const auto& p : probs)
+    if (p.cb != 0) { cb = p.cb; break; }
+  for (auto& p : probs) {
+    SPD_REQUIRE(p.cb == 0 || p.cb == cb, "near field: problems of one launch differ in column block");
+    p.cb = cb;
+  }
   const int step = cb < 0 ? -cb : cb;
   // the problems as launched: the many-column kernel takes 32 rows per CTA, so its
   // problems are cut into 32-row blocks (disjoint output rows)
@@ -460,7 +469,8 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   } else {
     exec_probs = probs;
   }
-  // split the segments when there are too few CTAs for the GPU
+  // split the segments when there are too few CTAs for the GPU; a problem that carries
+  // the split of its first upload keeps it
   parts = 1;
   part_probs.clear();
   red.clear();
@@ -472,13 +482,22 @@ void NearBatchT<T>::upload(cudaStream_t s) {
     }
     const int64_t want = 4 * 152;
     parts = (int)std::min<int64_t>(std::max<int64_t>(1, (want + ctas - 1) / ctas), std::min<int64_t>(8, maxseg));
+    for (auto& p : exec_probs)
+      if (p.parts == 0) p.parts = parts;
+    for (size_t q = 0, e = 0; q < probs.size(); ++q) {   // the choice, back to the originals
+      const size_t ne = (cb > 0) ? (size_t)((probs[q].rows + 31) / 32) : 1;
+      if (ne > 0) probs[q].parts = exec_probs[e].parts;
+      e += ne;
+    }
+    parts = 1;
+    for (const auto& p : exec_probs) parts = std::max(parts, std::min(p.parts, std::max(p.seg1 - p.seg0, 1)));
   }
   if (parts > 1) {
     int64_t off = 0;
     for (int p = 0; p < (int)exec_probs.size(); ++p) {
       const NearProbT<T>& P = exec_probs[p];
       const int ns = P.seg1 - P.seg0;
-      const int np = std::min(parts, std::max(ns, 1));
+      const int np = std::min(P.parts, std::max(ns, 1));
       const int64_t tot = (int64_t)P.rows * P.ncol;
       red.push_back(make_int4(p, (int)off, np, 0));
       for (int q = 0; q < np; ++q) {
@@ -534,22 +553,27 @@ struct DeferredNear : Deferred {
   const char* tag = "near";
   int kind = 0;
   void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
-    NearBatchT<T> m;
-    m.tag = tag;
+    // one launch per column block chosen by the instances (normally a single one)
+    std::map<int, NearBatchT<T>> by_cb;
     for (Deferred* d : group) {
       const auto* x = static_cast<const DeferredNear<T>*>(d);
-      const int off = (int)m.segs.size();
-      m.segs.insert(m.segs.end(), x->segs.begin(), x->segs.end());
       for (NearProbT<T> p : x->probs) {
-        p.seg0 += off;
-        p.seg1 += off;
+        NearBatchT<T>& m = by_cb[p.cb];
+        const int off = (int)m.segs.size();
+        m.segs.insert(m.segs.end(), x->segs.begin() + p.seg0, x->segs.begin() + p.seg1);
+        p.seg1 = off + (p.seg1 - p.seg0);
+        p.seg0 = off;
         m.probs.push_back(p);
       }
     }
     KernelFn k{};
     k.kind = kind;
-    m.upload(s);
-    m.launch(k, nullptr, 0, 0, s);
+    for (auto& kv : by_cb) {
+      NearBatchT<T>& m = kv.second;
+      m.tag = tag;
+      m.upload(s);
+      m.launch(k, nullptr, 0, 0, s);
+    }
   }
 };
 

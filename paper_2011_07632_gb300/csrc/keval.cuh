@@ -68,6 +68,10 @@ struct NearProbT {
   int64_t ldx = 0;
   int dim = 0;
   double inv_ell = 0.0, shift = 0.0;
+  // launch choices made when the problem's own batch was first uploaded (0: not yet): the
+  // column block cb and the segment parts, kept so that the problem is computed the same
+  // way (same bits) when it is later launched together with other instances' problems
+  int cb = 0, parts = 0;
 };
 template <class T>
 struct NearSegT {

@@ -60,8 +60,9 @@ _SIGS = {
     "spdhss_build_batched": [_I, ctypes.POINTER(_P), _PI64, ctypes.POINTER(_I),
                              ctypes.POINTER(KernelDesc), ctypes.POINTER(_I), ctypes.POINTER(_D),
                              ctypes.POINTER(_I), ctypes.POINTER(_I),
-                             ctypes.POINTER(ctypes.c_uint64), _P, ctypes.POINTER(_P),
-                             ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I)],
+                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_P), _P,
+                             ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                             ctypes.POINTER(_I)],
     "pcg_solve_batched": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                           ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
