@@ -1592,6 +1592,299 @@ static int geqp3_launch_lpc(const Batch<QrProb>& b, int pivot, int cluster, int 
 }
 
 // ---------------------------------------------------------------------------------------
+// Two stacked upper triangles reduced to one: column j of [R1; R2] has its non-zeros in
+// row j of R1 and rows 0..j of R2, so its reflector has j + 2 entries and touches only
+// those rows of the later columns.  Both triangles are held packed in shared memory
+// (column p: rows 0..p at p (p + 1) / 2).  Column p has a group of lanes of its own
+// (col_group_lanes); the reflector is unnormalized as in k_proxy_qr
+// (A <- A - c u (u^T A), c = -1 / (beta u_0)), and the group of column j + 1 forms the
+// next reflector's scalars right after its update, so a step costs one barrier.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double tri_scalars(double* d, double n2_rest, double* u0_out) {
+  const double alpha = *d;
+  const double normx = sqrt(fma(alpha, alpha, n2_rest));
+  double beta = alpha, c = 0.0, u0 = 0.0;
+  if (normx > 0.0) {
+    beta = alpha >= 0.0 ? -normx : normx;
+    u0 = alpha - beta;
+    c = -1.0 / (beta * u0);
+  }
+  *d = beta;
+  *u0_out = u0;
+  return c;
+}
+
+__global__ void __launch_bounds__(256) k_tri_merge(const TriMergeProb* __restrict__ probs) {
+  const TriMergeProb P = probs[blockIdx.x];
+  const int m = P.m;
+  extern __shared__ double sT[];
+  const int tri = m * (m + 1) / 2;
+  double* T1 = sT;
+  double* T2 = sT + tri;
+  __shared__ double s_c[2], s_u0[2];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int lanes = col_group_lanes(m), gpw = 32 / lanes;
+  const int g = tid / lanes, sl = tid % lanes;
+  const int g_lo = warp * gpw, g_hi = g_lo + gpw - 1;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, p = e / m;
+    if (i <= p) {
+      T1[p * (p + 1) / 2 + i] = P.R1[i + (int64_t)p * m];
+      T2[p * (p + 1) / 2 + i] = P.R2[i + (int64_t)p * m];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) s_c[0] = tri_scalars(T1, T2[0] * T2[0], &s_u0[0]);
+  __syncthreads();
+  const int gc = min(g, m - 1);
+  double* c1 = T1 + gc * (gc + 1) / 2;   // column g of R1 (rows 0..g)
+  double* c2 = T2 + gc * (gc + 1) / 2;   // column g of R2
+  for (int j = 0; j < m; ++j) {
+    if (g_hi > j && g_lo < m) {   // a warp with a column > j (warp-uniform)
+      const bool act = g > j && g < m;
+      const double c = s_c[j & 1], u0 = s_u0[j & 1];
+      const double* u2 = T2 + j * (j + 1) / 2;   // rows 0..j of R2's column j
+      const bool next = g == j + 1;              // this column forms the next reflector
+      double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+      if (act && c != 0.0) {
+        if (sl == 0) w0 = u0 * c1[j];
+        int i = sl;
+        for (; i + 3 * lanes <= j; i += 4 * lanes) {   // four independent loads per lane
+          w0 = fma(u2[i], c2[i], w0);
+          w1 = fma(u2[i + lanes], c2[i + lanes], w1);
+          w2 = fma(u2[i + 2 * lanes], c2[i + 2 * lanes], w2);
+          w3 = fma(u2[i + 3 * lanes], c2[i + 3 * lanes], w3);
+        }
+        for (; i <= j; i += lanes) w0 = fma(u2[i], c2[i], w0);
+      }
+      const double w = group_sum_n((w0 + w1) + (w2 + w3), lanes) * c;
+      double sq = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;   // next: squares of rows 0..j + 1
+      if (act && c != 0.0) {
+        if (sl == 0) c1[j] -= w * u0;
+        int k = sl;
+        for (; k + 3 * lanes <= j; k += 4 * lanes) {   // the column and u are disjoint
+          const double a0 = c2[k], a1 = c2[k + lanes], a2 = c2[k + 2 * lanes], a3 = c2[k + 3 * lanes];
+          const double v0 = u2[k], v1 = u2[k + lanes], v2 = u2[k + 2 * lanes], v3 = u2[k + 3 * lanes];
+          const double b0 = a0 - w * v0, b1 = a1 - w * v1, b2 = a2 - w * v2, b3 = a3 - w * v3;
+          c2[k] = b0; c2[k + lanes] = b1; c2[k + 2 * lanes] = b2; c2[k + 3 * lanes] = b3;
+          if (next) {
+            sq = fma(b0, b0, sq);
+            q1 = fma(b1, b1, q1);
+            q2 = fma(b2, b2, q2);
+            q3 = fma(b3, b3, q3);
+          }
+        }
+        for (; k <= j; k += lanes) {
+          const double b = c2[k] - w * u2[k];
+          c2[k] = b;
+          if (next) sq = fma(b, b, sq);
+        }
+        sq = (sq + q1) + (q2 + q3);
+      } else if (next) {
+        for (int k = sl; k <= j; k += lanes) sq = fma(c2[k], c2[k], sq);
+      }
+      if (g_lo <= j + 1 && j + 1 <= g_hi && j + 1 < m) {   // the warp of column j + 1
+        if (next && sl == (j + 1) % lanes) sq = fma(c2[j + 1], c2[j + 1], sq);
+        sq = group_sum_n(sq, lanes);
+        if (next && sl == 0) s_c[(j + 1) & 1] = tri_scalars(c1 + j + 1, sq, &s_u0[(j + 1) & 1]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, q = e / m;
+    P.R1[i + (int64_t)q * m] = (i <= q) ? T1[q * (q + 1) / 2 + i] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Column-pivoted QR of a small matrix (m, n <= kSmallQr), one CTA, every column resident
+// in shared memory with a lane group of its own (col_group_lanes): per step the CTA agrees
+// on the pivot (largest downdated norm, lowest position), the pivot column's group forms
+// the reflector from the exact norm of its trailing rows and applies the stop test
+// |R_kk| <= rtol |R_00|, and every later column is updated and its norm downdated
+// (recomputed when the downdate loses accuracy, qr_downdate).  Positions are permuted
+// through a column <-> position map; the columns go to their final positions at the end.
+// ---------------------------------------------------------------------------------------
+constexpr int kSmallQr = 160;
+
+__global__ void __launch_bounds__(256) k_geqp3_small(const QrProb* __restrict__ probs) {
+  const QrProb P = probs[blockIdx.x];
+  const int m = P.m, n = P.n;
+  const int lanes = col_group_lanes(n), ld = col_group_ld(m, lanes), gpw = 32 / lanes;
+  extern __shared__ double sA[];   // m x n, column-major, ld
+  __shared__ double s_vn1[kSmallQr], s_vn2[kSmallQr], s_diag[kSmallQr];
+  __shared__ int s_pos[kSmallQr], s_col[kSmallQr];   // column -> position, position -> column
+  __shared__ double s_wv[8];
+  __shared__ int s_wp[8];
+  __shared__ double s_c, s_first;
+  __shared__ int s_piv, s_stop;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = tid / lanes, sl = tid % lanes;
+  const bool own = g < n;
+  const unsigned FULL = 0xffffffffu;
+  for (int e = tid; e < m * n; e += blockDim.x) {
+    const int i = e % m, c = e / m;
+    sA[i + (int64_t)c * ld] = P.A[i + (int64_t)c * P.lda];
+  }
+  for (int c = tid; c < n; c += blockDim.x) { s_pos[c] = c; s_col[c] = c; }
+  __syncthreads();
+  {
+    double sq = 0.0;
+    if (own)
+      for (int i = sl; i < m; i += lanes) sq += sA[i + (int64_t)g * ld] * sA[i + (int64_t)g * ld];
+    sq = group_sum_n(sq, lanes);
+    if (own && sl == 0) { s_vn1[g] = sqrt(sq); s_vn2[g] = s_vn1[g]; }
+  }
+  __syncthreads();
+  const int kmax = min(P.kmax, min(m, n));
+  int j = 0;
+  for (; j < kmax; ++j) {
+    // pivot: the largest downdated norm among positions >= j, ties to the lowest position
+    double bv = -1.0;
+    int bp = n;
+    if (own && sl == 0 && s_pos[g] >= j) { bv = s_vn1[g]; bp = s_pos[g]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(FULL, bv, o);
+      const int p2 = __shfl_xor_sync(FULL, bp, o);
+      argmax_merge(bv, bp, v2, p2);
+    }
+    if (lane == 0) { s_wv[warp] = bv; s_wp[warp] = bp; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge(bv, bp, s_wv[w], s_wp[w]);
+      if (bp >= n) {   // no comparable norm left (NaN): stop
+        s_stop = 1;
+        s_piv = -1;
+      } else {
+        const int cp = s_col[bp], cj = s_col[j];
+        s_col[j] = cp; s_col[bp] = cj;
+        s_pos[cp] = j; s_pos[cj] = bp;
+        s_piv = cp;
+      }
+    }
+    __syncthreads();
+    const int cp = s_piv;
+    if (cp < 0) break;
+    if (warp == cp / gpw) {   // the pivot column's group: exact norm, reflector, stop test
+      double sq = 0.0;
+      if (g == cp)
+        for (int i = j + sl; i < m; i += lanes) sq += sA[i + (int64_t)cp * ld] * sA[i + (int64_t)cp * ld];
+      sq = group_sum_n(sq, lanes);
+      if (g == cp && sl == 0) {
+        const double normx = sqrt(sq);
+        if (j == 0) s_first = normx;
+        const int stop = !(normx > 0.0) || (j > 0 && normx <= P.rtol * s_first);
+        s_stop = stop;
+        if (!stop) s_c = hh_scalars(&sA[j + (int64_t)cp * ld], sq, &s_diag[j]);
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const double c = s_c;
+    const double* u = sA + (int64_t)cp * ld + j;
+    const int len = m - j;
+    const bool act = own && s_pos[g] > j;
+    double* ap = sA + (int64_t)(act ? g : cp) * ld + j;
+    double w0 = 0.0, w1 = 0.0;
+    if (act) {
+      int i = sl;
+      for (; i + lanes < len; i += 2 * lanes) {
+        w0 = fma(u[i], ap[i], w0);
+        w1 = fma(u[i + lanes], ap[i + lanes], w1);
+      }
+      if (i < len) w0 = fma(u[i], ap[i], w0);
+    }
+    const double w = group_sum_n(w0 + w1, lanes) * c;
+    if (act)
+      for (int i = sl; i < len; i += lanes) ap[i] -= w * u[i];
+    __syncwarp();
+    int rc = 0;
+    if (act && sl == 0) {
+      double v1 = s_vn1[g];
+      rc = qr_downdate(ap[0], v1, s_vn2[g]);
+      s_vn1[g] = v1;
+    }
+    rc = __shfl_sync(FULL, rc, (lane / lanes) * lanes);
+    double sq = 0.0;
+    if (act && rc)
+      for (int i = 1 + sl; i < len; i += lanes) sq += ap[i] * ap[i];
+    sq = group_sum_n(sq, lanes);
+    if (act && rc && sl == 0) { s_vn1[g] = sqrt(sq); s_vn2[g] = s_vn1[g]; }
+    __syncthreads();
+  }
+  // columns in pivot order; R_pp on the diagonal of the factored positions
+  for (int e = tid; e < m * n; e += blockDim.x) {
+    const int i = e % m, p = e / m;
+    const int c = s_col[p];
+    P.A[i + (int64_t)p * P.lda] = (p < j && i == p) ? s_diag[p] : sA[i + (int64_t)c * ld];
+  }
+  for (int c = tid; c < n; c += blockDim.x) P.piv[c] = s_col[c];
+  if (tid == 0) *P.rank = j;
+}
+
+int geqp3_small_launch(const Batch<QrProb>& b, const char* tag, cudaStream_t s) {
+  if (b.empty()) { merge_skip(); return -1; }
+  if (merging()) {
+    defer_launch("geqp3_small", b.h, [tag](std::vector<QrProb>& all, cudaStream_t st) {
+      Batch<QrProb> m;
+      m.h = std::move(all);
+      m.upload(st);
+      geqp3_small_launch(m, tag, st);
+    });
+    return -1;
+  }
+  size_t smem = 8;
+  for (const auto& q : b.h) {
+    SPD_REQUIRE(q.m >= 1 && q.n >= 1 && q.m <= kSmallQr && q.n <= kSmallQr,
+                "geqp3_small: matrix larger than the one-CTA limit");
+    smem = std::max(smem, (size_t)col_group_ld(q.m, col_group_lanes(q.n)) * q.n * sizeof(double));
+  }
+  constexpr int kDyn = 227 * 1024 - 8192;   // less the kernel's static arrays
+  SPD_REQUIRE(smem <= (size_t)kDyn, "geqp3_small: matrix exceeds shared memory");
+  static std::once_flag once;
+  std::call_once(once, [] {
+    SPD_CUDA(cudaFuncSetAttribute(k_geqp3_small, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn));
+  });
+  ProfScope ps(tag ? tag : "geqp3_small", s);
+  k_geqp3_small<<<(unsigned)b.size(), 256, smem, s>>>(b.d.p);
+  SPD_LAUNCHED();
+  return ps.slot;
+}
+
+void tri_merge_launch(const Batch<TriMergeProb>& b, const char* tag, cudaStream_t s) {
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    defer_launch("tri_merge", b.h, [tag](std::vector<TriMergeProb>& all, cudaStream_t st) {
+      Batch<TriMergeProb> m;
+      m.h = std::move(all);
+      m.upload(st);
+      tri_merge_launch(m, tag, st);
+    });
+    return;
+  }
+  int mmax = 1;
+  double f = 0.0;
+  for (const auto& p : b.h) {
+    mmax = std::max(mmax, p.m);
+    // column j: a reflector of j + 2 entries on m - j - 1 later columns (4 flops per entry)
+    const double mm = p.m;
+    f += 4.0 * (mm * mm * mm / 6.0 + mm * mm / 2.0);
+  }
+  const size_t smem = (size_t)mmax * (mmax + 1) * sizeof(double);
+  constexpr int kDyn = 227 * 1024 - 1024;   // less the kernel's static scalars
+  SPD_REQUIRE(smem <= (size_t)kDyn, "tri_merge: triangles exceed shared memory");
+  static std::once_flag once;
+  std::call_once(once, [] {
+    SPD_CUDA(cudaFuncSetAttribute(k_tri_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn));
+  });
+  ProfScope ps(tag ? tag : "tri_merge", s, f);
+  k_tri_merge<<<(unsigned)b.size(), 256, smem, s>>>(b.d.p);
+  SPD_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------------------
 // reflector application and explicit Q: one warp per column
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_hh_apply(const HhApplyProb* __restrict__ probs,

@@ -153,6 +153,63 @@ int geqp3_launch(const Batch<QrProb>& b, int pivot, int cluster, int max_m, cuda
 
 // Apply the k reflectors stored in (V, ldv, tau) to B (m x ncol) in place:
 // trans=1: B <- Q^T B;  trans=0: B <- Q B.   Q = H_0 H_1 ... H_{k-1}.
+// ---- shared-memory factorizations with one lane group per column ----------------------
+// A CTA of 256 threads gives each of the m columns of a matrix a group of `lanes` lanes
+// (a power of two <= 32, all threads busy when m <= 256); the lanes of a group take the
+// rows of their column round robin and add their partial sums by shuffles.  The column
+// stride ld of the shared-memory copy is padded to ld = lanes (mod 16) (any value for
+// lanes >= 16), so that the groups of a warp read disjoint banks.
+__host__ __device__ inline int col_group_lanes(int m) {
+  return m <= 8 ? 32 : (m <= 16 ? 16 : (m <= 32 ? 8 : (m <= 64 ? 4 : (m <= 128 ? 2 : 1))));
+}
+__host__ __device__ inline int col_group_ld(int rows, int lanes) {
+  if (lanes >= 16) return rows;
+  return rows + (((lanes - rows) % 16) + 16) % 16;
+}
+#ifdef __CUDACC__
+// sum over the `lanes` lanes of a group (every lane of the warp must call it)
+__device__ __forceinline__ double group_sum_n(double x, int lanes) {
+  for (int o = lanes >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+// Householder scalars of x (x_0 = *x0, |x|^2 = n2), the reflector left unnormalized:
+// u = x - beta e_1, H = I - c u u^T.  Writes u_0 over x_0, stores beta, returns c
+// (c = 0 for x = 0: the identity).
+__device__ __forceinline__ double hh_scalars(double* x0, double n2, double* beta_out) {
+  const double alpha = *x0;
+  const double normx = sqrt(n2);
+  double beta = alpha, c = 0.0;
+  if (normx > 0.0) {
+    beta = alpha >= 0.0 ? -normx : normx;
+    const double u0 = alpha - beta;
+    *x0 = u0;
+    c = -1.0 / (beta * u0);
+  }
+  *beta_out = beta;
+  return c;
+}
+#endif
+
+// Column-pivoted QR of small square (or short) matrices, one CTA each (H^2 ID on the
+// TSQR triangle): the pivot is the column of largest downdated norm (LAPACK's downdate
+// with its recomputation safeguard, qr_downdate), ties to the lowest position; the
+// factorization stops before step k when the exact norm |R_kk| of the pivot column is
+// <= rtol |R_00| (or 0).  On return A holds the columns in pivot order with R in their
+// upper k rows (below the diagonal: unspecified), piv[p] = original column at position
+// p, *rank = k.  m <= 160 (rows and columns).  Uses A, lda, m, n, rtol, piv, rank.
+int geqp3_small_launch(const Batch<QrProb>& b, const char* tag, cudaStream_t s);
+
+// ---- R factor of two stacked upper triangles: R1 <- R of QR([R1; R2]) ----------------
+// R1, R2: m x m upper triangular, column-major, leading dimension m (entries below the
+// diagonal are ignored on input; R1's are written as zeros).  The reduction step of a
+// blocked (TSQR) QR: merging the R factors of two row blocks gives the R factor of both.
+struct TriMergeProb {
+  double* R1;
+  const double* R2;
+  int m;
+};
+void tri_merge_launch(const Batch<TriMergeProb>& b, const char* tag, cudaStream_t s);
+
 struct HhApplyProb {
   const double* V;
   int64_t ldv;

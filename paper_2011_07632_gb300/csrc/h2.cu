@@ -119,28 +119,46 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
     for (int64_t k = 0; k < nn; ++k)
       if (mrows[o + k] > 0 && has_far_field(T, o + k)) todo.push_back(o + k);
     const size_t budget = (size_t)3 << 30;
+    // a node with few candidates takes the blocked QR (proxy rows evaluated and factored
+    // block by block in shared memory, the block triangles merged pairwise, the pivoted QR
+    // on the m x m result); a wider one the pivoted QR of its whole proxy matrix
+    auto blocked = [&](int m) { return m <= kIdTsqrMaxM; };
+    auto nblocks = [&](int m) { return ceil_div(np, id_tsqr_rows(m, np)); };
+    auto work_doubles = [&](int m) -> int64_t {
+      return blocked(m) ? (int64_t)nblocks(m) * m * m : (int64_t)np * m;
+    };
+    // merge rounds: fixed by the proxy count (the most blocks any node can have), so that
+    // every instance of a batched sweep makes the same sequence of launches
+    int rounds = 0, most = 1;
+    for (int m = 1; m <= kIdTsqrMaxM; ++m) most = std::max(most, nblocks(m));
+    while ((1 << rounds) < most) ++rounds;
     size_t pos = 0;
     while (pos < todo.size()) {
       size_t end = pos, bytes = 0;
       while (end < todo.size()) {
-        const size_t b = (size_t)np * mrows[todo[end]] * sizeof(double);
+        const size_t b = (size_t)work_doubles(mrows[todo[end]]) * sizeof(double);
         if (end > pos && bytes + b > budget) break;
         bytes += b;
         ++end;
       }
       const size_t nb = end - pos;
-      std::vector<int64_t> goff(nb + 1, 0), coff(nb + 1, 0);
-      int maxm = 0;
+      std::vector<int64_t> goff(nb + 1, 0), coff(nb + 1, 0), ldg(nb, np);
+      int maxm = 0, maxrows = 1;
       for (size_t b = 0; b < nb; ++b) {
         const int m = mrows[todo[pos + b]];
-        goff[b + 1] = goff[b] + (int64_t)np * m;
+        goff[b + 1] = goff[b] + work_doubles(m);
         coff[b + 1] = coff[b] + m;
         maxm = std::max(maxm, m);
+        if (blocked(m)) ldg[b] = m;
+        maxrows = std::max<int>(maxrows, (int)ldg[b]);
       }
       DevBuf<double> G(goff[nb]), tau(coff[nb]), norms(2 * coff[nb]);
       DevBuf<int> piv(coff[nb]), rk(nb);
       Batch<ProxyProb> pb;
-      Batch<QrProb> qb;
+      Batch<ProxyQrProb> zb[2];                 // row blocks: narrow, wide (m > 113)
+      std::vector<std::pair<int64_t, int>> tri; // blocked nodes: (R stack offset, m)
+      std::vector<int> trib;                    // and their block counts
+      Batch<QrProb> qb, qs;                     // pivoted QRs: whole proxy matrices, triangles
       for (size_t b = 0; b < nb; ++b) {
         const int64_t i = todo[pos + b];
         ProxyProb p;
@@ -161,31 +179,79 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
           const int64_t cb = T.child_begin[i] - T.depth_off[t + 1];
           p.xc = sx[t + 1].p; p.ldxc = (int64_t)sx[t + 1].n / crow; p.c0 = soff[t + 1][cb];
         }
-        p.cols = mrows[i];
-        p.out = G.p + goff[b];
-        p.ldo = np;
-        pb.push(p);
+        const int m = mrows[i];
+        p.cols = m;
         QrProb q;
-        q.A = G.p + goff[b]; q.lda = np; q.m = np; q.n = mrows[i];
-        q.kmax = std::min(np, mrows[i]); q.rtol = h->tol;
+        if (blocked(m)) {
+          // R_b of every row block into the node's stack; the merged R in block 0
+          const int br = id_tsqr_rows(m, np), nbk = nblocks(m);
+          for (int k2 = 0; k2 < nbk; ++k2) {
+            ProxyQrProb z;
+            z.p = p;
+            z.p.out = G.p + goff[b] + (int64_t)k2 * m * m;
+            z.p.ldo = m;
+            z.r0 = k2 * br;
+            z.rows = std::min(br, np - k2 * br);
+            zb[m * m > kIdTsqrBlockEntries ? 1 : 0].push(z);
+          }
+          tri.emplace_back(goff[b], m);
+          trib.push_back(nbk);
+          q.A = G.p + goff[b]; q.lda = m; q.m = m;
+          q.n = m;
+          q.kmax = m; q.rtol = h->tol;
+          q.piv = piv.p + coff[b]; q.tau = tau.p + coff[b]; q.rank = rk.p + b;
+          q.norms = norms.p + 2 * coff[b];
+          qs.push(q);
+          continue;
+        } else {
+          p.out = G.p + goff[b];
+          p.ldo = np;
+          pb.push(p);
+          q.A = G.p + goff[b]; q.lda = np; q.m = np;
+        }
+        q.n = m;
+        q.kmax = std::min(q.m, m); q.rtol = h->tol;
         q.piv = piv.p + coff[b]; q.tau = tau.p + coff[b]; q.rank = rk.p + b;
         q.norms = norms.p + 2 * coff[b];
         qb.push(q);
       }
       pb.upload(s);
       proxy_launch(pb, h->kfn, dim, s);
+      for (auto& z : zb) {
+        z.upload(s);
+        proxy_qr_launch(z, h->kfn, dim, "qr_h2_id_blocks", s);
+      }
+      // pairwise merges of the block triangles, block q absorbing block q + 2^r
+      for (int r = 0; r < rounds; ++r) {
+        Batch<TriMergeProb> mb;
+        for (size_t t2 = 0; t2 < tri.size(); ++t2) {
+          const int m = tri[t2].second, nbk = trib[t2];
+          const int64_t mm = (int64_t)m * m;
+          for (int q2 = 0; q2 + (1 << r) < nbk; q2 += 2 << r)
+            mb.push(TriMergeProb{G.p + tri[t2].first + q2 * mm,
+                                 G.p + tri[t2].first + (q2 + (1 << r)) * mm, m});
+        }
+        mb.upload(s);
+        tri_merge_launch(mb, "qr_h2_id_merge", s);
+      }
+      qs.upload(s);
+      const int sslot = geqp3_small_launch(qs, "qr_h2_id_pivot", s);
       qb.tag = "geqp3_h2_id";
       qb.upload(s);
       // cluster size: by the widest matrix, and wide enough that small batches still put
       // about two CTAs on every SM (the columns of a matrix are split over its cluster)
       int cl = maxm <= 128 ? 1 : (maxm <= 256 ? 2 : (maxm <= 512 ? 4 : 8));
       while (cl < 8 && (int64_t)nb * cl < 2 * 152 && maxm >= 32 * cl) cl *= 2;
-      const int pslot = geqp3_launch(qb, 1, cl, np, s);
+      const int pslot = geqp3_launch(qb, 1, cl, maxrows, s);
       std::vector<int> hrk = rk.download(s);
-      if (pslot >= 0) {
-        double f = 0.0;
-        for (size_t b = 0; b < nb; ++b) f += qr_flops(np, mrows[todo[pos + b]], hrk[b], true);
-        prof_add_flops(pslot, f);
+      {
+        double f = 0.0, fs = 0.0;
+        for (size_t b = 0; b < nb; ++b) {
+          const double fb = qr_flops((int)ldg[b], mrows[todo[pos + b]], hrk[b], true);
+          (blocked(mrows[todo[pos + b]]) ? fs : f) += fb;
+        }
+        if (pslot >= 0) prof_add_flops(pslot, f);
+        if (sslot >= 0) prof_add_flops(sslot, fs);
       }
       std::vector<int> hpiv = piv.download(s);
       // T = R11^{-1} R12 in place, then U
@@ -202,13 +268,13 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
         Uptr[i] = up;
         if (k < m && k > 0) {
           TrsmProb tp;
-          tp.T = G.p + goff[b]; tp.ldt = np;
-          tp.B = G.p + goff[b] + (int64_t)k * np; tp.ldb = np;
+          tp.T = G.p + goff[b]; tp.ldt = ldg[b];
+          tp.B = G.p + goff[b] + (int64_t)k * ldg[b]; tp.ldb = ldg[b];
           tp.n = k; tp.ncol = m - k; tp.lower = 0; tp.trans = 0;
           tb.push(tp);
         }
         IdProb ip;
-        ip.G = G.p + goff[b]; ip.ldg = np; ip.piv = piv.p + coff[b]; ip.rank = rk.p + b;
+        ip.G = G.p + goff[b]; ip.ldg = ldg[b]; ip.piv = piv.p + coff[b]; ip.rank = rk.p + b;
         ip.U = up; ip.m = m;
         ib.push(ip);
         up += (size_t)m * k;

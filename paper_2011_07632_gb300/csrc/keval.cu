@@ -1,5 +1,6 @@
 // Kernel-matrix evaluation kernels (see keval.cuh).
 #include <algorithm>
+#include <mutex>
 #include <map>
 #include <type_traits>
 
@@ -170,6 +171,169 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
     SPD_LAUNCHED();
   }
   SPD_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------------------
+// Row blocks of the proxy matrices, factored where they are evaluated (the first step of
+// the ID's QR).  CTA b evaluates its rows of K(P_i, X_cand) into shared memory (the same
+// entries as k_proxy) and reduces them by Householder reflections without pivoting to an
+// upper triangle R_b.  Only R is kept: the reflector of column j is u = x - beta e_1 with
+// x = A(j:, j), beta = -sign(x_0) |x|, applied as A <- A - c u (u^T A) with
+// c = -1 / (beta (x_0 - beta)) (= 2 / u^T u), so the reflectors are never normalized.
+// Every column has a group of lanes (col_group_lanes); the group of column j + 1 forms the
+// next reflector's scalars right after its own update (look-ahead), so a step costs one
+// barrier.  Stacking the R_b of all blocks and reducing them (k_tri_merge) gives the R
+// factor of the whole proxy matrix (TSQR), from which the column-pivoted QR chooses the
+// ID's skeleton: pivots and |R_kk| depend on the matrix M only through M^T M, which R
+// shares.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_proxy_qr(const ProxyQrProb* __restrict__ probs,
+                                                  KernelFn kf_, int dim_) {
+  const ProxyQrProb Q = probs[blockIdx.x];
+  const ProxyProb& P = Q.p;
+  const KernelFn kf = P.dim ? P.kf : kf_;
+  const int dim = P.dim ? P.dim : dim_;
+  const int kd = kernel_dofs(kf.kind);
+  extern __shared__ double sA[];            // rows x m, column-major, ld col_group_ld
+  __shared__ double s_diag[kIdTsqrMaxM];    // R_jj
+  __shared__ double s_c[2];                 // reflector coefficient of steps j, j + 1
+  const int rows = Q.rows, m = P.cols;
+  const int lanes = col_group_lanes(m), ld = col_group_ld(rows, lanes);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // evaluation: one proxy point per thread and row, every candidate column
+  for (int i = tid; i < rows; i += blockDim.x) {
+    const int r = Q.r0 + i;
+    double y[3] = {0, 0, 0};
+    proxy_point(P, dim, r / kd, y);
+    for (int j = 0; j < m; ++j) {
+      const int64_t pc = P.c0 + j;
+      double v;
+      if (kd > 1) {
+        v = rpy_entry<double>(y[0] - P.xc[pc], y[1] - P.xc[P.ldxc + pc],
+                              y[2] - P.xc[2 * P.ldxc + pc], r % kd, (int)P.xc[3 * P.ldxc + pc],
+                              kf.inv_ell);
+      } else {
+        double r2 = 0.0;
+        for (int a = 0; a < dim; ++a) {
+          const double d = y[a] - P.xc[a * P.ldxc + pc];
+          r2 += d * d;
+        }
+        v = kernel_r2(kf, r2);
+      }
+      sA[i + (int64_t)j * ld] = v;
+    }
+  }
+  __syncthreads();
+  const int g = tid / lanes, sl = tid % lanes;     // column g, lane sl of its group
+  const int gpw = 32 / lanes;                      // groups per warp
+  const int g_lo = warp * gpw, g_hi = g_lo + gpw - 1;
+  // the first reflector, by the warp of column 0
+  if (warp == 0) {
+    double sq = 0.0;
+    if (g == 0)
+      for (int i = sl; i < rows; i += lanes) sq += sA[i] * sA[i];
+    sq = group_sum_n(sq, lanes);
+    if (tid == 0) s_c[0] = hh_scalars(&sA[0], sq, &s_diag[0]);
+  }
+  __syncthreads();
+  const int steps = min(rows, m);
+  for (int j = 0; j < steps; ++j) {
+    // warps without a column > j skip the step (warp-uniform)
+    if (g_hi > j && g_lo < m) {
+      const double c = s_c[j & 1];
+      const double* u = sA + (int64_t)j * ld + j;   // u over rows j..rows-1
+      const int len = rows - j;
+      const bool act = g > j && g < m;
+      double* ap = sA + (int64_t)(act ? g : j) * ld + j;
+      double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+      if (act && c != 0.0) {
+        int i = sl;
+        for (; i + 3 * lanes < len; i += 4 * lanes) {   // four independent loads per lane
+          w0 = fma(u[i], ap[i], w0);
+          w1 = fma(u[i + lanes], ap[i + lanes], w1);
+          w2 = fma(u[i + 2 * lanes], ap[i + 2 * lanes], w2);
+          w3 = fma(u[i + 3 * lanes], ap[i + 3 * lanes], w3);
+        }
+        for (; i < len; i += lanes) w0 = fma(u[i], ap[i], w0);
+      }
+      const double w = group_sum_n((w0 + w1) + (w2 + w3), lanes) * c;
+      const bool next = g == j + 1;   // update, and the next reflector's norm
+      double sq = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;   // independent partial sums
+      if (act && (c != 0.0 || next)) {
+        // the column and u are disjoint: loads of four rows before their stores
+        int i = sl;
+        for (; i + 3 * lanes < len; i += 4 * lanes) {
+          const double a0 = ap[i], a1 = ap[i + lanes], a2 = ap[i + 2 * lanes], a3 = ap[i + 3 * lanes];
+          const double v0 = u[i], v1 = u[i + lanes], v2 = u[i + 2 * lanes], v3 = u[i + 3 * lanes];
+          const double b0 = a0 - w * v0, b1 = a1 - w * v1, b2 = a2 - w * v2, b3 = a3 - w * v3;
+          ap[i] = b0; ap[i + lanes] = b1; ap[i + 2 * lanes] = b2; ap[i + 3 * lanes] = b3;
+          if (next) {
+            q1 = fma(b1, b1, q1);
+            q2 = fma(b2, b2, q2);
+            q3 = fma(b3, b3, q3);
+            if (i > 0) sq = fma(b0, b0, sq);
+          }
+        }
+        for (; i < len; i += lanes) {
+          const double b = ap[i] - w * u[i];
+          ap[i] = b;
+          if (next && i > 0) sq = fma(b, b, sq);
+        }
+        sq = (sq + q1) + (q2 + q3);
+      }
+      if (g_lo <= j + 1 && j + 1 <= g_hi && j + 1 < steps) {   // the warp of column j + 1
+        sq = group_sum_n(sq, lanes);
+        __syncwarp();   // the group's updated rows, visible to its lane 0
+        if (g == j + 1 && sl == 0) s_c[(j + 1) & 1] = hh_scalars(ap + 1, sq, &s_diag[j + 1]);
+      }
+    }
+    __syncthreads();
+  }
+  // R_b, dense m x m with zeros below the diagonal (and in the rows a short block lacks)
+  double* R = P.out;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, p = e / m;
+    double v = 0.0;
+    if (i < steps) v = (i == p) ? s_diag[i] : (i < p ? sA[i + (int64_t)p * ld] : 0.0);
+    R[i + (int64_t)p * P.ldo] = v;
+  }
+}
+
+void proxy_qr_launch(const Batch<ProxyQrProb>& b, const KernelFn& k, int dim, const char* tag,
+                     cudaStream_t s) {
+  if (b.empty()) { merge_skip(); return; }
+  if (merging()) {
+    std::vector<ProxyQrProb> h = b.h;
+    for (auto& q : h)
+      if (!q.p.dim) { q.p.kf = k; q.p.dim = dim; }
+    defer_launch("proxy_qr", h, [tag](std::vector<ProxyQrProb>& all, cudaStream_t st) {
+      Batch<ProxyQrProb> m;
+      m.h = std::move(all);
+      m.upload(st);
+      proxy_qr_launch(m, KernelFn{}, 0, tag, st);
+    });
+    return;
+  }
+  size_t smem = 0;
+  double f = 0.0;
+  for (const auto& q : b.h) {
+    SPD_REQUIRE(q.p.cols <= kIdTsqrMaxM && q.rows >= 1, "proxy_qr: block too large");
+    smem = std::max(smem, (size_t)col_group_ld(q.rows, col_group_lanes(q.p.cols)) * q.p.cols *
+                              sizeof(double));
+    const double mm = q.p.cols, r = q.rows;
+    // Householder QR of a rows x m block: 2 m^2 (rows - m/3) flops (rows >= m)
+    f += r >= mm ? 2.0 * mm * mm * (r - mm / 3.0) : 2.0 * r * r * (mm - r / 3.0);
+  }
+  // dynamic shared memory: the 227 KB of a CTA less the kernel's static arrays
+  constexpr int kDyn = 227 * 1024 - 4096;
+  SPD_REQUIRE(smem <= (size_t)kDyn, "proxy_qr: block exceeds shared memory");
+  static std::once_flag once;
+  std::call_once(once, [] {
+    SPD_CUDA(cudaFuncSetAttribute(k_proxy_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn));
+  });
+  ProfScope ps(tag ? tag : "proxy_qr", s, f);
+  k_proxy_qr<<<(unsigned)b.size(), 256, smem, s>>>(b.d.p, k, dim);
+  SPD_LAUNCHED();
 }
 
 // ---------------------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 // near-field product Y_i += sum_j K(X_i, X_j) X_j with tiles evaluated on the fly.
 #pragma once
 
+#include <algorithm>
+
 #include "dense.cuh"
 #include "merge.cuh"
 
@@ -46,6 +48,25 @@ struct ProxyProb {
   int dim = 0;
 };
 void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s);
+
+// One row block of a proxy matrix, evaluated and factored in shared memory: rows
+// [r0, r0 + rows) of K(P_i, X_cand) (p.cols = m candidate columns) are reduced by an
+// unpivoted Householder QR to their upper-triangular factor R_b, written as a dense
+// m x m matrix (zeros below the diagonal) at p.out, leading dimension p.ldo (= m).
+struct ProxyQrProb {
+  ProxyProb p;
+  int r0, rows;
+};
+// Largest candidate count of the blocked ID and the shared-memory budget of one block:
+// a node with m <= kIdTsqrMaxM candidates is factored in row blocks of
+// id_tsqr_rows(m, np) rows (at least m, about kIdTsqrBlockEntries / m).
+constexpr int kIdTsqrMaxM = 160;
+constexpr int kIdTsqrBlockEntries = 7168;
+inline int id_tsqr_rows(int m, int np) {
+  return std::min(np, std::max(m, kIdTsqrBlockEntries / std::max(m, 1)));
+}
+void proxy_qr_launch(const Batch<ProxyQrProb>& b, const KernelFn& k, int dim, const char* tag,
+                     cudaStream_t s);
 
 // Near-field product.  Problem: rows [row0, row0 + rows) of the sorted points; output
 // out (rows x ncol, ld ldo), accumulated (beta = 1) or overwritten (beta = 0).
