@@ -239,6 +239,19 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
                               int nrhs, int64_t ld, double relres_tol, int maxit, int* iters_out,
                               double* relres_out, void* stream);
 
+/* ---- FP32 grouped GEMM (test and benchmark hook) -------------------------------------
+ * C = alpha op(A) op(B) + beta C for one M x N x K product of FP32 column-major DEVICE
+ * matrices (op = transpose when tA / tB is 1), through the library's grouped GEMM:
+ * mode 0 on the CUDA cores (FP32 FMA), mode 1 on the tensor cores in TF32 (tcgen05.mma
+ * kind::tf32, FP32 accumulation), mode 2 on the tensor cores with every operand split into
+ * two TF32 parts (3xTF32: FP32-accurate products).  The FP32 H^2 products of the
+ * precision mode use modes 1 and 2.  The paper has no counterpart: the operation is the
+ * dense GEMM the H^2 products consist of.  Synchronizes `stream`.  Errors: EINVAL,
+ * TIMEOUT (a bounded wait in the tensor-core kernel gave up), ECUDA. */
+spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, int64_t lda, int tA,
+                              const float* B, int64_t ldb, int tB, float* C, int64_t ldc,
+                              float alpha, float beta, int mode, void* stream);
+
 /* ---- batched level sweep over independent instances -----------------------------------
  * The construction of Alg. 5.3 (with the H^2 build before it and the ULV factorization
  * after it) proceeds level by level with the same steps for every matrix; for many

@@ -328,6 +328,20 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
   vbeg.clear();
   flops = 0.0;
   bytes = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {   // tensor cores: the problems as given, 128 x tc_nt tiles
+      for (const auto& P : probs) {
+        double kk = 0.0;
+        for (int g = P.seg0; g < P.seg1; ++g) kk += segs[g].K;
+        flops += 2.0 * P.M * (double)P.N * kk;
+      }
+      tiles = tc_gemm_tiles(probs, &tc_nt);
+      d_segs.upload(segs, s);
+      d_probs.upload(probs, s);
+      d_tiles.upload(tiles, s);
+      return;
+    }
+  }
   int maxn = 0;
   for (const auto& p : probs) maxn = std::max(maxn, p.N);
   nb = gemm_variant(maxn);
@@ -438,9 +452,11 @@ struct DeferredGemm : Deferred {
   std::vector<GemmSegT<T>> segs;
   std::vector<GemmProbT<T>> probs;
   const char* tag = "gemm";
+  int tc = 0;
   void launch_merged(const std::vector<Deferred*>& group, cudaStream_t s) override {
     GemmBatchT<T> m;
     m.tag = tag;
+    m.tc = tc;
     for (Deferred* d : group) {
       const auto* x = static_cast<const DeferredGemm<T>*>(d);
       const int off = (int)m.segs.size();
@@ -464,12 +480,20 @@ void GemmBatchT<T>::launch(cudaStream_t s) const {
     d->segs = segs;
     d->probs = probs;
     d->tag = tag;
-    merge_ctx().m->submit(sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", std::move(d));
+    d->tc = tc;
+    merge_ctx().m->submit(sizeof(T) == 8 ? "gemm_f64" : "gemm_f32_tc" + std::to_string(tc),
+                          std::move(d));
     return;
   }
   const int64_t nt = (int64_t)tiles.size();
   if (nt == 0) return;
   ProfScope ps(tag, s, flops, bytes);
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {
+      tc_gemm_launch(d_probs.p, d_segs.p, d_tiles.p, nt, tc_nt, tc == 2, tc_error_word(), s);
+      return;
+    }
+  }
   for (size_t v = 0; v < vnb.size(); ++v) {
     for (int64_t b0 = vbeg[v]; b0 < vbeg[v + 1]; b0 += 2147483647LL) {
       const int g = (int)std::min<int64_t>(vbeg[v + 1] - b0, 2147483647LL);

@@ -63,6 +63,8 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_P), _P,
                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                              ctypes.POINTER(_I)],
+    "spdhss_gemm_f32": [_I, _I, _I, _P, _I64, _I, _P, _I64, _I, _P, _I64, ctypes.c_float,
+                        ctypes.c_float, _I, _P],
     "pcg_solve_batched": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                           ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
