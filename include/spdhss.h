@@ -153,6 +153,24 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
                                const double* omega, uint64_t seed, void* stream,
                                hss_handle* out);
 
+/* spdhss_build_tol with a precision mode for the sampling product Y^(k) = (A - blkdiag_k A)
+ * Omega, the construction's dominant cost (Sec. 6.1):
+ *   precision 0: FP64 throughout (= spdhss_build_tol);
+ *   precision 1: the H^2 product run in FP32 (FP32 copies of the bases and couplings made
+ *                on first use and kept in the H^2 handle, near-field kernel entries
+ *                evaluated in FP32, FP32 accumulation), its basis and coupling GEMMs on
+ *                the tensor cores with split operands (3xTF32: FP32-accurate products);
+ *   precision 2: the same with plain TF32 products (about 1e-3 relative error per product).
+ * Everything after the sampling stays FP64: the diagonal-block Cholesky factorizations,
+ * the triangular solves, the column-pivoted QR that compresses the scaled samples into
+ * orthonormal bases, and the formation of B_ij, U_i and R_i, so that the result keeps the
+ * SPD guarantee of Sec. 3.2 (the bases are orthonormal to FP64 rounding).  Errors as
+ * spdhss_build_tol, and EINVAL for another precision, TIMEOUT if a bounded wait in a
+ * tensor-core kernel gave up. */
+spdhss_status spdhss_build_precision(h2_handle h2, int rank, double tol, int oversample,
+                                     const double* omega, uint64_t seed, int precision,
+                                     void* stream, hss_handle* out);
+
 /* Y = H X with the HSS approximation H (same layout rules as h2_matmul). */
 spdhss_status hss_matmul(hss_handle hss, const double* X, double* Y, int nrhs, int64_t ld,
                          void* stream);

@@ -124,9 +124,10 @@ class HSS:
     """SPD HSS approximation built from an H^2 matrix (spdhss_build, Alg. 5.3)."""
 
     def __init__(self, h2: H2, rank: int, oversample: int = 10, omega=None, seed: int = 0,
-                 stream=None, tol: float = 0.0):
+                 stream=None, tol: float = 0.0, precision: int = 0):
         """tol > 0: bases truncated at that relative tolerance, rank being the cap
-        (spdhss_build_tol)."""
+        (spdhss_build_tol).  precision 1 / 2: the sampling product in FP32 on the tensor
+        cores, 3xTF32 / TF32 (spdhss_build_precision)."""
         self.h2 = h2
         self.rank, self.oversample, self.tol = int(rank), int(oversample), float(tol)
         om = None
@@ -134,9 +135,10 @@ class HSS:
             om = _colmajor(omega)
             assert om.shape == (rank + oversample, h2.n)
         h = ctypes.c_void_p()
-        N.check(N.lib().spdhss_build_tol(h2._h, int(rank), float(tol), int(oversample),
-                                         _ptr(om) if om is not None else None, int(seed),
-                                         _stream(stream), ctypes.byref(h)))
+        N.check(N.lib().spdhss_build_precision(h2._h, int(rank), float(tol), int(oversample),
+                                               _ptr(om) if om is not None else None, int(seed),
+                                               int(precision), _stream(stream),
+                                               ctypes.byref(h)))
         self._h = h
 
     def matmul(self, X, stream=None) -> torch.Tensor:

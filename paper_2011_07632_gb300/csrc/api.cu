@@ -325,11 +325,12 @@ spdhss_status h2_destroy(h2_handle h) {
 
 extern "C" {
 
-spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversample,
-                               const double* omega, uint64_t seed, void* stream,
-                               hss_handle* out) {
+spdhss_status spdhss_build_precision(h2_handle h2, int rank, double tol, int oversample,
+                                     const double* omega, uint64_t seed, int precision,
+                                     void* stream, hss_handle* out) {
   return spd::guarded("spdhss_build", [&] {
     SPD_REQUIRE(tol >= 0.0 && tol < 1.0, "tol must be in [0, 1)");
+    SPD_REQUIRE(precision >= 0 && precision <= 2, "precision must be 0, 1 or 2");
     spd::StreamScope ss((cudaStream_t)stream);
     SPD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -339,7 +340,8 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
     SPD_REQUIRE(omega == nullptr || spd::is_device_pointer(omega), "omega must be a device pointer");
     if (tol <= 0.0) {
       std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-      spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream, tol);
+      spd::spdhss_build_impl(hs.get(), h2, rank, oversample, omega, seed, (cudaStream_t)stream, tol,
+                             precision);
       *out = hs.release();
       return;
     }
@@ -348,7 +350,8 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
     int r = std::min(rank, 64);
     while (true) {
       std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
-      spd::spdhss_build_impl(hs.get(), h2, r, oversample, omega, seed, (cudaStream_t)stream, tol);
+      spd::spdhss_build_impl(hs.get(), h2, r, oversample, omega, seed, (cudaStream_t)stream, tol,
+                             precision);
       int mr = 0;
       for (int v : hs->rk) mr = std::max(mr, v);
       if (mr < r || r >= rank) {
@@ -360,9 +363,15 @@ spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversampl
   });
 }
 
+spdhss_status spdhss_build_tol(h2_handle h2, int rank, double tol, int oversample,
+                               const double* omega, uint64_t seed, void* stream,
+                               hss_handle* out) {
+  return spdhss_build_precision(h2, rank, tol, oversample, omega, seed, 0, stream, out);
+}
+
 spdhss_status spdhss_build(h2_handle h2, int rank, int oversample, const double* omega,
                            uint64_t seed, void* stream, hss_handle* out) {
-  return spdhss_build_tol(h2, rank, 0.0, oversample, omega, seed, stream, out);
+  return spdhss_build_precision(h2, rank, 0.0, oversample, omega, seed, 0, stream, out);
 }
 
 spdhss_status hss_matmul(hss_handle hs, const double* X, double* Y, int nrhs, int64_t ld,

@@ -458,7 +458,7 @@ static bool near_store(spdhss_h2_s* h, cudaStream_t s) {
 
 template <class F>
 static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int nslot,
-                            const F* Ub, const F* Cb, cudaStream_t s) {
+                            const F* Ub, const F* Cb, cudaStream_t s, int tc = 0) {
   const TreeHost& T = h->th;
   const int64_t n = T.n, K = std::max<int64_t>(h->Ktot, 1);
   const int D = T.D;
@@ -615,6 +615,17 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   p.up_leaf.tag = p.leaf_out.tag = btag;
   for (auto& g : p.up) g.tag = btag;
   for (auto& g : p.down) g.tag = btag;
+  if (tc) {   // FP32 plans: the basis and coupling products on the tensor cores
+    p.up_leaf.tc = p.leaf_out.tc = p.coupling.tc = tc;
+    for (auto& g : p.up) g.tc = tc;
+    for (auto& g : p.down) g.tc = tc;
+    const char* ttag = nslot > 1 ? "h2_basis_sample_tc" : "h2_basis_tc";
+    p.up_leaf.tag = p.leaf_out.tag = ttag;
+    for (auto& g : p.up) g.tag = ttag;
+    for (auto& g : p.down) g.tag = ttag;
+    p.coupling.tag = nslot > 1 ? "h2_coupling_sample_tc" : "h2_coupling_tc";
+    p.near.tag = nslot > 1 ? "near_sample_f32" : "near_h2_f32";
+  }
   p.up_leaf.upload(s);
   for (auto& g : p.up) g.upload(s);
   p.coupling.upload(s);
@@ -1054,6 +1065,22 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
     return;
   }
   h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, h->coup.p, s);
+}
+
+// The sampling product of the precision mode: an FP32 plan with LCA slots over FP32
+// copies of the bases and (source-major) couplings, its GEMMs on the tensor cores
+// (tc = 1: TF32, 2: 3xTF32), the near field evaluated in FP32 on the fly.
+void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, cudaStream_t s) {
+  if (h->basis_f.n == 0) {
+    h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
+    convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
+  }
+  if (h->coup_f.n == 0) {
+    h->coup_f.alloc(std::max<size_t>(h->coup.n, 1));
+    if (h->coup.n) convert_d2f(h->coup.p, h->coup_f.p, (int64_t)h->coup.n, s);
+  }
+  h2_plan_build_t<float>(h, p, ncol, nslot, h->basis_f.p, h->coup_f.p, s, tc);
+  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {

@@ -126,6 +126,7 @@ struct spdhss_h2_s {
   // destination-major couplings (made on first use): FP32 and FP64 copies, and per node the
   // offset of its coupling matrix in them
   spd::DevBuf<float> coup_fd;
+  spd::DevBuf<float> coup_f;         // FP32 copy of `coup` (precision-mode sampling), on use
   spd::DevBuf<double> coup_dd;
   std::vector<int64_t> coup_dm_off;
   std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
@@ -141,6 +142,9 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
 void h2_plan_run(const spdhss_h2_s* h, const H2Plan& p, cudaStream_t s);
 // the FP32 plan for ncol columns (generators converted on first use), cached in the handle
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s);
+// the precision mode's sampling plan: FP32, LCA slots, GEMMs on the tensor cores
+// (tc = 1 TF32, 2 3xTF32), near field in FP32 on the fly
+void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, cudaStream_t s);
 void h2_plan_run(const spdhss_h2_s* h, const H2PlanF& p, cudaStream_t s);
 // element-wise conversions of n x ncol column-major blocks between FP64 and FP32
 void convert_d2f(const double* x, float* y, int64_t count, cudaStream_t s);

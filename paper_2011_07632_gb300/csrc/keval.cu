@@ -610,7 +610,7 @@ void NearBatchT<T>::upload(cudaStream_t s) {
   // Problems that carry the choice of their first upload keep it (all of one launch
   // share it: merged launches are grouped by it).
   if (mx <= 16) cb = -(mx <= 1 ? 1 : (mx <= 2 ? 2 : (mx <= 4 ? 4 : (mx <= 8 ? 8 : 16))));
-  else cb = 64;
+  else cb = std::is_same<T, double>::value ? 64 : -16;   // FP32: blocks of 16 columns
   for (const auto& p : probs)
     if (p.cb != 0) { cb = p.cb; break; }
   for (auto& p : probs) {

@@ -61,7 +61,7 @@ struct ProxyQrProb {
 // a node with m <= kIdTsqrMaxM candidates is factored in row blocks of
 // id_tsqr_rows(m, np) rows (at least m, about kIdTsqrBlockEntries / m).
 constexpr int kIdTsqrMaxM = 160;
-constexpr int kIdTsqrBlockEntries = 24576;
+constexpr int kIdTsqrBlockEntries = 12800;
 inline int id_tsqr_rows(int m, int np) {
   return std::min(np, std::max(m, kIdTsqrBlockEntries / std::max(m, 1)));
 }

@@ -99,7 +99,8 @@ void check_info(DevBuf<int>& info, const char* what, int64_t base, cudaStream_t 
 }  // namespace
 
 void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
-                       const double* omega, uint64_t seed, cudaStream_t s, double rtol) {
+                       const double* omega, uint64_t seed, cudaStream_t s, double rtol,
+                       int precision) {
   const TreeHost& T = h2->th;
   const int64_t n = T.n;
   const int D = T.D;
@@ -130,18 +131,42 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
   merge_stage(3, 0);
   const int nslot = L - 1;
   H2Plan plan;
-  h2_plan_build(h2, plan, sc, nslot, s);
-  if (omega) permute_to_sorted(omega, n, plan.xs.p, n, sc, h2->td.perm.p, s);
-  else {
+  DevBuf<double> Ymixed;
+  double* Y = nullptr;            // n x (s * (L-1)), ld n
+  if (precision == 0) {
+    h2_plan_build(h2, plan, sc, nslot, s);
+    if (omega) permute_to_sorted(omega, n, plan.xs.p, n, sc, h2->td.perm.p, s);
+    else {
+      DevBuf<double> om((size_t)n * sc);
+      philox_normal(om.p, n, sc, n, seed, s);
+      permute_to_sorted(om.p, n, plan.xs.p, n, sc, h2->td.perm.p, s);
+      SPD_CUDA(cudaStreamSynchronize(s));
+    }
+    h2_plan_run(h2, plan, s);
+    Y = plan.ys.p;
+  } else {
+    // precision mode: the sampling product in FP32 (FP32 generators and kernel entries,
+    // basis and coupling GEMMs on the tensor cores, FP32 accumulation), then FP64 again
+    spdhss_h2_s* hm = const_cast<spdhss_h2_s*>(h2);   // FP32 copies: a cache of the handle
+    H2PlanF fp;
+    h2_plan_sample_f(hm, fp, sc, nslot, precision == 2 ? 1 : 2, s);
     DevBuf<double> om((size_t)n * sc);
-    philox_normal(om.p, n, sc, n, seed, s);
-    permute_to_sorted(om.p, n, plan.xs.p, n, sc, h2->td.perm.p, s);
-    SPD_CUDA(cudaStreamSynchronize(s));
+    if (omega) permute_to_sorted(omega, n, om.p, n, sc, h2->td.perm.p, s);
+    else {
+      DevBuf<double> o2((size_t)n * sc);
+      philox_normal(o2.p, n, sc, n, seed, s);
+      permute_to_sorted(o2.p, n, om.p, n, sc, h2->td.perm.p, s);
+      SPD_CUDA(cudaStreamSynchronize(s));
+    }
+    convert_d2f(om.p, fp.xs.p, n * sc, s);
+    h2_plan_run(h2, fp, s);
+    Ymixed.alloc((size_t)n * sc * nslot);
+    convert_f2d(fp.ys.p, Ymixed.p, n * sc * nslot, s);
+    tc_check(s);
+    Y = Ymixed.p;
   }
-  h2_plan_run(h2, plan, s);
-  k_suffix_slots<<<ceil_div(n * sc, 256), 256, 0, s>>>(plan.ys.p, n * sc, nslot);
+  k_suffix_slots<<<ceil_div(n * sc, 256), 256, 0, s>>>(Y, n * sc, nslot);
   SPD_LAUNCHED();
-  double* Y = plan.ys.p;          // n x (s * (L-1)), ld n
   const int64_t ycols = (int64_t)sc * nslot;
 
   DevBuf<int> info(2);

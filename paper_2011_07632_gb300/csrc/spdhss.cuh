@@ -26,8 +26,11 @@ struct spdhss_hss_s {
 };
 
 namespace spd {
+// precision: 0 FP64 throughout; 1 the sampling product in FP32 with its GEMMs on the
+// tensor cores in 3xTF32; 2 the same in plain TF32.  Everything after the sampling is FP64.
 void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
-                       const double* omega, uint64_t seed, cudaStream_t s, double rtol = 0.0);
+                       const double* omega, uint64_t seed, cudaStream_t s, double rtol = 0.0,
+                       int precision = 0);
 void hss_matmul_impl(spdhss_hss_s* hs, const double* X, double* Y, int nrhs, int64_t ld,
                      cudaStream_t s);
 // Philox4x32-10 standard normals: out[i + j*ld] for i < n, j < ncol, counter (i, j)

@@ -45,6 +45,8 @@ _SIGS = {
     "h2_destroy": [_P],
     "spdhss_build": [_P, _I, _I, _P, ctypes.c_uint64, _P, ctypes.POINTER(_P)],
     "spdhss_build_tol": [_P, _I, _D, _I, _P, ctypes.c_uint64, _P, ctypes.POINTER(_P)],
+    "spdhss_build_precision": [_P, _I, _D, _I, _P, ctypes.c_uint64, _I, _P,
+                               ctypes.POINTER(_P)],
     "hss_matmul": [_P, _P, _P, _I, _I64, _P],
     "hss_info": [_P, _PI64],
     "hss_destroy": [_P],

@@ -66,3 +66,56 @@ def test_fp32_product_split_rows(nrhs):
     assert rel(y32, y64) < 1e-4
     # deterministic: a second product is bit-identical
     assert np.array_equal(h.matmul_mixed(x).cpu().numpy(), y32)
+
+
+# ---- precision mode of the construction (spdhss_build_precision) ------------------------
+# The sampling product runs in FP32 with its GEMMs on the tensor cores (3xTF32, or plain
+# TF32); everything after it is FP64.  Bounds from the arithmetic and measured values:
+# 3xTF32 carries FP32 rounding (~1e-6 relative) into the samples, which moves the HSS by
+# about 1e-5 (measured 6e-6 .. 3e-5 against the FP64 oracle) and leaves its approximation
+# error and PCG iteration counts unchanged; plain TF32 products carry ~1e-3 (measured
+# 1e-3 .. 7e-3 against the oracle, iterations up to 1.7x on the Matern case).
+PREC_CASES = [("exp", 1.0, 1e-2, 3, 3000, 64, 40), ("matern32", 0.2, 1e-3, 2, 2500, 64, 30),
+              ("gauss", 0.3, 1e-3, 3, 2000, 64, 30)]
+
+
+@pytest.mark.parametrize("kind,ell,sigma,dim,n,leaf,r", PREC_CASES)
+def test_precision_mode_against_the_oracle(kind, ell, sigma, dim, n, leaf, r):
+    api = need_gpu()
+    from oracle import h2 as OH
+    from oracle import pcg as OP
+    from oracle import spdhss as OS
+    from oracle import tree as OT
+    from oracle import ulv as OU
+    X = inputs.uniform_cube(n, dim, 0)
+    Om = inputs.sketch(n, r + 10, 2)
+    h = api.H2(X, kind, ell, sigma, leaf, 1e-8)
+    tr = OT.build_tree(X, leaf)
+    Mh = OH.dense(OH.build_h2(tr, X, OK.NAMES[kind], ell, sigma, 1e-8))
+    ohss = OS.build_spdhss(tr, Mh, Om[tr.perm], r)
+    Ho = OS.assemble_dense(ohss)
+    b = inputs.rhs(n, 1, 1)
+    _, ito, _ = OP.pcg(lambda v: Mh @ v, OU.ULV(ohss).solve, b[tr.perm], 1e-6, 3000)
+    a_oracle = rel(Ho, Mh)   # the oracle's approximation error
+    for prec, bound, approx_slack, it_factor in ((1, 1e-4, 1e-3, 1.0), (2, 2e-2, 0.3, 2.0)):
+        hs = api.HSS(h, r, 10, omega=Om, precision=prec)
+        Hg = hs.matmul(np.eye(n)).cpu().numpy()[np.ix_(tr.perm, tr.perm)]
+        assert rel(Hg, Ho) < bound, (prec, rel(Hg, Ho))
+        assert rel(Hg, Mh) <= a_oracle * (1 + approx_slack) + 1e-8, (prec, rel(Hg, Mh), a_oracle)
+        x, it, rr = api.pcg_solve(h, api.ULV(hs), b, tol=1e-6, raise_on_no_convergence=True)
+        assert rr[0] <= 1e-6
+        assert it[0] <= it_factor * int(ito[0]) + 1, (prec, int(it[0]), int(ito[0]))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_precision_mode_is_spd(prec):
+    """SPD by a dense eigensolve at n = 512 with tiny shifts (Sec. 3.2): the compression,
+    the factors and B_ij stay FP64, so FP32 samples leave the guarantee intact."""
+    api = need_gpu()
+    n = 512
+    X = inputs.uniform_cube(n, 3, 6)
+    for kind, sigma, r in (("gauss", 1e-6, 4), ("matern32", 1e-5, 10)):
+        h = api.H2(X, kind, 0.2, sigma, 16, 1e-8)
+        hs = api.HSS(h, r, 10, seed=11, precision=prec)
+        Hg = hs.matmul(np.eye(n)).cpu().numpy()
+        assert np.linalg.eigvalsh(0.5 * (Hg + Hg.T)).min() > 0.0
