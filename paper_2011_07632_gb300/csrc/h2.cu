@@ -1084,11 +1084,13 @@ void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, c
 }
 
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
+  // each FP32 copy on its own first use (the precision-mode sampling makes the bases and
+  // the source-major couplings, the products here the destination-major couplings)
   if (h->basis_f.n == 0) {
     h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
     convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
-    coup_dm_build<float>(h, h->coup_fd, s);
   }
+  if (h->coup_fd.n == 0) coup_dm_build<float>(h, h->coup_fd, s);
   auto it = h->plans_f.find(ncol);
   if (it == h->plans_f.end()) {
     std::unique_ptr<H2PlanF> p(new H2PlanF());

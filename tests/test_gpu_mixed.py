@@ -119,3 +119,20 @@ def test_precision_mode_is_spd(prec):
         hs = api.HSS(h, r, 10, seed=11, precision=prec)
         Hg = hs.matmul(np.eye(n)).cpu().numpy()
         assert np.linalg.eigvalsh(0.5 * (Hg + Hg.T)).min() > 0.0
+
+
+def test_precision_build_then_fp32_products_on_one_handle():
+    """The precision-mode build makes some FP32 copies of the H^2 generators (bases,
+    source-major couplings); the FP32 product made afterwards on the same handle must still
+    make its own (destination-major couplings) and agree with the FP64 product."""
+    api = need_gpu()
+    n = 3000
+    X = inputs.uniform_cube(n, 3, 8)
+    h = api.H2(X, "matern32", 0.2, 1e-3, 64, 1e-8)
+    hs = api.HSS(h, 30, 10, seed=4, precision=1)
+    x = inputs.rhs(n, 2, 9)
+    assert rel(h.matmul_mixed(x).cpu().numpy(), h.matmul(x).cpu().numpy()) < 2e-5
+    b = inputs.rhs(n, 1, 10)
+    _, it, rr = api.pcg_solve(h, api.ULV(hs), b, tol=1e-6, mixed=True,
+                              raise_on_no_convergence=True)
+    assert rr[0] <= 1e-6
