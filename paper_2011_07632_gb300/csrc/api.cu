@@ -45,7 +45,23 @@ static cudaMemPool_t pool_for_current_device() {
 
 void* pool_alloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
-  SPD_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s));
+  cudaMemPool_t pool = pool_for_current_device();
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+  if (e == cudaErrorMemoryAllocation) {
+    // the pool keeps freed memory for reuse; a large request that its free pieces cannot
+    // serve gets the memory back from the pool (after the stream's pending frees) and
+    // is tried once more
+    cudaGetLastError();
+    SPD_CUDA(cudaStreamSynchronize(s));
+    SPD_CUDA(cudaMemPoolTrimTo(pool, 0));
+    e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? SPDHSS_ENOMEM : SPDHSS_ECUDA,
+                std::string("device allocation of ") + std::to_string(bytes) + " bytes: " +
+                    cudaGetErrorString(e));
+  }
   return p;
 }
 

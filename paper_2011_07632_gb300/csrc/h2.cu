@@ -1075,11 +1075,12 @@ void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, c
     h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
     convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
   }
-  if (h->coup_f.n == 0) {
-    h->coup_f.alloc(std::max<size_t>(h->coup.n, 1));
-    if (h->coup.n) convert_d2f(h->coup.p, h->coup_f.p, (int64_t)h->coup.n, s);
-  }
-  h2_plan_build_t<float>(h, p, ncol, nslot, h->basis_f.p, h->coup_f.p, s, tc);
+  // the source-major FP32 couplings live as long as the plan (half the FP64 couplings'
+  // bytes; made again per build rather than kept beside the destination-major copy of the
+  // FP32 products)
+  p.coup_src.alloc(std::max<size_t>(h->coup.n, 1));
+  if (h->coup.n) convert_d2f(h->coup.p, p.coup_src.p, (int64_t)h->coup.n, s);
+  h2_plan_build_t<float>(h, p, ncol, nslot, h->basis_f.p, p.coup_src.p, s, tc);
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -89,6 +89,7 @@ struct H2PlanT {
   GemmBatchT<T> near_g;     // the near field from the stored blocks (replaces `near`)
   RowCoupBatchT<T> near_r;  // ... streamed row by row for at most 4 columns
   bool near_stored = false, near_rows = false;
+  DevBuf<T> coup_src;       // couplings in this plan's type when it owns a copy of them
 };
 using H2Plan = H2PlanT<double>;
 using H2PlanF = H2PlanT<float>;
@@ -126,7 +127,6 @@ struct spdhss_h2_s {
   // destination-major couplings (made on first use): FP32 and FP64 copies, and per node the
   // offset of its coupling matrix in them
   spd::DevBuf<float> coup_fd;
-  spd::DevBuf<float> coup_f;         // FP32 copy of `coup` (precision-mode sampling), on use
   spd::DevBuf<double> coup_dd;
   std::vector<int64_t> coup_dm_off;
   std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
