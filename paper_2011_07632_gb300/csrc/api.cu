@@ -35,6 +35,11 @@ static cudaMemPool_t pool_for_current_device() {
   props.handleTypes = cudaMemHandleTypeNone;
   props.location.type = cudaMemLocationTypeDevice;
   props.location.id = dev;
+  // the pool may grow to the whole device (its default limit is smaller), so that the
+  // largest workloads can hold their generators and factors in it
+  size_t free_b = 0, total_b = 0;
+  SPD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  props.maxSize = total_b;
   cudaMemPool_t pool;
   SPD_CUDA(cudaMemPoolCreate(&pool, &props));
   uint64_t keep = UINT64_MAX;
