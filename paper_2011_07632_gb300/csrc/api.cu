@@ -1,3 +1,4 @@
+#include <unordered_set>
 // C ABI entry points (include/spdhss.h): argument checks, error capture, and the H^2 calls.
 #include <atomic>
 #include <cstdio>
@@ -23,6 +24,7 @@ cudaStream_t& current_stream() {
 // One memory pool per device, kept across calls (release threshold: never trim).
 static std::mutex g_pool_mu;
 static std::map<int, cudaMemPool_t> g_pools;
+static std::unordered_set<void*> g_plain;   // allocations made outside the pool
 
 static cudaMemPool_t pool_for_current_device() {
   int dev = 0;
@@ -60,6 +62,16 @@ void* pool_alloc(size_t bytes, cudaStream_t s) {
     SPD_CUDA(cudaStreamSynchronize(s));
     SPD_CUDA(cudaMemPoolTrimTo(pool, 0));
     e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+      // the pool's address ranges are fragmented: a plain allocation, which pool_free
+      // recognizes and returns with cudaFree
+      cudaGetLastError();
+      e = cudaMalloc(&p, bytes);
+      if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        g_plain.insert(p);
+      }
+    }
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -71,6 +83,16 @@ void* pool_alloc(size_t bytes, cudaStream_t s) {
 }
 
 void pool_free(void* p, cudaStream_t s) {
+  bool plain = false;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    plain = g_plain.erase(p) > 0;
+  }
+  if (plain) {   // the stream's work on it first, then the plain free
+    cudaStreamSynchronize(s);
+    cudaFree(p);
+    return;
+  }
   if (cudaFreeAsync(p, s) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(p);
