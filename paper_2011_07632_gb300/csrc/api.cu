@@ -82,6 +82,17 @@ void* pool_alloc(size_t bytes, cudaStream_t s) {
   return p;
 }
 
+size_t device_free_bytes(cudaStream_t s) {
+  (void)s;
+  cudaMemPool_t pool = pool_for_current_device();
+  uint64_t reserved = 0, used = 0;
+  SPD_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  SPD_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  size_t f = 0, t = 0;
+  SPD_CUDA(cudaMemGetInfo(&f, &t));
+  return f + (size_t)(reserved > used ? reserved - used : 0);
+}
+
 void pool_free(void* p, cudaStream_t s) {
   bool plain = false;
   {

@@ -82,6 +82,12 @@ struct StreamScope {
 };
 void* pool_alloc(size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
+// device memory free, counting what the library pool holds unused
+size_t device_free_bytes(cudaStream_t s);
+// whether an optional copy of `bytes` fits with a margin for the work that follows
+inline bool fits_on_device(size_t bytes, cudaStream_t s) {
+  return bytes + ((size_t)16 << 30) <= device_free_bytes(s);
+}
 
 // Device allocation owned by its object, stream ordered on the stream current at allocation.
 template <class T>

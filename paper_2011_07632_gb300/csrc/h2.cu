@@ -1056,8 +1056,11 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
   // Few columns: the coupling step streams the destination-major FP64 copy (each entry read
   // once, coalesced, spread over many CTAs); the grouped GEMM would give every node one CTA
   // with a long serial loop over its partners.  The copy is made on first use and kept.
-  if (nslot == 1 && ncol <= 4) {
-    spdhss_h2_s* hm = const_cast<spdhss_h2_s*>(h);   // a cache of the handle
+  // (each unordered pair twice: twice the bytes of the FP64 couplings; made only when it
+  // fits beside everything else, else the grouped GEMM over the stored couplings)
+  spdhss_h2_s* hm = const_cast<spdhss_h2_s*>(h);   // a cache of the handle
+  if (nslot == 1 && ncol <= 4 &&
+      (hm->coup_dd.n > 0 || fits_on_device(2 * h->coup.bytes(), s))) {
     if (hm->coup_dd.n == 0) coup_dm_build<double>(hm, hm->coup_dd, s);
     h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, nullptr, s);
     rowcoup_plan<double>(h, p, ncol, h->coup_dd.p, s);
@@ -1091,12 +1094,22 @@ H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
     h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
     convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
   }
-  if (h->coup_fd.n == 0) coup_dm_build<float>(h, h->coup_fd, s);
+  // the destination-major FP32 couplings (each pair twice: the bytes of the FP64
+  // couplings) when they fit; else each plan converts the couplings once (half those
+  // bytes) and runs the grouped GEMM over them
   auto it = h->plans_f.find(ncol);
   if (it == h->plans_f.end()) {
+    const bool dm = h->coup_fd.n > 0 || fits_on_device(h->coup.bytes(), s);
+    if (dm && h->coup_fd.n == 0) coup_dm_build<float>(h, h->coup_fd, s);
     std::unique_ptr<H2PlanF> p(new H2PlanF());
-    h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, nullptr, s);
-    rowcoup_plan<float>(h, *p, ncol, h->coup_fd.p, s);
+    if (dm) {
+      h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, nullptr, s);
+      rowcoup_plan<float>(h, *p, ncol, h->coup_fd.p, s);
+    } else {
+      p->coup_src.alloc(std::max<size_t>(h->coup.n, 1));
+      if (h->coup.n) convert_d2f(h->coup.p, p->coup_src.p, (int64_t)h->coup.n, s);
+      h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, p->coup_src.p, s);
+    }
     SPD_CUDA(cudaStreamSynchronize(s));
     it = h->plans_f.emplace(ncol, std::move(p)).first;
   }
