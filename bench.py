@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--matvec-case", type=int, default=0,
                     help="profiling case: H2 of the Gaussian workload at this n, then 5 products "
                          "with 8 columns (prints timings, no benchmark line)")
+    ap.add_argument("--precision", action="store_true",
+                    help="the precision workload (n = 500,000 Matern-3/2, rank 100) as its own line")
+    ap.add_argument("--n-precision", type=int, default=500_000)
     ap.add_argument("--mixed", action="store_true",
                     help="with --matvec-case: also 5 FP32 products (mixed precision)")
     return ap.parse_args()
@@ -270,6 +273,7 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     native.lib().spdhss_profile(0)
     (x2, it2, rr2), t_pcg32 = timed(lambda: api.pcg_solve(h, u, B, tol=c["relres"], maxit=k, mixed=True))
     info = h.info()
+    prec = precision_build_record(api, native, torch, h, hs, c, timed, c["n"])
     # where the construction's time goes: a second, profiled build (library CUDA events)
     u.close(); hs.close(); h.close()
     del u, hs, h
@@ -308,11 +312,131 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
             "roofline_h2_coupling_f32": roof_hbm(prof32.get("h2_coupling_f32")),
             "kernels": {k2: round(v["ms"] / reps, 3) for k2, v in prof32.items()},
         },
+        "precision_build": prec,
     }
     u.close(); hs.close(); h.close()
     del pts, B
     torch.cuda.empty_cache()
     return out
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 figure times TF32's nominal ratio (1/2)."""
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    return pk["bf16_tflops"] / 2.0, "measured bf16 x 1/2 (nominal TF32:BF16 dense ratio)"
+
+
+def precision_build_record(api, native, torch, h, hs64, c, timed, n):
+    """The precision mode of the construction on an H^2 matrix already built: the sampling
+    product in FP32 with tensor-core (3xTF32) GEMMs, FP64 afterwards.  Its build time next
+    to the FP64 one, where the time goes, the tensor-core coupling GEMM against the TF32
+    peak, and the difference of the two HSS matrices on random vectors."""
+    from paper_2011_07632_gb300 import inputs
+    hs1, t1 = timed(lambda: api.HSS(h, c["rank"], c["oversample"], seed=7, precision=1))
+    hs1.close()
+    native.lib().spdhss_profile(1)
+    hs1, t1b = timed(lambda: api.HSS(h, c["rank"], c["oversample"], seed=7, precision=1))
+    prof = native.profile_report()
+    native.lib().spdhss_profile(0)
+    x = inputs.rhs(n, 4, 21)
+    y64 = hs64.matmul(x).cpu().numpy()
+    y1 = hs1.matmul(x).cpu().numpy()
+    hs1.close()
+    diff = float(np.linalg.norm(y1 - y64) / np.linalg.norm(y64))
+    tc = prof.get("h2_coupling_sample_tc", {"ms": 0.0, "flops": 0.0})
+    peak, src = tf32_peak()
+    ach = tc["flops"] / max(tc["ms"], 1e-9) / 1e9   # algorithmic TFLOP/s (FP32-accurate products)
+    return {"spdhss_build_ms": t1, "spdhss_build_profiled_ms": t1b,
+            "hss_product_rel_diff_vs_fp64": diff,
+            "kernels_ms": {k: round(v["ms"], 2) for k, v in
+                           sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+            "roofline_coupling_tc": {"bound": "tensor", "kernel": "k_gemm_tf32 (3xTF32)",
+                                     "achieved": ach, "achieved_tf32_mma": 3 * ach,
+                                     "peak": peak, "peak_source": src, "unit": "TFLOP/s",
+                                     "frac": 3 * ach / peak}}
+
+
+def run_precision(args):
+    """The precision workload: n = 500,000 points uniform in [0,1]^3, Matern-3/2 (ell 0.1)
+    + 1e-3 I, leaf 128, H^2 tol 1e-8, rank 100, one RHS N(0,1); a step is h2_build +
+    spdhss_build in the precision mode (FP32 sampling, tensor-core GEMMs) + ulv_factor +
+    FP64 PCG to relres 1e-6, inputs resident on the device.  Also once, outside the timed
+    steps, the FP64 construction of the same H^2 matrix for comparison."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07632_gb300 import api, inputs, native
+    c = dict(workload="precision_matern3d_n%d" % args.n_precision, n=args.n_precision, dim=3,
+             kernel="matern32", ell=0.1, shift=1e-3, leaf_size=128, h2_tol=1e-8, rank=100,
+             oversample=10, nrhs=1, relres=1e-6, maxit=3000, precision="fp32 sampling (3xTF32 "
+             "tensor-core GEMMs), fp64 compression / factors / PCG",
+             points="uniform [0,1]^3 seed 0", rhs="N(0,1) seed 1", l2="inputs larger than L2")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    pts = torch.from_numpy(inputs.uniform_cube(c["n"], 3, 0)).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(inputs.rhs(c["n"], 1, 1))).to(dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def step():
+        e0 = ev()
+        h = api.H2(pts, c["kernel"], c["ell"], c["shift"], c["leaf_size"], c["h2_tol"])
+        e1 = ev()
+        hs = api.HSS(h, c["rank"], c["oversample"], seed=7, precision=1)
+        e2 = ev()
+        u = api.ULV(hs)
+        e3 = ev()
+        x, it, rr = api.pcg_solve(h, u, b, tol=c["relres"], maxit=c["maxit"])
+        e4 = ev()
+        torch.cuda.synchronize()
+        parts = [e0.elapsed_time(e1), e1.elapsed_time(e2), e2.elapsed_time(e3), e3.elapsed_time(e4)]
+        u.close(); hs.close(); h.close()
+        return parts, int(it[0]), float(rr[0])
+
+    for _ in range(args.warmup):
+        step()
+    mon = ClockSampler(0)
+    parts_all, its = [], []
+    with mon:
+        torch.cuda.synchronize()
+        t0 = ev()
+        for _ in range(args.steps):
+            parts, it, rr = step()
+            parts_all.append(parts)
+            its.append(it)
+        t1 = ev()
+        torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    # the FP64 construction of the same matrix, once (context for the precision mode)
+    h = api.H2(pts, c["kernel"], c["ell"], c["shift"], c["leaf_size"], c["h2_tol"])
+    e0 = ev()
+    hs64 = api.HSS(h, c["rank"], c["oversample"], seed=7)
+    e1 = ev()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+
+    def timed(fn):
+        a = ev()
+        out = fn()
+        z = ev()
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(z)
+
+    prec = precision_build_record(api, native, torch, h, hs64, c, timed, c["n"])
+    hs64.close(); h.close()
+    ms = total / args.steps
+    mean = np.mean(np.array(parts_all), axis=0)
+    print(json.dumps({
+        "metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32/tf32", "data": "synthetic", "config": c,
+        "components_ms": {"h2_build": mean[0], "spdhss_build_precision": mean[1],
+                          "ulv_factor": mean[2], "pcg": mean[3]},
+        "pcg_iters": its, "pcg_relres": rr, "spdhss_build_fp64_ms": t64,
+        "precision_build": prec, "clocks": mon.summary()}))
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel family on
@@ -893,6 +1017,9 @@ def main():
         return
     if args.serve:
         run_serve(args.serve)
+        return
+    if args.precision:
+        run_precision(args)
         return
     if args.matvec_case:
         run_matvec_case(args.matvec_case, args.mixed)
