@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-at-scale", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: this many Poisson-arriving mixed requests, served one at "
                          "a time and then concurrently; prints a serving JSON line")
@@ -611,6 +613,7 @@ def run_gpu(args):
                 "share_of_step": st["ms"] / max(total_ms, 1e-9),
                 "launches_per_step": st["launches"] / args.steps}
     at_scale = None if args.no_at_scale else run_at_scale(api, native, torch, dev, stream, fp64_peak)
+    serving = None if args.no_serving or rank != 0 else serving_comparison(args.serve_requests)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(cfg, steps=3)
@@ -626,7 +629,7 @@ def run_gpu(args):
                                     "near_kernel_entries")},
         "hss": hinfo,
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-        "at_scale": at_scale,
+        "at_scale": at_scale, "serving": serving,
         "clocks": clk.summary(), "kernels": family_table(prof, fp64_peak),
     }
     print(json.dumps(line), flush=True)
@@ -663,27 +666,55 @@ def run_matvec_case(n, mixed=False):
     print(json.dumps(out))
 
 
+SERVE_WORKLOAD = "poisson200_n1000-16000_2d3d_exp-gauss-matern_rank50_rhs1-16"
+
+
+def serving_comparison(count, waves_only_stats=False):
+    """The serving workload (Poisson arrivals at 200 requests/s, seed 1; n log-uniform in
+    [1000, 16000]; 2D and 3D alternating; kernels cycled {exp, Gaussian ell=0.1, Matern-3/2
+    ell=0.1}; shift 1e-3; rank 50; 1..16 right-hand sides) served two ways on the same GPU:
+    plain FP64, one request at a time; and the served mixed-precision batched form (waves
+    of the requests admitted meanwhile, merged construction launches with the tensor-core
+    sampling, lockstep FP64 PCG, two waves overlapping).  Latency = arrival to last
+    solution on the host."""
+    import torch
+    from paper_2011_07632_gb300 import serve
+    reqs = serve.synthetic_stream(count, rate=200.0, n_lo=1000, n_hi=16000, seed=1)
+    warm = [serve.Request(**{**r.__dict__, "arrival": 0.0}) for r in reqs[:3]]
+    serve.Server(serve.GpuExecutor(1), slots=1).run(warm)
+    serve.Server(None).run_waves(warm, serve.WaveExecutor(1, precision=1), wave_slots=1)
+    free = torch.cuda.mem_get_info()[0]
+    one, st1 = serve.Server(serve.GpuExecutor(1), slots=1).run(reqs)
+    wav, stw = serve.Server(None, hbm_budget=int(0.6 * free)).run_waves(
+        reqs, serve.WaveExecutor(2, precision=1), wave_slots=2, max_wave=16)
+    diff = max(float(np.linalg.norm(xw - xo) / max(np.linalg.norm(xo), 1e-300))
+               for a, b in zip(one, wav) for xo, xw in zip(a.x, b.x))
+    keys = ("requests", "completed", "failed", "wall_s", "requests_per_s", "p50_latency_s",
+            "p99_latency_s", "max_inflight")
+    return {"workload": SERVE_WORKLOAD, "requests": count,
+            "fp64_one_at_a_time": {k: st1[k] for k in keys},
+            "mixed_batched_waves": {k: stw[k] for k in keys},
+            "speedup_requests_per_s": stw["requests_per_s"] / st1["requests_per_s"],
+            "p99_ratio": stw["p99_latency_s"] / st1["p99_latency_s"],
+            "max_rel_diff_mixed_vs_fp64_solutions": diff,
+            "pcg_iters_fp64": [int(np.max(r.iters[0])) for r in one if r.iters]}
+
+
 def run_serve(count):
-    """Poisson stream (200 req/s) of build+solve requests, n log-uniform in [1000, 16000], 2D
-    and 3D, kernels {exp, Gaussian ell=0.1, Matern-3/2 ell=0.1}, shift 1e-3, rank 50, 1..16
-    right-hand sides: one instance at a time versus 4 concurrent streams."""
+    """--serve N: the serving comparison over N requests, plus 4 concurrent single-request
+    streams (FP64) for context."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2011_07632_gb300 import serve
+    out = serving_comparison(count)
     reqs = serve.synthetic_stream(count, rate=200.0, n_lo=1000, n_hi=16000, seed=1)
-    serve.Server(serve.GpuExecutor(1), slots=1).run(reqs[:2])          # warm-up
     free = torch.cuda.mem_get_info()[0]
-    one, st1 = serve.Server(serve.GpuExecutor(1), slots=1).run(reqs)
-    mix, st4 = serve.Server(serve.GpuExecutor(4), slots=4, hbm_budget=int(0.6 * free)).run(reqs)
-    same = max(float(np.linalg.norm(xm - xo) / max(np.linalg.norm(xo), 1e-300))
-               for a, b in zip(one, mix) for xo, xm in zip(a.x, b.x))
-    iters = [int(np.max(r.iters[0])) for r in one if r.iters]
-    print(json.dumps({"metric": "served build+solve requests/s, p50/p99 latency",
-                      "workload": "poisson200_n1000-16000_mixed", "requests": count,
-                      "one_at_a_time": st1, "concurrent_4_streams": st4,
-                      "max_rel_diff_alone_vs_mix": same, "pcg_iters": iters,
-                      "dtype": "f64", "data": "synthetic"}))
+    _, st4 = serve.Server(serve.GpuExecutor(4), slots=4, hbm_budget=int(0.6 * free)).run(reqs)
+    out["fp64_concurrent_4_streams"] = st4
+    print(json.dumps({"metric": "served build+solve requests/s, p50/p99 latency", **out,
+                      "dtype": "f64 (+ fp32/tf32 sampling in the batched form)",
+                      "data": "synthetic"}))
 
 
 def batch_instances(count, seed=3):

@@ -286,10 +286,12 @@ spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, int64_t lda, 
  * All work runs on `stream`.  Arrays are HOST arrays of `count` entries.
  *
  * spdhss_build_batched: for instance i, h2_build(points[i], n[i], dim[i], kernel[i],
- *   leaf_size[i], tol[i]) -> spdhss_build(rank[i], oversample[i], omega[i], seed[i]) ->
+ *   leaf_size[i], tol[i]) -> spdhss_build_precision(rank[i], 0, oversample[i], omega[i],
+ *   seed[i], precision[i]) ->
  *   ulv_factor.  points[i]: n[i] x dim[i] column-major, HOST or DEVICE.  omega: NULL, or a
  *   HOST array of `count` entries, each NULL (the sketch drawn from seed[i]) or a DEVICE
- *   n[i] x (rank[i] + oversample[i]) column-major sketch as spdhss_build's.  Outputs: HOST
+ *   n[i] x (rank[i] + oversample[i]) column-major sketch as spdhss_build's.  precision: NULL
+ *   (all 0) or a HOST array of `count` modes as spdhss_build_precision's.  Outputs: HOST
  *   arrays of handles (NULL entry where that instance failed) and status[i] per instance
  *   (may be NULL).  Returns OK when every instance succeeded, else the first failing
  *   instance's status (spdhss_last_error names it).  The caller destroys the handles.
@@ -302,7 +304,8 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
                                    const int* oversample, const uint64_t* seed,
-                                   const double* const* omega, void* stream,
+                                   const double* const* omega, const int* precision,
+                                   void* stream,
                                    h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
                                    spdhss_status* status);
 spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,

@@ -243,7 +243,8 @@ def build_batched(instances, stream=None):
 
     instances: list of dicts with keys points ((n, dim) array or tensor), kernel, ell,
     shift, leaf_size, tol, rank, oversample (default 10), seed (default 0), omega (optional
-    (n, rank + oversample) sketch, else drawn on the device from seed).
+    (n, rank + oversample) sketch, else drawn on the device from seed), precision (0 FP64,
+    1 / 2 the sampling product on the tensor cores, as HSS(precision=...)).
     Returns (list of (H2, HSS, ULV) or None per instance, per-instance status codes,
     (merged launches, hand-overs))."""
     m = len(instances)
@@ -275,10 +276,11 @@ def build_batched(instances, stream=None):
         oms.append(om)
     keep.extend(o for o in oms if o is not None)
     omp = (ctypes.c_void_p * m)(*[o.data_ptr() if o is not None else None for o in oms])
+    prec = (ctypes.c_int * m)(*[int(i.get("precision", 0)) for i in instances])
     h2o, hso, ulo = (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)(), (ctypes.c_void_p * m)()
     st = (ctypes.c_int * m)()
     rc = N.lib().spdhss_build_batched(m, ptr, _i64(n), dim, kd, leaf, tol, rank, over, seed,
-                                      omp, _stream(stream), h2o, hso, ulo, st)
+                                      omp, prec, _stream(stream), h2o, hso, ulo, st)
     if rc != N.OK and all(v == N.OK for v in st):
         N.check(rc)
     out = []

@@ -622,7 +622,8 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
                                    const int* oversample, const uint64_t* seed,
-                                   const double* const* omega, void* stream,
+                                   const double* const* omega, const int* precision,
+                                   void* stream,
                                    h2_handle* h2_out, hss_handle* hss_out, ulv_handle* ulv_out,
                                    spdhss_status* status) {
   std::vector<spdhss_status> st;
@@ -644,8 +645,10 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
       std::unique_ptr<spdhss_h2_s> h =
           h2_build_one(points[i], n[i], dim[i], kernel[i], leaf_size[i], tol[i], s);
       std::unique_ptr<spdhss_hss_s> hs(new spdhss_hss_s());
+      const int prec = precision ? precision[i] : 0;
+      SPD_REQUIRE(prec >= 0 && prec <= 2, "precision must be 0, 1 or 2");
       spdhss_build_impl(hs.get(), h.get(), rank[i], oversample[i], omega ? omega[i] : nullptr,
-                        seed[i], s, 0.0);
+                        seed[i], s, 0.0, prec);
       std::unique_ptr<spdhss_ulv_s> u(new spdhss_ulv_s());
       ulv_factor_impl(u.get(), hs.get(), s);
       ulv_out[i] = u.release();

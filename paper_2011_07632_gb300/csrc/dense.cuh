@@ -65,7 +65,7 @@ struct GemmBatchT {
   // FP32 batches only: 0 CUDA cores; 1 tensor cores in TF32 (tcgen05, FP32 accumulation);
   // 2 tensor cores with split operands (3xTF32, FP32-accurate products)
   int tc = 0;
-  int tc_nt = 64;            // tile columns of the tensor-core kernel
+  int tc_nt = 0;             // tensor cores: tiles [0, tc_nt) are 128 x 64, the rest 128 x 128
   int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
   // launched problems: every problem in the orientation (C or C^T = B^T A^T) that wastes
   // the fewest padded FMAs, grouped by the kernel variant of its column count; one launch
@@ -89,12 +89,12 @@ struct GemmBatchT {
 using GemmBatch = GemmBatchT<double>;
 using SGemmBatch = GemmBatchT<float>;
 
-// Tensor-core grouped FP32 GEMM (tc_gemm.cu): 128 x nt tiles (nt 64 or 128) of the given
-// problems; split = 3xTF32.  A bounded wait that gives up sets the device error word,
+// Tensor-core grouped FP32 GEMM (tc_gemm.cu): 128 x 64 tiles for problems of at most 64
+// columns (the first n64 tiles), 128 x 128 for the others; split = 3xTF32.  A bounded wait that gives up sets the device error word,
 // which tc_check() reads (and clears), throwing SPDHSS_TIMEOUT.
-std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int* nt_out);
+std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int* n64_out);
 void tc_gemm_launch(const GemmProbT<float>* d_probs, const GemmSegT<float>* d_segs,
-                    const int4* d_tiles, int64_t ntiles, int nt, bool split, int* d_err,
+                    const int4* d_tiles, int64_t ntiles, int n64, bool split, int* d_err,
                     cudaStream_t s);
 int* tc_error_word();
 void tc_check(cudaStream_t s);

@@ -283,30 +283,34 @@ void tc_go(const GemmProbT<float>* pr, const GemmSegT<float>* sg, const int4* tl
 
 }  // namespace
 
-// Tiles of the tensor-core kernel: 128 x nt per tile (nt = 64 when every problem has at
-// most 64 columns, else 128).
-std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int* nt_out) {
-  int maxn = 1;
-  for (const auto& p : probs) maxn = std::max(maxn, p.N);
-  const int nt = maxn <= 64 ? 64 : 128;
+// Tiles of the tensor-core kernel: 128 x 64 for a problem of at most 64 columns, 128 x 128
+// otherwise (a choice of the problem alone, so that its arithmetic does not depend on the
+// other problems of the launch).  The 64-column tiles come first, *n64_out of them.
+std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int* n64_out) {
   std::vector<int4> tiles;
-  for (int p = 0; p < (int)probs.size(); ++p)
-    for (int m0 = 0; m0 < probs[p].M; m0 += TC_M)
-      for (int n0 = 0; n0 < probs[p].N; n0 += nt) tiles.push_back(make_int4(p, m0, n0, 0));
-  *nt_out = nt;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int p = 0; p < (int)probs.size(); ++p) {
+      const int nt = probs[p].N <= 64 ? 64 : 128;
+      if ((nt == 64) != (pass == 0)) continue;
+      for (int m0 = 0; m0 < probs[p].M; m0 += TC_M)
+        for (int n0 = 0; n0 < probs[p].N; n0 += nt) tiles.push_back(make_int4(p, m0, n0, 0));
+    }
+    if (pass == 0) *n64_out = (int)tiles.size();
+  }
   return tiles;
 }
 
 void tc_gemm_launch(const GemmProbT<float>* d_probs, const GemmSegT<float>* d_segs,
-                    const int4* d_tiles, int64_t ntiles, int nt, bool split, int* d_err,
+                    const int4* d_tiles, int64_t ntiles, int n64, bool split, int* d_err,
                     cudaStream_t s) {
   if (ntiles <= 0) return;
-  if (nt == 64) {
-    if (split) tc_go<64, true>(d_probs, d_segs, d_tiles, ntiles, d_err, s);
-    else tc_go<64, false>(d_probs, d_segs, d_tiles, ntiles, d_err, s);
-  } else {
-    if (split) tc_go<128, true>(d_probs, d_segs, d_tiles, ntiles, d_err, s);
-    else tc_go<128, false>(d_probs, d_segs, d_tiles, ntiles, d_err, s);
+  if (n64 > 0) {
+    if (split) tc_go<64, true>(d_probs, d_segs, d_tiles, n64, d_err, s);
+    else tc_go<64, false>(d_probs, d_segs, d_tiles, n64, d_err, s);
+  }
+  if (ntiles > n64) {
+    if (split) tc_go<128, true>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, s);
+    else tc_go<128, false>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, s);
   }
 }
 

@@ -62,7 +62,8 @@ _SIGS = {
     "spdhss_build_batched": [_I, ctypes.POINTER(_P), _PI64, ctypes.POINTER(_I),
                              ctypes.POINTER(KernelDesc), ctypes.POINTER(_I), ctypes.POINTER(_D),
                              ctypes.POINTER(_I), ctypes.POINTER(_I),
-                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_P), _P,
+                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_P),
+                             ctypes.POINTER(_I), _P,
                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                              ctypes.POINTER(_I)],
     "spdhss_gemm_f32": [_I, _I, _I, _P, _I64, _I, _P, _I64, _I, _P, _I64, ctypes.c_float,

@@ -1,5 +1,11 @@
 """Serving loop: continuous batching of build+solve requests on one GPU.
 
+Two forms share the admission policy.  Server.run gives every admitted request a worker
+slot and a CUDA stream of its own (one-request-at-a-time with one slot); Server.run_waves
+gathers the requests admitted while earlier waves are on the GPU into the next wave,
+served by the batched ABI (merged construction launches in the precision mode, lockstep
+PCG), with two waves overlapping on the device.
+
 Requests (points, kernel, shift, HSS rank, one or more blocks of right-hand sides) arrive
 over time.  A request is admitted as soon as its arrival time has passed, a worker slot is
 free and its estimated device footprint fits the HBM budget (first come, first served; a
@@ -151,9 +157,83 @@ class Server:
         for th in threads:
             th.join()
         wall = self.clock() - t0
+        return sorted(results, key=lambda r: r.rid), self._stats(reqs, results, wall)
+
+
+    def run_waves(self, requests: Sequence[Request], execute_wave: Callable,
+                  wave_slots: int = 2, max_wave: int = 16):
+        """Continuous batching in waves.  Admission is as in run() (arrival order, HBM
+        budget, first come first served); admitted requests queue, and each of
+        `wave_slots` wave workers takes every queued request (up to `max_wave`) as one wave
+        the moment it is free, so that requests arriving while waves are on the GPU join
+        the next wave and two waves overlap on the device.  `execute_wave(requests, slot)`
+        returns one (x blocks, iteration arrays, relres arrays) per request."""
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        t0 = self.clock()
+        cv = threading.Condition()
+        state = {"in_use": 0, "queue": [], "admitting": True, "busy": 0}
+        results: List[Result] = []
+
+        def wave_worker(slot: int):
+            while True:
+                with cv:
+                    while not state["queue"] and state["admitting"]:
+                        cv.wait()
+                    if not state["queue"]:
+                        return
+                    wave = state["queue"][:max_wave]
+                    del state["queue"][:len(wave)]
+                    state["busy"] += 1
+                outs, err = None, None
+                try:
+                    outs = execute_wave([w[0] for w in wave], slot)
+                except Exception as e:   # a failed wave frees its requests' memory
+                    err = f"{type(e).__name__}: {e}"
+                done = self.clock() - t0
+                with cv:
+                    for k, (req, fp, admitted) in enumerate(wave):
+                        xs, its, rrs = outs[k] if outs is not None else ([], [], [])
+                        results.append(Result(req.rid, xs, its, rrs, req.arrival, admitted, done,
+                                              fp, err))
+                        state["in_use"] -= fp
+                    state["busy"] -= 1
+                    self.trace.append((done, state["in_use"], len(wave)))
+                    cv.notify_all()
+
+        workers = [threading.Thread(target=wave_worker, args=(k,), daemon=True)
+                   for k in range(wave_slots)]
+        for w in workers:
+            w.start()
+        for req in reqs:
+            fp = int(self.footprint(req))
+            if self.hbm_budget is not None and fp > self.hbm_budget:
+                with cv:
+                    results.append(Result(req.rid, [], [], [], req.arrival, req.arrival,
+                                          req.arrival, fp, "rejected: footprint exceeds the HBM budget"))
+                continue
+            wait = req.arrival - (self.clock() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            with cv:
+                while not (self.hbm_budget is None or state["in_use"] + fp <= self.hbm_budget):
+                    cv.wait()
+                state["in_use"] += fp
+                admitted = self.clock() - t0
+                state["queue"].append((req, fp, admitted))
+                self.trace.append((admitted, state["in_use"], len(state["queue"])))
+                cv.notify_all()
+        with cv:
+            state["admitting"] = False
+            cv.notify_all()
+        for w in workers:
+            w.join()
+        wall = self.clock() - t0
+        return sorted(results, key=lambda r: r.rid), self._stats(reqs, results, wall)
+
+    def _stats(self, reqs, results, wall):
         ok = [r for r in results if r.error is None]
         lat = [r.latency for r in ok]
-        stats = {
+        return {
             "requests": len(reqs), "completed": len(ok), "failed": len(results) - len(ok),
             "wall_s": wall, "requests_per_s": len(ok) / wall if wall > 0 else float("nan"),
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
@@ -161,7 +241,6 @@ class Server:
             "max_inflight": max((t[2] for t in self.trace), default=0),
             "max_in_use_bytes": max((t[1] for t in self.trace), default=0),
         }
-        return sorted(results, key=lambda r: r.rid), stats
 
 
 class GpuExecutor:
@@ -194,6 +273,51 @@ class GpuExecutor:
             hs.close()
             h.close()
         return xs, its, rrs
+
+
+class WaveExecutor:
+    """Runs a wave of requests through the batched C ABI on one CUDA stream per wave slot:
+    spdhss_build_batched (H^2, SPD-HSS in the given precision mode, ULV, with the batched
+    kernel launches of all requests of the wave merged step by step), then
+    pcg_solve_batched for every block of right-hand sides (the iterations of all requests
+    in lockstep).  Every request's result equals the one it gets alone (a wave of one)."""
+
+    def __init__(self, slots: int, precision: int = 1):
+        import torch
+        self.torch = torch
+        self.precision = int(precision)
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+
+    def __call__(self, reqs: Sequence[Request], slot: int):
+        from . import api
+        torch = self.torch
+        s = self.streams[slot]
+        insts = [dict(points=np.ascontiguousarray(r.points, dtype=np.float64), kernel=r.kernel,
+                      ell=r.ell, shift=r.shift, leaf_size=r.leaf_size, tol=r.tol, rank=r.rank,
+                      oversample=r.oversample, seed=r.seed, precision=self.precision)
+                 for r in reqs]
+        outs = [([], [], []) for _ in reqs]
+        with torch.cuda.stream(s):
+            built, status, _ = api.build_batched(insts, stream=s)
+            bad = [k for k, v in enumerate(status) if v != 0]
+            if bad:
+                raise RuntimeError(f"requests {[reqs[k].rid for k in bad]} failed to build")
+            nblk = max(len(r.rhs) for r in reqs)
+            for j in range(nblk):
+                ks = [k for k, r in enumerate(reqs) if j < len(r.rhs)]
+                X, its, rrs, st = api.pcg_solve_batched(
+                    [built[k][0] for k in ks], [built[k][2] for k in ks],
+                    [np.asfortranarray(reqs[k].rhs[j]) for k in ks], tol=reqs[ks[0]].relres,
+                    maxit=reqs[ks[0]].maxit, stream=s)
+                for k, x, it, rr in zip(ks, X, its, rrs):
+                    outs[k][0].append(x.cpu().numpy())
+                    outs[k][1].append(it)
+                    outs[k][2].append(rr)
+            for h, hs, u in built:
+                u.close()
+                hs.close()
+                h.close()
+        return outs
 
 
 def synthetic_stream(count: int, rate: float, n_lo: int, n_hi: int, seed: int = 1,

@@ -92,3 +92,50 @@ def test_footprint_counts_unknowns():
     rpy = serve.Request(rid=1, arrival=0.0, points=X, kernel="rpy", leaf_size=64)
     assert scalar.unknowns == 5000 and rpy.unknowns == 15000
     assert serve.footprint_bytes(rpy) >= 3 * (serve.footprint_bytes(scalar) - (64 << 20))
+
+
+def test_waves_batch_arrivals_and_respect_the_budget():
+    """Requests admitted while waves run join later waves; at most `wave_slots` waves at a
+    time; memory in use never exceeds the budget; every request gets its own result."""
+    fp = lambda r: 100 + r.rid          # noqa: E731
+    budget = 1000
+    seen = {"waves": [], "live": 0, "max_live": 0}
+    lock = threading.Lock()
+
+    def execute_wave(reqs, slot):
+        with lock:
+            seen["waves"].append([r.rid for r in reqs])
+            seen["live"] += 1
+            seen["max_live"] = max(seen["max_live"], seen["live"])
+        time.sleep(0.02)
+        with lock:
+            seen["live"] -= 1
+        return [([np.full((r.n, 1), r.rid)], [np.array([1])], [np.array([0.0])]) for r in reqs]
+
+    srv = serve.Server(None, hbm_budget=budget, footprint=fp)
+    res, st = srv.run_waves(_reqs(30, gap=0.003), execute_wave, wave_slots=2, max_wave=6)
+    assert st["completed"] == 30 and st["failed"] == 0
+    assert seen["max_live"] <= 2
+    assert max(len(w) for w in seen["waves"]) <= 6
+    assert len(seen["waves"]) < 30            # arrivals were batched
+    assert sorted(sum(seen["waves"], [])) == list(range(30))
+    assert st["max_in_use_bytes"] <= budget
+    assert all(r.x[0][0, 0] == r.rid for r in res)
+    # first come, first served into waves
+    order = sum(seen["waves"], [])
+    assert order == sorted(order)
+
+
+def test_failed_wave_frees_its_memory():
+    calls = {"n": 0}
+
+    def execute_wave(reqs, slot):
+        calls["n"] += 1
+        if calls["n"] == 1:
+            raise RuntimeError("NOT_SPD: injected on the host")
+        return [([np.zeros((r.n, 1))], [np.array([1])], [np.array([0.0])]) for r in reqs]
+
+    srv = serve.Server(None, hbm_budget=10**12, footprint=lambda r: 10)
+    res, st = srv.run_waves(_reqs(8, gap=0.01), execute_wave, wave_slots=1, max_wave=4)
+    assert st["completed"] + st["failed"] == 8 and st["failed"] >= 1
+    assert all(r.error is None for r in res if r.rid >= 4)
