@@ -262,8 +262,9 @@ spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, dou
  * matrices (op = transpose when tA / tB is 1), through the library's grouped GEMM:
  * mode 0 on the CUDA cores (FP32 FMA), mode 1 on the tensor cores in TF32 (tcgen05.mma
  * kind::tf32, FP32 accumulation), mode 2 on the tensor cores with every operand split into
- * two TF32 parts (3xTF32: FP32-accurate products).  The FP32 H^2 products of the
- * precision mode use modes 1 and 2.  The paper has no counterpart: the operation is the
+ * two TF32 parts (3xTF32: FP32-accurate products); mode 3 is a test of the tensor-core
+ * kernel's bounded waits (it issues no MMA, its waits give up after about a second and the
+ * call returns TIMEOUT).  The FP32 H^2 products of the precision mode use modes 1 and 2.  The paper has no counterpart: the operation is the
  * dense GEMM the H^2 products consist of.  Synchronizes `stream`.  Errors: EINVAL,
  * TIMEOUT (a bounded wait in the tensor-core kernel gave up), ECUDA. */
 spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, int64_t lda, int tA,

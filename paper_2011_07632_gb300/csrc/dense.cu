@@ -490,7 +490,8 @@ void GemmBatchT<T>::launch(cudaStream_t s) const {
   ProfScope ps(tag, s, flops, bytes);
   if constexpr (sizeof(T) == 4) {
     if (tc) {
-      tc_gemm_launch(d_probs.p, d_segs.p, d_tiles.p, nt, tc_nt, tc == 2, tc_error_word(), s);
+      tc_gemm_launch(d_probs.p, d_segs.p, d_tiles.p, nt, tc_nt, tc == 2, tc_error_word(), s,
+                     tc_stall);
       return;
     }
   }

@@ -66,6 +66,7 @@ struct GemmBatchT {
   // 2 tensor cores with split operands (3xTF32, FP32-accurate products)
   int tc = 0;
   int tc_nt = 0;             // tensor cores: tiles [0, tc_nt) are 128 x 64, the rest 128 x 128
+  int tc_stall = 0;          // test of the bounded waits: issue nothing, let the waits expire
   int nb = 0;                        // 1/2/4: K-split kernel; 8/16/32: skinny kernel; 0: 64x64 tiles
   // launched problems: every problem in the orientation (C or C^T = B^T A^T) that wastes
   // the fewest padded FMAs, grouped by the kernel variant of its column count; one launch
@@ -95,7 +96,7 @@ using SGemmBatch = GemmBatchT<float>;
 std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int* n64_out);
 void tc_gemm_launch(const GemmProbT<float>* d_probs, const GemmSegT<float>* d_segs,
                     const int4* d_tiles, int64_t ntiles, int n64, bool split, int* d_err,
-                    cudaStream_t s);
+                    cudaStream_t s, int stall = 0);
 int* tc_error_word();
 void tc_check(cudaStream_t s);
 

@@ -31,7 +31,7 @@ namespace {
 constexpr int TC_M = 128;     // tile rows (TMEM lanes)
 constexpr int TC_KC = 32;     // K elements per stage
 constexpr int TC_KS = 8;      // K per MMA instruction (32 bytes of TF32)
-constexpr uint32_t kTcWaitTries = 1u << 22;
+constexpr long long kTcWaitCycles = 1LL << 31;   // about one second at the SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -71,10 +71,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// true once the phase with the given parity has completed; false after the try limit
+// true once the phase with the given parity has completed; false after about a second
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kTcWaitTries; ++it) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < kTcWaitCycles) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -124,7 +125,7 @@ template <int NT, bool SPLIT>
 __global__ void __launch_bounds__(128) k_gemm_tf32(const GemmProbT<float>* __restrict__ probs,
                                                    const GemmSegT<float>* __restrict__ segs,
                                                    const int4* __restrict__ tiles,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err, int stall) {
   constexpr int NOP = SPLIT ? 2 : 1;                        // hi (, lo) per operand
   constexpr int SA = stage_bytes(TC_M), SB = stage_bytes(NT);
   constexpr int STAGE = NOP * (SA + SB);
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(const GemmProbT<float>* __res
       // the staged chunk, visible to the tensor cores
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0 && !stall) {   // stall (test of the bounded waits): nothing is issued
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = sbase + st * STAGE, b0 = a0 + NOP * SA;
 #pragma unroll
@@ -267,7 +268,7 @@ constexpr int tc_smem_bytes() {
 
 template <int NT, bool SPLIT>
 void tc_go(const GemmProbT<float>* pr, const GemmSegT<float>* sg, const int4* tl, int64_t nt,
-           int* err, cudaStream_t s) {
+           int* err, int stall, cudaStream_t s) {
   constexpr int smem = tc_smem_bytes<NT, SPLIT>();
   static std::once_flag once;
   std::call_once(once, [] {
@@ -276,7 +277,7 @@ void tc_go(const GemmProbT<float>* pr, const GemmSegT<float>* sg, const int4* tl
   });
   for (int64_t b0 = 0; b0 < nt; b0 += 2147483647LL) {
     const unsigned g = (unsigned)std::min<int64_t>(nt - b0, 2147483647LL);
-    k_gemm_tf32<NT, SPLIT><<<g, 128, smem, s>>>(pr, sg, tl + b0, err);
+    k_gemm_tf32<NT, SPLIT><<<g, 128, smem, s>>>(pr, sg, tl + b0, err, stall);
     SPD_LAUNCHED();
   }
 }
@@ -302,15 +303,15 @@ std::vector<int4> tc_gemm_tiles(const std::vector<GemmProbT<float>>& probs, int*
 
 void tc_gemm_launch(const GemmProbT<float>* d_probs, const GemmSegT<float>* d_segs,
                     const int4* d_tiles, int64_t ntiles, int n64, bool split, int* d_err,
-                    cudaStream_t s) {
+                    cudaStream_t s, int stall) {
   if (ntiles <= 0) return;
   if (n64 > 0) {
-    if (split) tc_go<64, true>(d_probs, d_segs, d_tiles, n64, d_err, s);
-    else tc_go<64, false>(d_probs, d_segs, d_tiles, n64, d_err, s);
+    if (split) tc_go<64, true>(d_probs, d_segs, d_tiles, n64, d_err, stall, s);
+    else tc_go<64, false>(d_probs, d_segs, d_tiles, n64, d_err, stall, s);
   }
   if (ntiles > n64) {
-    if (split) tc_go<128, true>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, s);
-    else tc_go<128, false>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, s);
+    if (split) tc_go<128, true>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, stall, s);
+    else tc_go<128, false>(d_probs, d_segs, d_tiles + n64, ntiles - n64, d_err, stall, s);
   }
 }
 
@@ -349,13 +350,14 @@ extern "C" spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, in
   try {
     SPD_REQUIRE(M >= 1 && N >= 1 && K >= 0, "spdhss_gemm_f32: bad sizes");
     SPD_REQUIRE(C && (K == 0 || (A && B)), "spdhss_gemm_f32: NULL argument");
-    SPD_REQUIRE(mode >= 0 && mode <= 2, "spdhss_gemm_f32: mode must be 0, 1 or 2");
+    SPD_REQUIRE(mode >= 0 && mode <= 3, "spdhss_gemm_f32: mode must be 0, 1, 2 or 3");
     SPD_REQUIRE(ldc >= M && lda >= (tA ? K : M) && ldb >= (tB ? N : K),
                 "spdhss_gemm_f32: leading dimension too small");
     cudaStream_t s = (cudaStream_t)stream;
     spd::StreamScope ss(s);
     spd::GemmBatchT<float> g;
-    g.tc = mode;
+    g.tc = mode == 3 ? 2 : mode;
+    g.tc_stall = mode == 3;
     g.tag = "gemm_f32";
     g.prob(C, ldc, M, N, alpha, beta);
     if (K > 0) g.seg(A, lda, tA, B, ldb, tB, K);

@@ -55,3 +55,23 @@ def test_tensor_core_gemm(M, N, K, tA, tB, mode):
     assert err < TOL[mode], err
     err = _run(torch, native, M, N, K, tA, tB, mode, -0.5, 2.0, M + N + 3 * K)
     assert err < TOL[mode], err
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable():
+    """Mode 3 issues no MMA, so the kernel's mbarrier waits cannot complete: each gives up
+    after about a second, the kernel records the failure, frees its tensor memory and
+    returns, and the call reports TIMEOUT.  The next product on the same context is right."""
+    need_gpu()
+    import torch
+    from paper_2011_07632_gb300 import native
+    A = torch.ones((64, 64), dtype=torch.float32, device="cuda")
+    C = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    st = native.lib().spdhss_gemm_f32(64, 64, 64, ctypes.c_void_p(A.data_ptr()), 64, 0,
+                                      ctypes.c_void_p(A.data_ptr()), 64, 0,
+                                      ctypes.c_void_p(C.data_ptr()), 64, ctypes.c_float(1.0),
+                                      ctypes.c_float(0.0), 3,
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == native.TIMEOUT
+    assert b"gave up" in native.lib().spdhss_last_error()
+    err = _run(torch, native, 100, 60, 77, 0, 0, 2, 1.0, 0.0, 5)
+    assert err < TOL[2]
