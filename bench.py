@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import tempfile
@@ -68,6 +69,8 @@ def parse():
                     help="the paper's RPY iteration runs at these particle counts")
     ap.add_argument("--rank-sweep", action="store_true",
                     help="fixed ranks 100 and 200 on the paper's Matern ball/sphere workload")
+    ap.add_argument("--sweep-kernel", default="matern32", choices=["matern32", "gauss", "imq"],
+                    help="kernel of --kernel-sweep")
     ap.add_argument("--kernel-sweep", action="store_true",
                     help="block Jacobi and SPD-HSS r=100 over the Matern parameter l on the "
                          "paper's 320,000-point ball")
@@ -238,6 +241,21 @@ def roof_hbm(st):
             "tflops": st["flops"] / (st["ms"] / 1e3) / 1e12}
 
 
+def roof_product_f32(info, c, ms):
+    """HBM roofline of the whole FP32 H^2 product (the public call, permutations and
+    conversions included) on its algorithmic bytes: the FP32 generators (bases and every
+    coupling once), x and y in FP32, and the coordinates the near field is evaluated from."""
+    peak = 6801.7
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    nbytes = info["stored_bytes"] / 2 + 4 * 2 * c["n"] * c["nrhs"] + 8 * 3 * c["n"]
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "bytes": nbytes, "ms": ms, "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak}
+
+
 def run_at_scale(api, native, torch, dev, stream, fp64_peak):
     """Components of the n = 200,000 Gaussian workload, each timed with CUDA events."""
     from paper_2011_07632_gb300 import inputs
@@ -312,6 +330,7 @@ def run_at_scale(api, native, torch, dev, stream, fp64_peak):
             "pcg_ms_per_iteration": t_pcg32 / max(int(it2.max()), 1),
             "pcg_relres_after_probe": float(rr2.max()),
             "roofline_h2_coupling_f32": roof_hbm(prof32.get("h2_coupling_f32")),
+            "roofline_h2_product_f32": roof_product_f32(info, c, t_mv32 / reps),
             "kernels": {k2: round(v["ms"] / reps, 3) for k2, v in prof32.items()},
         },
         "precision_build": prec,
@@ -899,11 +918,17 @@ def run_rpy_sweep(sizes):
                       "dtype": "f64", "data": "synthetic"}))
 
 
-def run_kernel_sweep():
-    """The paper's parameter sweep: Matern-3/2 kernel matrices sigma I + K_l on 320,000
-    points in a ball (constant density), l from 0.001 to 1 (length scale 1/l), sigma 1e-2,
-    leaf boxes of up to 400 points; block Jacobi (rank 0) and SPD-HSS with r = 100; PCG to
-    relres 1e-4 with a right-hand side uniform on [-0.5, 0.5]."""
+SWEEP_L = {"matern32": (0.001, 0.01, 0.1, 1.0),
+           "gauss": (0.0001, 0.001, 0.01, 0.1, 1.0),
+           "imq": (0.001, 0.01, 0.1, 1.0, 10.0, 100.0)}
+
+
+def run_kernel_sweep(kind="matern32"):
+    """The paper's parameter sweep: kernel matrices sigma I + K_l on 320,000 points in a
+    ball (constant density), sigma 1e-2, leaf boxes of up to 400 points; block Jacobi
+    (rank 0) and SPD-HSS with r = 100; PCG to relres 1e-4 with a right-hand side uniform on
+    [-0.5, 0.5].  The paper's l multiplies the distance (Matern-3/2: length scale 1/l) or
+    the squared distance (Gaussian, IMQ: length scale 1/sqrt(l))."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -912,8 +937,9 @@ def run_kernel_sweep():
     pts = torch.from_numpy(inputs.ball(n, 0)).cuda()
     b = torch.from_numpy(np.ascontiguousarray(inputs.rhs_uniform(n, 1, 1))).cuda()
     rows = []
-    for l in (0.001, 0.01, 0.1, 1.0):
-        h = api.H2(pts, "matern32", 1.0 / l, 1e-2, 400, 1e-8)
+    for l in SWEEP_L[kind]:
+        ell = 1.0 / l if kind == "matern32" else 1.0 / math.sqrt(l)
+        h = api.H2(pts, kind, ell, 1e-2, 400, 1e-8)
         for r in (0, 100):
             hs = api.HSS(h, r, 10, seed=2)
             u = api.ULV(hs)
@@ -922,9 +948,9 @@ def run_kernel_sweep():
             u.close(); hs.close()
         h.close()
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "PCG iterations over the Matern length scale",
-                      "workload": "matern32_ball_n320k_l0.001-1", "rows": rows,
-                      "dtype": "f64", "data": "synthetic"}))
+    print(json.dumps({"metric": f"PCG iterations over the {kind} kernel parameter",
+                      "workload": f"{kind}_ball_n320k_l{SWEEP_L[kind][0]}-{SWEEP_L[kind][-1]}",
+                      "rows": rows, "dtype": "f64", "data": "synthetic"}))
 
 
 def run_paper_table():
@@ -1038,7 +1064,7 @@ def main():
         run_rank_sweep()
         return
     if args.kernel_sweep:
-        run_kernel_sweep()
+        run_kernel_sweep(args.sweep_kernel)
         return
     if args.paper_table:
         run_paper_table()

@@ -458,7 +458,8 @@ static bool near_store(spdhss_h2_s* h, cudaStream_t s) {
 
 template <class F>
 static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int nslot,
-                            const F* Ub, const F* Cb, cudaStream_t s, int tc = 0) {
+                            const F* Ub, const F* Cb, cudaStream_t s, int tc = 0,
+                            bool basis = true) {
   const TreeHost& T = h->th;
   const int64_t n = T.n, K = std::max<int64_t>(h->Ktot, 1);
   const int D = T.D;
@@ -472,12 +473,12 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   auto U = [&](int64_t i) { return Ub + h->U_off[i]; };
   // upward
   p.up_leaf = GemmBatchT<F>();
-  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i)
+  for (int64_t i = T.depth_off[D]; basis && i < T.depth_off[D + 1]; ++i)
     if (h->rank(i) > 0)
       p.up_leaf.add(p.xhat.p + h->skel_off[i], K, h->rank(i), ncol, U(i), h->U_rows[i], 1,
                     p.xs.p + T.begin[i], n, 0, h->U_rows[i], 1.0, 0.0);
   p.up.clear();
-  for (int t = D - 1; t >= 1; --t) {
+  for (int t = D - 1; basis && t >= 1; --t) {
     p.up.emplace_back();
     GemmBatchT<F>& g = p.up.back();
     for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i)
@@ -510,7 +511,7 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   }
   // downward
   p.down.clear();
-  for (int t = 1; t <= D - 1; ++t) {
+  for (int t = 1; basis && t <= D - 1; ++t) {
     p.down.emplace_back();
     GemmBatchT<F>& g = p.down.back();
     for (int64_t i = T.depth_off[t]; i < T.depth_off[t + 1]; ++i) {
@@ -525,7 +526,7 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   }
   // leaves
   p.leaf_out = GemmBatchT<F>();
-  for (int64_t i = T.depth_off[D]; i < T.depth_off[D + 1]; ++i) {
+  for (int64_t i = T.depth_off[D]; basis && i < T.depth_off[D + 1]; ++i) {
     p.leaf_out.prob(p.ys.p + T.begin[i], n, (int)T.size(i), W, 1.0, 0.0);
     if (h->rank(i) > 0)
       p.leaf_out.seg(U(i), h->U_rows[i], 0, p.yhat.p + h->skel_off[i], K, 0, h->rank(i));
@@ -1088,24 +1089,21 @@ void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, c
 }
 
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
-  // each FP32 copy on its own first use (the precision-mode sampling makes the bases and
-  // the source-major couplings, the products here the destination-major couplings)
-  if (h->basis_f.n == 0) {
-    h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
-    convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
-  }
-  // the destination-major FP32 couplings (each pair twice: the bytes of the FP64
-  // couplings) when they fit; else each plan converts the couplings once (half those
-  // bytes) and runs the grouped GEMM over them
+  // up to 16 columns: the once-read product over the padded FP32 layout (made on first use,
+  // about half the bytes of the FP64 generators); else, or when the layout does not fit,
+  // each plan converts the couplings once and runs the grouped GEMMs over them
   auto it = h->plans_f.find(ncol);
   if (it == h->plans_f.end()) {
-    const bool dm = h->coup_fd.n > 0 || fits_on_device(h->coup.bytes(), s);
-    if (dm && h->coup_fd.n == 0) coup_dm_build<float>(h, h->coup_fd, s);
     std::unique_ptr<H2PlanF> p(new H2PlanF());
-    if (dm) {
-      h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, nullptr, s);
-      rowcoup_plan<float>(h, *p, ncol, h->coup_fd.p, s);
+    if (ncol <= 16 && sym_layout_fits(h, s)) {
+      sym_layout(h, s);
+      h2_plan_build_t<float>(h, *p, ncol, 1, nullptr, nullptr, s, 0, false);
+      sym_plan_build(h, *p, ncol, s);
     } else {
+      if (h->basis_f.n == 0) {
+        h->basis_f.alloc(std::max<size_t>(h->basis.n, 1));
+        convert_d2f(h->basis.p, h->basis_f.p, (int64_t)h->basis.n, s);
+      }
       p->coup_src.alloc(std::max<size_t>(h->coup.n, 1));
       if (h->coup.n) convert_d2f(h->coup.p, p->coup_src.p, (int64_t)h->coup.n, s);
       h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, p->coup_src.p, s);
@@ -1118,6 +1116,11 @@ H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
 
 template <class T>
 static void h2_plan_run_t(const spdhss_h2_s* h, const H2PlanT<T>& p, cudaStream_t s) {
+  if (p.sym) {
+    sym_plan_run(*p.sym, s);
+    p.near.launch(h->kfn, h->td.xs.p, h->th.n, h->th.dim, s);
+    return;
+  }
   p.up_leaf.launch(s);
   for (const auto& g : p.up) g.launch(s);
   if constexpr (std::is_same<T, double>::value) copy_vec(p.yhat.p, nullptr, (int64_t)p.yhat.n, s);

@@ -67,6 +67,76 @@ struct RowCoupBatchT {
   void launch(cudaStream_t s) const;
 };
 
+// The FP32 product that reads every stored generator once (couplings once per unordered
+// pair, both directions from the same tile).  Skeleton-space vectors (x^, y^, per-pair
+// pieces, partial tiles) are row-interleaved: entry (row r, right-hand side c) at
+// [r * nc + c], nc = the launch width (1, 2, 4, 8 or 16), right-hand sides >= ncol zero.
+// A job is rows [r0, r0 + R) (R <= 512, r0 % 4 == 0) and columns [c0, c1) of an FP32
+// column-major matrix A whose leading dimension is a multiple of 4 (zero rows below the
+// matrix) on a 16-byte boundary:
+//   direction 1 (y1 != null): y1[r * y1rs + c * y1cs] (mode1: += / =)
+//                             sum_col A[r0 + r, col] x1[idx(col) * nc + c],
+//                             idx(col) = cmap ? cmap[col] : col  (x1 row-interleaved);
+//   direction 2 (z != null):  z[(col - c0) * zcs + c * zrs] (mode2)
+//                             sum_r A[r0 + r, col] x2[r * x2rs + c * x2cs].
+struct SymJob {
+  const float* A;
+  int64_t lda;
+  int r0, R, c0, c1;
+  int S;                       // columns per pipeline stage (chosen from R and the width)
+  int ncol;                    // right-hand sides (<= the launch width)
+  float* y1;
+  int64_t y1rs, y1cs;
+  int mode1;
+  const float* x1;
+  const int* cmap;
+  float* z;
+  int64_t zcs, zrs;
+  int mode2;
+  const float* x2;
+  int64_t x2rs, x2cs;
+};
+// y (rows x ncol, row-interleaved with stride nc) (mode: += / =) the sum of the
+// row-interleaved sources [s0, s1) (same stride) in that order
+struct SymSrc {
+  const float* p;
+};
+struct SymSum {
+  float* y;
+  int rows, ncol, nc, mode, s0, s1;
+};
+struct SymBatch {
+  std::vector<SymJob> jobs;
+  DevBuf<SymJob> d_jobs;
+  int nc = 8, ncol = 1;
+  const char* tag = "h2_coupling_f32";
+  double flops = 0.0, bytes = 0.0;
+  void upload(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+};
+struct SymSumBatch {
+  std::vector<SymSum> jobs;
+  std::vector<SymSrc> srcs;
+  DevBuf<SymSum> d_jobs;
+  DevBuf<SymSrc> d_srcs;
+  int ncol = 1;
+  const char* tag = "h2_coupling_f32";
+  double bytes = 0.0;
+  void upload(cudaStream_t s);
+  void launch(cudaStream_t s) const;
+};
+struct PlanStep {
+  std::unique_ptr<SymBatch> sym;
+  std::unique_ptr<SymSumBatch> sum;
+};
+// upward levels (each with its partial sums), couplings, their sums, downward levels
+struct SymPlan {
+  int nc = 0;
+  std::vector<PlanStep> steps;
+  DevBuf<float> xh, yh;  // x^ and y^ (K x nc, row-interleaved)
+  DevBuf<float> part;    // partial tiles and the per-pair pieces of the couplings
+};
+
 // One H^2 product plan for a fixed number of columns: upward pass, Type-3 couplings,
 // downward pass, leaf bases and near field.  With nslot > 1 the product is split by the
 // HSS level of the lowest common ancestor of every block (slot l - 2 for level l), which
@@ -90,6 +160,7 @@ struct H2PlanT {
   RowCoupBatchT<T> near_r;  // ... streamed row by row for at most 4 columns
   bool near_stored = false, near_rows = false;
   DevBuf<T> coup_src;       // couplings in this plan's type when it owns a copy of them
+  std::shared_ptr<SymPlan> sym;   // FP32: the once-read product (replaces the GEMM steps)
 };
 using H2Plan = H2PlanT<double>;
 using H2PlanF = H2PlanT<float>;
@@ -124,12 +195,18 @@ struct spdhss_h2_s {
   int near_state = 0;   // 0: not decided, 1: stored, 2: evaluated on the fly
   // FP32 copies of the generators for the mixed-precision products (made on first use)
   spd::DevBuf<float> basis_f;
-  // destination-major couplings (made on first use): FP32 and FP64 copies, and per node the
-  // offset of its coupling matrix in them
-  spd::DevBuf<float> coup_fd;
+  // destination-major FP64 couplings (made on first use for products of at most 4
+  // columns), and per node the offset of its coupling matrix in them
   spd::DevBuf<double> coup_dd;
   std::vector<int64_t> coup_dm_off;
   std::map<int, std::unique_ptr<spd::H2PlanF>> plans_f;
+  // the FP32 once-read layout (made on first FP32 product): padded copies of the bases
+  // (offset per node) and of every owner's coupling region M_i = [B_ij ...] over its
+  // partners j > i (offset and columns per node), the x^ row of every region column, and
+  // per far-list entry the first column of its pair's block in the owner's region
+  spd::DevBuf<float> sym_f;
+  std::vector<int64_t> sym_U_off, sym_M_off, sym_Kc, sym_cmap_off, sym_colstart;
+  spd::DevBuf<int> sym_cmap;
 
   int rank(int64_t i) const { return (int)(skel_off[i + 1] - skel_off[i]); }
 };
@@ -146,6 +223,11 @@ H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s);
 // (tc = 1 TF32, 2 3xTF32), near field in FP32 on the fly
 void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, cudaStream_t s);
 void h2_plan_run(const spdhss_h2_s* h, const H2PlanF& p, cudaStream_t s);
+// the once-read FP32 layout of the handle: whether it fits, building it, a plan's steps
+bool sym_layout_fits(const spdhss_h2_s* h, cudaStream_t s);
+void sym_layout(spdhss_h2_s* h, cudaStream_t s);
+void sym_plan_build(const spdhss_h2_s* h, H2PlanF& p, int ncol, cudaStream_t s);
+void sym_plan_run(const SymPlan& P, cudaStream_t s);
 // element-wise conversions of n x ncol column-major blocks between FP64 and FP32
 void convert_d2f(const double* x, float* y, int64_t count, cudaStream_t s);
 void convert_f2d(const float* x, double* y, int64_t count, cudaStream_t s);

@@ -43,22 +43,22 @@ def test_mixed_pcg_reaches_fp64_tolerance(nrhs):
     assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0) <= 1.01e-6)
 
 
-@pytest.mark.parametrize("nrhs", [3, 8, 16])
-def test_fp32_product_split_rows(nrhs):
-    """A size where high-rank nodes carry row tiles of more than 2^20 coupling entries (the
-    FP32 coupling step then splits them over several CTAs and adds the parts in order)."""
+@pytest.mark.parametrize("nrhs,row_block", [(3, None), (8, None), (16, None), (8, "128"),
+                                            (13, "256")])
+def test_fp32_product_split_rows(nrhs, row_block, monkeypatch):
+    """High-rank nodes (ranks and transfer-matrix heights above the 128-512 rows of one
+    job): the FP32 product then splits their rows over several jobs and adds the partial
+    results in a fixed order.  SPDHSS_SYM_ROW_BLOCK lowers the rows per job so that every
+    level takes the split path."""
     api = need_gpu()
+    if row_block:
+        monkeypatch.setenv("SPDHSS_SYM_ROW_BLOCK", row_block)
     n = 60000
     X = inputs.uniform_cube(n, 3, 11)
     h = api.H2(X, "gauss", 0.1, 1e-4, 128, 1e-8)
-    tr = h.export_tree()
     off, _ = h.export_skeletons()
     k = np.diff(off)
-    big = 0
-    for i in range(len(k)):
-        kt = sum(int(k[j]) for j in tr["far_idx"][tr["far_off"][i]:tr["far_off"][i + 1]])
-        big = max(big, min(int(k[i]), 256) * kt)
-    assert big > (1 << 20)
+    assert k.max() > int(row_block or 512) // 2
     x = inputs.rhs(n, nrhs, 12)
     y64 = h.matmul(x).cpu().numpy()
     y32 = h.matmul_mixed(x).cpu().numpy()
@@ -66,6 +66,19 @@ def test_fp32_product_split_rows(nrhs):
     assert rel(y32, y64) < 1e-4
     # deterministic: a second product is bit-identical
     assert np.array_equal(h.matmul_mixed(x).cpu().numpy(), y32)
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (65, 2), (700, 5), (700, 9), (2500, 16)])
+def test_fp32_product_small_and_ragged(n, nrhs):
+    """Single points, a single leaf, ragged leaves and right-hand-side counts between the
+    kernel's column widths (1, 2, 4, 8, 16) against the exact kernel matrix."""
+    api = need_gpu()
+    X = inputs.uniform_cube(n, 3, 21)
+    h = api.H2(X, "exp", 0.5, 1e-2, 64, 1e-8)
+    x = inputs.rhs(n, nrhs, 22)
+    y32 = h.matmul_mixed(x).cpu().numpy()
+    A = OK.dense_matrix(OK.NAMES["exp"], 0.5, 1e-2, X)
+    assert rel(y32, A @ x) < 2e-5
 
 
 # ---- precision mode of the construction (spdhss_build_precision) ------------------------
