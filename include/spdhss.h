@@ -89,6 +89,17 @@ typedef struct spdhss_ulv_s* ulv_handle;
 spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_desc kernel,
                        int leaf_size, double tol, void* stream, h2_handle* out);
 
+/* Values of a scalar kernel function of Sec. 6 (EXP, GAUSS, MATERN32, IMQ; not RPY) at n
+ * squared distances, computed on the device by the same code that fills every kernel
+ * tile, proxy matrix and near-field block of the path (the diagonal shift is not added):
+ *   out[i] = K(sqrt(r2[i])) with the descriptor's length scale.
+ *   r2, out  DEVICE arrays of n doubles (n >= 0) that do not overlap.
+ * The exponential of the EXP, GAUSS and MATERN32 kernels is a table-driven method (Tang
+ * 1989, 64 entries): within two units in the last place of the exact value.
+ * Errors: EINVAL for the RPY kind, a length scale <= 0, host pointers; ECUDA. */
+spdhss_status spdhss_kernel_eval(spdhss_kernel_desc kernel, const double* r2, double* out,
+                                 int64_t n, void* stream);
+
 /* Y = A X with the H^2 matrix A (Sec. 5.1): upward pass, Type-3 couplings, downward pass,
  * and near-field kernel tiles evaluated on the fly (shift included).
  *   X, Y  device, n x nrhs column-major, leading dimension ld >= n, original point order.

@@ -203,6 +203,16 @@ class ULV:
             pass
 
 
+def kernel_eval(kernel: str, ell: float, r2, stream=None) -> torch.Tensor:
+    """K(r) at squared distances r2 (FP64, any shape), evaluated on the device the way the
+    H^2 and SPD-HSS kernels evaluate it (scalar kernels only, no shift)."""
+    r2 = torch.as_tensor(r2, dtype=torch.float64).cuda().contiguous()
+    out = torch.empty_like(r2)
+    N.check(N.lib().spdhss_kernel_eval(N.KernelDesc(N.KERNELS[kernel], float(ell), 0.0),
+                                       _ptr(r2), _ptr(out), r2.numel(), _stream(stream)))
+    return out
+
+
 def pcg_solve(h2: H2, ulv: ULV, B, tol: float = 1e-6, maxit: int = 3000, stream=None,
               raise_on_no_convergence: bool = False, mixed: bool = False):
     """PCG (Sec. 6.2): returns (X (n, nrhs), iterations per column, true relres per column).

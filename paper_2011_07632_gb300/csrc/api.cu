@@ -277,6 +277,23 @@ spdhss_status h2_build(const double* points, int64_t n, int dim, spdhss_kernel_d
   });
 }
 
+spdhss_status spdhss_kernel_eval(spdhss_kernel_desc kernel, const double* r2, double* out,
+                                int64_t n, void* stream) {
+  return guarded("spdhss_kernel_eval", [&] {
+    SPD_REQUIRE(n >= 0, "n must be >= 0");
+    SPD_REQUIRE(n == 0 || (r2 && out), "NULL argument");
+    SPD_REQUIRE(kernel.kind >= 0 && kernel.kind <= 3, "scalar kernel kind expected");
+    SPD_REQUIRE(kernel.ell > 0.0, "kernel length scale must be > 0");
+    SPD_REQUIRE(n == 0 || (is_device_pointer(r2) && is_device_pointer(out)),
+                "r2 and out must be device pointers");
+    KernelFn k;
+    k.kind = kernel.kind;
+    k.inv_ell = 1.0 / kernel.ell;
+    k.shift = 0.0;
+    kernel_eval_launch(k, r2, out, n, (cudaStream_t)stream);
+  });
+}
+
 spdhss_status h2_matmul(h2_handle h, const double* X, double* Y, int nrhs, int64_t ld,
                         void* stream) {
   return guarded("h2_matmul", [&] {

@@ -152,15 +152,69 @@ struct KernelFn {
   double shift;
 };
 
+// exp(x) for x <= 0 by Tang's table-driven method (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point arithmetic", ACM TOMS
+// 15(2), 1989), here with 64 table entries: x = (64 m + j) ln2/64 + r with |r| <= ln2/128,
+// exp(x) = 2^m 2^(j/64) e^r, and e^r - 1 by its Taylor series through r^5 (the first
+// omitted term is below 0.16 units in the last place).  ln2/64 is split into a 29-bit head,
+// whose product with the integer 64 m + j is exact, and a tail; 2^m is applied to the
+// exponent field (the result stays normal for x >= -700).  Arguments below -700 (and NaN)
+// take exp().  Each table entry is 2^(j/64) rounded to the nearest double.
+// EXP2_TABLE_BEGIN
+__device__ const double kExp2By64[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0,
+    0x1.0874518759bc8p+0, 0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0,
+    0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0, 0x1.172b83c7d517bp+0,
+    0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0,
+    0x1.2d285a6e4030bp+0, 0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0,
+    0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0, 0x1.3dea64c123422p+0,
+    0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0,
+    0x1.56f4736b527dap+0, 0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0,
+    0x1.6247eb03a5585p+0, 0x1.6623882552225p+0, 0x1.6a09e667f3bcdp+0,
+    0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0,
+    0x1.868d99b4492edp+0, 0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0, 0x1.9c49182a3f090p+0,
+    0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0,
+    0x1.bcc1e904bc1d2p+0, 0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0,
+    0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0, 0x1.d5818dcfba487p+0,
+    0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0,
+    0x1.fa7c1819e90d8p+0,
+};
+// EXP2_TABLE_END
+__device__ __forceinline__ double exp_neg(double x) {
+  if (!(x >= -700.0)) return exp(x);
+  const double kInvStep = 0x1.71547652b82fep+6;    // 64 / ln2
+  const double kStepHi = 0x1.62e42ff000000p-7;     // ln2/64, head
+  const double kStepLo = -0x1.718432a1b0e26p-41;   // ln2/64 - head
+  const double kShift = 0x1.8p52;                  // round-to-integer shifter
+  const double t = fma(x, kInvStep, kShift);       // 64 m + j in the low word
+  const int N = __double2loint(t);
+  const double Nd = t - kShift;
+  double r = fma(-Nd, kStepHi, x);
+  r = fma(-Nd, kStepLo, r);
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r * r, r);                            // e^r - 1
+  const double T = __ldg(kExp2By64 + (N & 63));
+  const double v = fma(T, p, T);
+  return __hiloint2double(__double2hiint(v) + (N >> 6) * (1 << 20), __double2loint(v));
+}
+
 __device__ __forceinline__ double kernel_r2(const KernelFn& k, double r2) {
   switch (k.kind) {
     case SPDHSS_K_EXP:
-      return exp(-sqrt(r2) * k.inv_ell);
+      return exp_neg(-sqrt(r2) * k.inv_ell);
     case SPDHSS_K_GAUSS:
-      return exp(-r2 * (k.inv_ell * k.inv_ell));
+      return exp_neg(-r2 * (k.inv_ell * k.inv_ell));
     case SPDHSS_K_MATERN32: {
       double t = 1.7320508075688772 * sqrt(r2) * k.inv_ell;
-      return (1.0 + t) * exp(-t);
+      return (1.0 + t) * exp_neg(-t);
     }
     default:
       return 1.0 / sqrt(1.0 + r2 * (k.inv_ell * k.inv_ell));
@@ -170,11 +224,11 @@ __device__ __forceinline__ double kernel_r2(const KernelFn& k, double r2) {
 // The same kernel with its kind fixed at compile time (no per-entry branch).
 template <int KIND>
 __device__ __forceinline__ double kernel_r2_k(double r2, double inv_ell) {
-  if (KIND == SPDHSS_K_EXP) return exp(-sqrt(r2) * inv_ell);
-  if (KIND == SPDHSS_K_GAUSS) return exp(-r2 * (inv_ell * inv_ell));
+  if (KIND == SPDHSS_K_EXP) return exp_neg(-sqrt(r2) * inv_ell);
+  if (KIND == SPDHSS_K_GAUSS) return exp_neg(-r2 * (inv_ell * inv_ell));
   if (KIND == SPDHSS_K_MATERN32) {
     const double t = 1.7320508075688772 * sqrt(r2) * inv_ell;
-    return (1.0 + t) * exp(-t);
+    return (1.0 + t) * exp_neg(-t);
   }
   return 1.0 / sqrt(1.0 + r2 * (inv_ell * inv_ell));
 }

@@ -19,7 +19,7 @@
 //
 // One CTA (8 warps) takes a job: rows [r0, r0 + R) (R <= 512, slices of 128 rows, a lane
 // holding 4 consecutive rows) and a column range, staged S columns at a time through a
-// 4-deep shared-memory pipeline.  Warps are slices x teams; a team takes every TM-th
+// 3-deep shared-memory pipeline of 32 KB stages.  Warps are slices x teams; a team takes every TM-th
 // group of CG columns, and each warp applies both directions to the entries it loads:
 //  - Direction 1 (A x): each lane accumulates its 4 rows x NC right-hand sides over the
 //    columns; the teams' partial sums are added in team order at the end.
@@ -39,8 +39,8 @@ namespace spd {
 
 namespace {
 
-constexpr int kSymStages = 4;
-constexpr int kSymStageFloats = 4096;   // A entries per pipeline stage (16 KB)
+constexpr int kSymStages = 3;
+constexpr int kSymStageFloats = 8192;   // A entries per pipeline stage (32 KB)
 constexpr int kSymMaxCols = 128;        // columns per stage
 constexpr int kSymRed2 = 1024;          // direction-2 slice partials per stage
 
@@ -393,7 +393,7 @@ static int sym_row_block() {
 }
 
 // columns per stage for a job of R rows: a multiple of CG x teams, a power of two,
-// S * ceil4(R) <= 4096, S <= 128 (64 for 16 right-hand sides: one x1 piece per thread)
+// S * ceil4(R) <= 8192, S <= 128 (64 for 16 right-hand sides: one x1 piece per thread)
 static int sym_stage_cols(int R, int nc) {
   const int R4 = (int)align4(R);
   const int RS = (R + 127) / 128;

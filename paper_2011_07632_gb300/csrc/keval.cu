@@ -142,6 +142,29 @@ __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ pro
   }
 }
 
+template <int KIND>
+__global__ void k_kernel_eval(const double* __restrict__ r2, double* __restrict__ out, int64_t n,
+                              double inv_ell) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = kernel_r2_k<KIND>(r2[i], inv_ell);
+}
+
+void kernel_eval_launch(const KernelFn& k, const double* r2, double* out, int64_t n,
+                        cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
+  switch (k.kind) {
+    case SPDHSS_K_EXP: k_kernel_eval<SPDHSS_K_EXP><<<g, 256, 0, s>>>(r2, out, n, k.inv_ell); break;
+    case SPDHSS_K_GAUSS: k_kernel_eval<SPDHSS_K_GAUSS><<<g, 256, 0, s>>>(r2, out, n, k.inv_ell); break;
+    case SPDHSS_K_MATERN32:
+      k_kernel_eval<SPDHSS_K_MATERN32><<<g, 256, 0, s>>>(r2, out, n, k.inv_ell);
+      break;
+    default: k_kernel_eval<SPDHSS_K_IMQ><<<g, 256, 0, s>>>(r2, out, n, k.inv_ell); break;
+  }
+  SPD_LAUNCHED();
+}
+
 void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s) {
   if (b.empty()) { merge_skip(); return; }
   if (merging()) {
@@ -187,6 +210,22 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 // ID's skeleton: pivots and |R_kk| depend on the matrix M only through M^T M, which R
 // shares.
 // ---------------------------------------------------------------------------------------
+// one proxy row against the m candidate columns: col[j * ld] = K(y, x_(c0 + j))
+template <int KIND>
+__device__ __forceinline__ void proxy_row(double* col, int ld, const double* y,
+                                          const double* __restrict__ xc, int64_t ldxc,
+                                          int64_t c0, int m, int dim, double inv_ell) {
+  for (int j = 0; j < m; ++j) {
+    const int64_t pc = c0 + j;
+    double r2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double d = y[a] - xc[a * ldxc + pc];
+      r2 += d * d;
+    }
+    col[(int64_t)j * ld] = kernel_r2_k<KIND>(r2, inv_ell);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_proxy_qr(const ProxyQrProb* __restrict__ probs,
                                                   KernelFn kf_, int dim_) {
   const ProxyQrProb Q = probs[blockIdx.x];
@@ -200,27 +239,32 @@ __global__ void __launch_bounds__(256) k_proxy_qr(const ProxyQrProb* __restrict_
   const int rows = Q.rows, m = P.cols;
   const int lanes = col_group_lanes(m), ld = col_group_ld(rows, lanes);
   const int tid = threadIdx.x, warp = tid >> 5;
-  // evaluation: one proxy point per thread and row, every candidate column
-  for (int i = tid; i < rows; i += blockDim.x) {
-    const int r = Q.r0 + i;
-    double y[3] = {0, 0, 0};
-    proxy_point(P, dim, r / kd, y);
-    for (int j = 0; j < m; ++j) {
-      const int64_t pc = P.c0 + j;
-      double v;
-      if (kd > 1) {
-        v = rpy_entry<double>(y[0] - P.xc[pc], y[1] - P.xc[P.ldxc + pc],
-                              y[2] - P.xc[2 * P.ldxc + pc], r % kd, (int)P.xc[3 * P.ldxc + pc],
-                              kf.inv_ell);
-      } else {
-        double r2 = 0.0;
-        for (int a = 0; a < dim; ++a) {
-          const double d = y[a] - P.xc[a * P.ldxc + pc];
-          r2 += d * d;
-        }
-        v = kernel_r2(kf, r2);
+  // evaluation: one proxy point per thread and row, every candidate column (the
+  // descriptor's fields in registers, the kernel kind dispatched once per row)
+  {
+    const double* __restrict__ xc = P.xc;
+    const int64_t ldxc = P.ldxc, c0 = P.c0;
+    const int r0 = Q.r0;
+    for (int i = tid; i < rows; i += blockDim.x) {
+      const int r = r0 + i;
+      double y[3] = {0, 0, 0};
+      proxy_point(P, dim, r / kd, y);
+      double* col = sA + i;
+      switch (kd > 1 ? -1 : kf.kind) {
+        case SPDHSS_K_EXP: proxy_row<SPDHSS_K_EXP>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
+        case SPDHSS_K_GAUSS: proxy_row<SPDHSS_K_GAUSS>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
+        case SPDHSS_K_MATERN32:
+          proxy_row<SPDHSS_K_MATERN32>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell);
+          break;
+        case SPDHSS_K_IMQ: proxy_row<SPDHSS_K_IMQ>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
+        default:
+          for (int j = 0; j < m; ++j) {
+            const int64_t pc = c0 + j;
+            col[(int64_t)j * ld] =
+                rpy_entry<double>(y[0] - xc[pc], y[1] - xc[ldxc + pc], y[2] - xc[2 * ldxc + pc],
+                                  r % kd, (int)xc[3 * ldxc + pc], kf.inv_ell);
+          }
       }
-      sA[i + (int64_t)j * ld] = v;
     }
   }
   __syncthreads();

@@ -25,6 +25,10 @@ struct TileProb {
   int dim = 0;
 };
 void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStream_t s);
+// out[i] = K(r) for r2[i] = r^2, the scalar kernel function exactly as the tiles evaluate
+// it (no shift); device arrays of n entries
+void kernel_eval_launch(const KernelFn& k, const double* r2, double* out, int64_t n,
+                        cudaStream_t s);
 
 // Proxy points of one node (reading of the proxy point method): 6 cube surfaces of
 // half-width h_t = 3h + (H - 3h) (t/5)^2 around the cell centre c, each face carrying a

@@ -39,6 +39,7 @@ _PI64 = ctypes.POINTER(ctypes.c_int64)
 _SIGS = {
     "h2_build": [_P, _I64, _I, KernelDesc, _I, _D, _P, ctypes.POINTER(_P)],
     "h2_matmul": [_P, _P, _P, _I, _I64, _P],
+    "spdhss_kernel_eval": [KernelDesc, _P, _P, _I64, _P],
     "h2_info": [_P, _PI64],
     "h2_export_tree": [_P] + [_PI64] * 11,
     "h2_export_skeletons": [_P, _PI64, _PI64],

