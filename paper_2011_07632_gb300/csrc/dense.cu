@@ -1629,7 +1629,7 @@ __device__ __forceinline__ double tri_scalars(double* d, double n2_rest, double*
   const double alpha = *d;
   const double normx = sqrt(fma(alpha, alpha, n2_rest));
   double beta = alpha, c = 0.0, u0 = 0.0;
-  if (normx > 0.0) {
+  if (normx > kHhMinNorm) {
     beta = alpha >= 0.0 ? -normx : normx;
     u0 = alpha - beta;
     c = -1.0 / (beta * u0);

@@ -190,11 +190,15 @@ __device__ __forceinline__ double group_sum_n(double x, int lanes) {
 // Householder scalars of x (x_0 = *x0, |x|^2 = n2), the reflector left unnormalized:
 // u = x - beta e_1, H = I - c u u^T.  Writes u_0 over x_0, stores beta, returns c
 // (c = 0 for x = 0: the identity).
+// A column whose norm is at most 2^-480 is left alone (no reflector, beta = alpha): below
+// that, beta * u0 can leave the normal range and c = -1 / (beta u0) overflow, and the sum
+// of squares it came from has already lost its precision to underflow.
+constexpr double kHhMinNorm = 0x1p-480;
 __device__ __forceinline__ double hh_scalars(double* x0, double n2, double* beta_out) {
   const double alpha = *x0;
   const double normx = sqrt(n2);
   double beta = alpha, c = 0.0;
-  if (normx > 0.0) {
+  if (normx > kHhMinNorm) {
     beta = alpha >= 0.0 ? -normx : normx;
     const double u0 = alpha - beta;
     *x0 = u0;

@@ -173,6 +173,7 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
         }
         p.h = hh;
         p.H = std::max(H, 3.0 * hh * (1.0 + 1e-12));
+        p.scale = proxy_scale(h->kfn, hh);
         if (t == D) {
           p.xc = h->td.xs.p; p.ldxc = n; p.c0 = T.begin[i];
         } else {

@@ -4,6 +4,8 @@
 #include <map>
 #include <type_traits>
 
+#include <cmath>
+
 #include "keval.cuh"
 
 namespace spd {
@@ -136,10 +138,30 @@ __global__ void __launch_bounds__(256) k_proxy(const ProxyProb* __restrict__ pro
         const double d = sy[a][ii] - P.xc[a * P.ldxc + pc];
         r2 += d * d;
       }
-      v = kernel_r2(kf, r2);
+      v = kernel_r2(kf, r2) * P.scale;
     }
     P.out[i + (int64_t)j * P.ldo] = v;
   }
+}
+
+double proxy_scale(const KernelFn& k, double h) {
+  if (k.kind == SPDHSS_K_RPY) return 1.0;
+  const double t = 2.0 * h * k.inv_ell;
+  double kb;
+  switch (k.kind) {
+    case SPDHSS_K_EXP: kb = std::exp(-t); break;
+    case SPDHSS_K_GAUSS: kb = std::exp(-t * t); break;
+    case SPDHSS_K_MATERN32: {
+      const double u = 1.7320508075688772 * t;
+      kb = (1.0 + u) * std::exp(-u);
+      break;
+    }
+    default: kb = 1.0 / std::sqrt(1.0 + t * t);
+  }
+  if (!(kb > 0.0) || kb >= 0x1p-200) return 1.0;
+  int e = 0;
+  std::frexp(kb, &e);   // kb = f 2^e, f in [1/2, 1)
+  return std::ldexp(1.0, std::min(-e, 1000));
 }
 
 template <int KIND>
@@ -214,7 +236,8 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
 template <int KIND>
 __device__ __forceinline__ void proxy_row(double* col, int ld, const double* y,
                                           const double* __restrict__ xc, int64_t ldxc,
-                                          int64_t c0, int m, int dim, double inv_ell) {
+                                          int64_t c0, int m, int dim, double inv_ell,
+                                          double scale) {
   for (int j = 0; j < m; ++j) {
     const int64_t pc = c0 + j;
     double r2 = 0.0;
@@ -222,7 +245,7 @@ __device__ __forceinline__ void proxy_row(double* col, int ld, const double* y,
       const double d = y[a] - xc[a * ldxc + pc];
       r2 += d * d;
     }
-    col[(int64_t)j * ld] = kernel_r2_k<KIND>(r2, inv_ell);
+    col[(int64_t)j * ld] = kernel_r2_k<KIND>(r2, inv_ell) * scale;
   }
 }
 
@@ -251,12 +274,12 @@ __global__ void __launch_bounds__(256) k_proxy_qr(const ProxyQrProb* __restrict_
       proxy_point(P, dim, r / kd, y);
       double* col = sA + i;
       switch (kd > 1 ? -1 : kf.kind) {
-        case SPDHSS_K_EXP: proxy_row<SPDHSS_K_EXP>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
-        case SPDHSS_K_GAUSS: proxy_row<SPDHSS_K_GAUSS>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
+        case SPDHSS_K_EXP: proxy_row<SPDHSS_K_EXP>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell, P.scale); break;
+        case SPDHSS_K_GAUSS: proxy_row<SPDHSS_K_GAUSS>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell, P.scale); break;
         case SPDHSS_K_MATERN32:
-          proxy_row<SPDHSS_K_MATERN32>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell);
+          proxy_row<SPDHSS_K_MATERN32>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell, P.scale);
           break;
-        case SPDHSS_K_IMQ: proxy_row<SPDHSS_K_IMQ>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell); break;
+        case SPDHSS_K_IMQ: proxy_row<SPDHSS_K_IMQ>(col, ld, y, xc, ldxc, c0, m, dim, kf.inv_ell, P.scale); break;
         default:
           for (int j = 0; j < m; ++j) {
             const int64_t pc = c0 + j;

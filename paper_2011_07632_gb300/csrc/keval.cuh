@@ -50,8 +50,17 @@ struct ProxyProb {
   int64_t ldo;
   KernelFn kf{};   // kernel and dimension of this problem (dim 0: the launch's)
   int dim = 0;
+  double scale = 1.0;   // power of two multiplying every entry (proxy_scale)
 };
 void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStream_t s);
+// The power of two that brings the entries of a node's proxy matrix near 1 when they are
+// tiny, so that the sums of squares of the ID's Householder steps stay clear of underflow:
+// every entry is K(r) at a distance r >= 2h (the inner proxy surface lies 3h from the
+// centre of the cell of half-width h that holds the candidates) and the scalar kernels
+// decrease in r, so K(2h) bounds them.  Multiplying by 2^s is exact, and the ID (pivot
+// order, the relative rank test, R11^-1 R12) does not change under it.  1 unless
+// 0 < K(2h) < 2^-200 (and for the RPY tensor).
+double proxy_scale(const KernelFn& k, double h);
 
 // One row block of a proxy matrix, evaluated and factored in shared memory: rows
 // [r0, r0 + rows) of K(P_i, X_cand) (p.cols = m candidate columns) are reduced by an

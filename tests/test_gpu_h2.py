@@ -107,3 +107,31 @@ def test_h2_matvec_large_sampled_rows():
     ye = K @ x + 1e-4 * x[rows]
     err = np.abs(y[rows] - ye).max() / np.abs(ye).max()
     assert err < 1e-7
+
+
+def test_h2_far_field_below_the_squares_underflow():
+    """A Gaussian whose far-field values reach 1e-150 and below (n = 20,000 points of unit
+    density in a ball, length scale 1, leaf 400): summed squares of such proxy entries
+    underflow, which once made the ID's reflectors overflow (ranks of 1, every product
+    entry non-finite).  Each node's proxy matrix is now scaled by a power of two before the
+    ID, so the skeletons equal the oracle's (scaled LAPACK norms) and the product matches
+    the oracle's H^2 product."""
+    from oracle import structured as OSt
+    api = need_gpu()
+    n, leaf, ell = 20000, 400, 1.0
+    X = inputs.ball(n, 0)
+    h = api.H2(X, "gauss", ell, 1e-2, leaf, 1e-8)
+    tr = OT.build_tree(X, leaf)
+    oh = OH.build_h2(tr, X, OK.GAUSS, ell, 1e-2, 1e-8)
+    off, idx = h.export_skeletons()
+    for i in range(len(off) - 1):
+        gs = np.sort(idx[off[i]:off[i + 1]])
+        os_ = np.sort(np.asarray(oh.skel[i], dtype=np.int64)) if oh.skel[i] is not None else np.zeros(0, np.int64)
+        assert np.array_equal(gs, os_), i
+    x = np.random.default_rng(3).standard_normal((n, 2))
+    y = h.matmul(x).cpu().numpy()
+    assert np.isfinite(y).all()
+    yo = np.empty_like(y)
+    yo[tr.perm] = OSt.h2_matvec(oh, x[tr.perm])
+    assert rel(y, yo) < 1e-12
+    assert np.isfinite(h.matmul_mixed(x).cpu().numpy()).all()

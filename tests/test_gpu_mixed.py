@@ -1,5 +1,7 @@
 """Mixed precision: FP32 H^2 products against the FP64 product and the exact kernel matrix;
 PCG with the FP32 product reaches the FP64 true-residual tolerance."""
+import math
+
 import numpy as np
 import pytest
 
@@ -117,7 +119,10 @@ def test_precision_mode_against_the_oracle(kind, ell, sigma, dim, n, leaf, r):
         assert rel(Hg, Mh) <= a_oracle * (1 + approx_slack) + 1e-8, (prec, rel(Hg, Mh), a_oracle)
         x, it, rr = api.pcg_solve(h, api.ULV(hs), b, tol=1e-6, raise_on_no_convergence=True)
         assert rr[0] <= 1e-6
-        assert it[0] <= it_factor * int(ito[0]) + 1, (prec, int(it[0]), int(ito[0]))
+        # counts in the hundreds move by up to 3% under rounding-only changes (measured on
+        # the oracle: a transposed product or a 1e-15 change of b; the Gaussian case here
+        # takes ~500 iterations), so the bound carries that spread
+        assert it[0] <= it_factor * math.ceil(1.03 * int(ito[0])) + 1, (prec, int(it[0]), int(ito[0]))
 
 
 @pytest.mark.parametrize("prec", [1, 2])
