@@ -537,7 +537,10 @@ def run_gpu(args):
     cfg["n"], cfg["rank"] = args.n, args.rank
     n, nrhs = cfg["n"], cfg["nrhs"]
     dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.current_stream()
+    # the step runs on a stream of its own (the library captures steady PCG iterations as
+    # CUDA graphs on a caller stream; the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     pts_h = inputs.uniform_cube(n, 3, 0 + rank)
     b_h = inputs.rhs(n, nrhs, 1 + rank)
     pts = torch.from_numpy(pts_h).to(dev)

@@ -6,6 +6,7 @@
 // per iteration to decide.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ulv.cuh"
 
@@ -230,6 +231,76 @@ static void sub(const double* b, const double* ax, double* out, int64_t count, c
   SPD_LAUNCHED();
 }
 
+// Pinned host landing place of the per-iteration residual norms (a device-to-host copy
+// that a captured graph can hold).
+struct PinnedScalars {
+  double* p = nullptr;
+  explicit PinnedScalars(int n) { SPD_CUDA(cudaHostAlloc((void**)&p, sizeof(double) * std::max(n, 1), cudaHostAllocDefault)); }
+  ~PinnedScalars() { if (p) cudaFreeHost(p); }
+  PinnedScalars(const PinnedScalars&) = delete;
+  PinnedScalars& operator=(const PinnedScalars&) = delete;
+};
+
+// SPDHSS_PCG_GRAPHS=0 launches every iteration directly (the graphs replay the same
+// launches in the same order, so results do not depend on the setting).
+static bool pcg_graphs_enabled() {
+  const char* e = std::getenv("SPDHSS_PCG_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
+// A CUDA graph of a fixed launch sequence, captured once on the solve's stream (relaxed
+// mode: the launchers' attribute calls are allowed) and replayed; if the capture fails the
+// solve keeps launching directly.
+struct PcgGraph {
+  bool enabled;
+  bool tried = false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  int64_t launches = 0;   // kernels per replay (added to the launch count)
+  explicit PcgGraph(bool on) : enabled(on) {}
+  ~PcgGraph() {
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+  }
+  bool ready() const { return ex != nullptr; }
+  template <class F>
+  void capture(cudaStream_t s, F&& body) {
+    if (tried) return;
+    tried = true;
+    const int64_t before = spdhss_launch_count();
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    bool ok = true;
+    try {
+      body();
+    } catch (...) {
+      ok = false;
+    }
+    cudaGraph_t cg = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &cg);
+    launches = spdhss_launch_count() - before;
+    count_launches(-launches);   // captured, not executed
+    if (!ok || e != cudaSuccess || !cg) {
+      if (cg) cudaGraphDestroy(cg);
+      cudaGetLastError();
+      return;
+    }
+    if (cudaGraphInstantiate(&ex, cg, 0) != cudaSuccess) {
+      cudaGraphDestroy(cg);
+      ex = nullptr;
+      cudaGetLastError();
+      return;
+    }
+    g = cg;
+  }
+  void launch(cudaStream_t s) {
+    SPD_CUDA(cudaGraphLaunch(ex, s));
+    count_launches(launches);
+  }
+};
+
 // precision = 0: FP64 throughout.  precision = 1: the product with A inside the iteration
 // uses the FP32 copy of the H^2 matrix (FP32 kernel entries and accumulation); the ULV
 // preconditioner, the recurrences and every residual check stay FP64, and every
@@ -310,9 +381,10 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     for (int c = 0; c < nrhs; ++c) rel[c] = std::sqrt(std::max(h[c], 0.0)) / bn[c];
     (void)replace_active;
   };
-  int it = 0;
-  for (it = 1; it <= maxit; ++it) {
-    merge_stage(10, it);
+  // One iteration's launches between its two host decisions: s1 (q = A p, the step, the
+  // residual norms, landing in pinned host memory) and s2 (z = M^-1 r, the new direction).
+  PinnedScalars prr(nrhs);
+  auto s1 = [&]() {
     if (PF) {                                     // q = A p in FP32
       convert_d2f(p, PF->xs.p, nc, s);
       h2_plan_run(h2, *PF, s);
@@ -323,8 +395,28 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
     dots(p, q, n, nrhs, part.p, pq, s);
     axpy_xr(x.p, r.p, p, q, n, nrhs, rz, pq, done.p, s);
     dots(r.p, r.p, n, nrhs, part.p, rr, s);
-    SPD_CUDA(cudaMemcpyAsync(hrr.data(), rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPD_CUDA(cudaMemcpyAsync(prr.p, rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  };
+  auto s2 = [&]() {
+    copy_vec(z, r.p, nc, s);
+    if (PU) ulv_solve_sorted(u, *PU, s);          // z = M^{-1} r
+    dots(r.p, z, n, nrhs, part.p, rzn, s);
+    update_p(p, z, n, nrhs, rzn, rz, done.p, s);
+    copy_vec(rz, rzn, nrhs, s);
+  };
+  // Steady iterations (no host intervention) replay s2 of one iteration and s1 of the next
+  // as one captured CUDA graph: the launches and their order are those of the direct path,
+  // so the results are identical.  Captured from the third iteration on, once per solve.
+  PcgGraph graph(pcg_graphs_enabled() && !merging() && !prof_enabled() && s != nullptr &&
+                 s != cudaStreamLegacy && s != cudaStreamPerThread);
+  bool fused = false;   // s1 of this iteration was launched inside the graph
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    merge_stage(10, it);
+    if (!fused) s1();
+    fused = false;
     SPD_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < nrhs; ++c) hrr[c] = prr.p[c];
     bool any_pass = false;
     for (int c = 0; c < nrhs; ++c) {
       if (hdone[c] == 1) continue;
@@ -359,16 +451,23 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       true_residual(trel, false);
       copy_vec(r.p, PR.ys.p, nc, s);
     }
-    copy_vec(z, r.p, nc, s);
-    if (PU) ulv_solve_sorted(u, *PU, s);          // z = M^{-1} r
-    dots(r.p, z, n, nrhs, part.p, rzn, s);
-    update_p(p, z, n, nrhs, rzn, rz, done.p, s);
-    copy_vec(rz, rzn, nrhs, s);
-    bool restarted = false;
-    for (int c = 0; c < nrhs; ++c)
-      if (hdone[c] == 2) { hdone[c] = 0; restarted = true; }
-    if (restarted)
+    bool restart = false;
+    for (int c = 0; c < nrhs; ++c) restart = restart || hdone[c] == 2;
+    // a restart changes the device flags between s2 and the next s1: launched directly
+    if (graph.enabled && !restart && it >= 2 && it < maxit) {
+      if (!graph.ready()) graph.capture(s, [&]() { s2(); s1(); });
+      if (graph.ready()) {
+        graph.launch(s);
+        fused = true;
+        continue;
+      }
+    }
+    s2();
+    if (restart) {
+      for (int c = 0; c < nrhs; ++c)
+        if (hdone[c] == 2) hdone[c] = 0;
       SPD_CUDA(cudaMemcpyAsync(done.p, hdone.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
   }
   std::vector<double> trel;
   merge_stage(11, 0);

@@ -133,3 +133,31 @@ def test_not_spd_is_reported():
     with pytest.raises(native.SpdhssError) as e:
         api.HSS(h, 8, 10, seed=1)
     assert e.value.status == native.NOT_SPD
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("case", ["headline", "long"])
+def test_pcg_graph_replay_is_identical(case, mixed, monkeypatch):
+    """Steady PCG iterations replay a captured CUDA graph of the same launches; with the
+    graphs off (SPDHSS_PCG_GRAPHS=0) every iteration is launched directly.  Iteration
+    counts, residuals and solutions are bit-identical, through residual replacements,
+    restarts and (mixed) the FP64 refreshes every 50 iterations."""
+    api = need_gpu()
+    if case == "headline":
+        n, kind, ell, sigma, r, nrhs = 4096, "exp", 1.0, 1e-2, 50, 3
+    else:
+        n, kind, ell, sigma, r, nrhs = 3000, "gauss", 0.2, 1e-4, 10, 2
+    X = inputs.uniform_cube(n, 3, 0)
+    h = api.H2(X, kind, ell, sigma, 64, 1e-8)
+    u = api.ULV(api.HSS(h, r, 10, omega=inputs.sketch(n, r + 10, 2)))
+    b = inputs.rhs(n, nrhs, 1)
+    import torch
+    st = torch.cuda.Stream()   # graphs are captured on the caller's stream (not the legacy one)
+    x1, it1, rr1 = api.pcg_solve(h, u, b, tol=1e-6, mixed=mixed, stream=st)
+    monkeypatch.setenv("SPDHSS_PCG_GRAPHS", "0")
+    x0, it0, rr0 = api.pcg_solve(h, u, b, tol=1e-6, mixed=mixed, stream=st)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.asarray(it1), np.asarray(it0))
+    assert np.array_equal(np.asarray(rr1), np.asarray(rr0))
+    assert np.array_equal(x1.cpu().numpy(), x0.cpu().numpy())
+    assert int(np.max(it1)) > 3
