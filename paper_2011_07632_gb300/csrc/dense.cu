@@ -711,7 +711,6 @@ static void potrf_blocked(const std::vector<PotrfProb>& big, int* d_info, const 
     }
   z.upload(s);
   copy_launch(z, s);
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 void potrf_launch(const Batch<PotrfProb>& b, int* d_info, cudaStream_t s) {
@@ -991,7 +990,6 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
     ProfScope ps(b.tag ? b.tag : "trsm", s, f);
     trsm_go(b.d.p, dw.p, (int64_t)work.size(), nblk, variant, smem, s);
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2075,7 +2073,6 @@ void householder_launch(const Batch<HhApplyProb>& b, int trans, cudaStream_t s) 
     ProfScope ps(b.tag ? b.tag : "householder", s);
     hh_go(b.d.p, dw.p, nw, nreg, hh_ept(b), trans, s);
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 __global__ void __launch_bounds__(256) k_form_q(const FormQProb* __restrict__ probs,
@@ -2128,7 +2125,6 @@ void form_q_launch(const Batch<FormQProb>& b, cudaStream_t s) {
     k_form_q<<<ceil_div(nw, 8), 256, 0, s>>>(b.d.p, dw.p, nw);
     SPD_LAUNCHED();
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------------------

@@ -304,7 +304,6 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
         k_id_assemble<<<(unsigned)ib.size(), 256, 0, s>>>(ib.d.p);
         SPD_LAUNCHED();
       }
-      SPD_CUDA(cudaStreamSynchronize(s));
       pos = end;
     }
     // per-depth skeleton offsets and coordinates
@@ -321,7 +320,6 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
       di.upload(sidx, s);
       k_gather_coords<<<ceil_div(Kt, 256), 256, 0, s>>>(h->td.xs.p, n, crow, di.p, Kt, sx[t].p);
       SPD_LAUNCHED();
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
     // sx[t].n is used as the leading dimension holder: crow * Kt entries
     if (Kt == 0) sx[t].n = crow;
@@ -358,7 +356,6 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
     cb.upload(s);
     copy_launch(cb, s);
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
   upool.clear();
   const int64_t K = h->Ktot;
   h->skel_x.alloc((size_t)std::max<int64_t>(K, 1) * crow);
@@ -367,7 +364,6 @@ void h2_build_impl(spdhss_h2_s* h, const double* d_points, int64_t n, int dim, i
     di.upload(h->skel_idx, s);
     k_gather_coords<<<ceil_div(K, 256), 256, 0, s>>>(h->td.xs.p, n, crow, di.p, K, h->skel_x.p);
     SPD_LAUNCHED();
-    SPD_CUDA(cudaStreamSynchronize(s));
   }
 
   // couplings, once per unordered far pair
@@ -634,7 +630,6 @@ static void h2_plan_build_t(const spdhss_h2_s* h, H2PlanT<F>& p, int ncol, int n
   for (auto& g : p.down) g.upload(s);
   p.leaf_out.upload(s);
   p.near.upload(s);
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 
@@ -1066,7 +1061,6 @@ void h2_plan_build(const spdhss_h2_s* h, H2Plan& p, int ncol, int nslot, cudaStr
     if (hm->coup_dd.n == 0) coup_dm_build<double>(hm, hm->coup_dd, s);
     h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, nullptr, s);
     rowcoup_plan<double>(h, p, ncol, h->coup_dd.p, s);
-    SPD_CUDA(cudaStreamSynchronize(s));
     return;
   }
   h2_plan_build_t<double>(h, p, ncol, nslot, h->basis.p, h->coup.p, s);
@@ -1086,7 +1080,6 @@ void h2_plan_sample_f(spdhss_h2_s* h, H2PlanF& p, int ncol, int nslot, int tc, c
   p.coup_src.alloc(std::max<size_t>(h->coup.n, 1));
   if (h->coup.n) convert_d2f(h->coup.p, p.coup_src.p, (int64_t)h->coup.n, s);
   h2_plan_build_t<float>(h, p, ncol, nslot, h->basis_f.p, p.coup_src.p, s, tc);
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
@@ -1109,7 +1102,6 @@ H2PlanF& h2_plan_f(spdhss_h2_s* h, int ncol, cudaStream_t s) {
       if (h->coup.n) convert_d2f(h->coup.p, p->coup_src.p, (int64_t)h->coup.n, s);
       h2_plan_build_t<float>(h, *p, ncol, 1, h->basis_f.p, p->coup_src.p, s);
     }
-    SPD_CUDA(cudaStreamSynchronize(s));
     it = h->plans_f.emplace(ncol, std::move(p)).first;
   }
   return *it->second;

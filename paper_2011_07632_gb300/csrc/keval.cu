@@ -70,7 +70,6 @@ void tile_launch(const Batch<TileProb>& b, const KernelFn& k, int dim, cudaStrea
     k_tiles<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
     SPD_LAUNCHED();
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -215,7 +214,6 @@ void proxy_launch(const Batch<ProxyProb>& b, const KernelFn& k, int dim, cudaStr
     k_proxy<<<(unsigned)work.size(), 256, 0, s>>>(b.d.p, dw.p, k, dim);
     SPD_LAUNCHED();
   }
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------------------

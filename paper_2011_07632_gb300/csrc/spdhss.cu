@@ -140,7 +140,6 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
       DevBuf<double> om((size_t)n * sc);
       philox_normal(om.p, n, sc, n, seed, s);
       permute_to_sorted(om.p, n, plan.xs.p, n, sc, h2->td.perm.p, s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
     h2_plan_run(h2, plan, s);
     Y = plan.ys.p;
@@ -156,7 +155,6 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
       DevBuf<double> o2((size_t)n * sc);
       philox_normal(o2.p, n, sc, n, seed, s);
       permute_to_sorted(o2.p, n, om.p, n, sc, h2->td.perm.p, s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
     convert_d2f(om.p, fp.xs.p, n * sc, s);
     h2_plan_run(h2, fp, s);
@@ -440,7 +438,6 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
       }
       zb.run(s);
       pbt.run(s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
 
     // (e) coefficient matrices for every near (!= self) and far pair of this level, i < j
@@ -565,7 +562,6 @@ void spdhss_build_impl(spdhss_hss_s* hs, const spdhss_h2_s* h2, int r, int p,
         nb.launch(h2->kfn, xs, n, dim, s);
         g1.run(s);
         g2.run(s);
-        SPD_CUDA(cudaStreamSynchronize(s));
         pos = end;
       }
       // sibling pairs of this level, kept for the final HSS
@@ -702,7 +698,6 @@ static void hss_plan_build(const spdhss_hss_s* hs, HssPlan& P, int ncol, cudaStr
   for (auto& g : P.down) g.upload(s);
   P.leaf_out.upload(s);
   P.near.upload(s);
-  SPD_CUDA(cudaStreamSynchronize(s));
 }
 
 void hss_matmul_impl(spdhss_hss_s* hs, const double* X, double* Y, int nrhs, int64_t ld,

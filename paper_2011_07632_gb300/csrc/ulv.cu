@@ -158,7 +158,6 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
       gw.run(s);
       g1.run(s);
       g2.run(s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
     // (2) QR of W_i, U~_i
     {
@@ -193,7 +192,6 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
         ds.upload(src, s); dd.upload(dst, s); dl.upload(lds, s); dr.upload(rr, s);
         k_triu<<<(unsigned)src.size(), 256, 0, s>>>(ds.p, dl.p, dd.p, dr.p, (int)src.size());
         SPD_LAUNCHED();
-        SPD_CUDA(cudaStreamSynchronize(s));
       }
     }
     // (3) Q^T D Q
@@ -225,7 +223,6 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
       tr.upload(s); copy_launch(tr, s);
       h2b.upload(s); householder_launch(h2b, 1, s);
       back.upload(s); copy_launch(back, s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
     // (4) eliminate the complement
     {
@@ -261,7 +258,6 @@ void ulv_factor_impl(spdhss_ulv_s* u, const spdhss_hss_s* hs, cudaStream_t s) {
       tb.upload(s);
       trsm_launch(tb, s);
       gb.run(s);
-      SPD_CUDA(cudaStreamSynchronize(s));
     }
   }
   // root block from the level L-1 reduced blocks
@@ -492,7 +488,6 @@ UlvPlan& ulv_plan(spdhss_ulv_s* u, int ncol, cudaStream_t s) {
   P.root_f.tag = P.root_b.tag = "gemm_ulv_root";
   P.root_f.upload(s);
   P.root_b.upload(s);
-  SPD_CUDA(cudaStreamSynchronize(s));
   it = u->plans.emplace(ncol, std::move(pp)).first;
   return *it->second;
 }
