@@ -464,7 +464,14 @@ def run_precision(args):
 # the n = 4096 workload, from one ncu capture.  Each entry names the source files of the
 # family's kernels and a fingerprint of their text at the time of the capture: when the
 # files have changed since, the bench reports the traffic as null (stale capture).
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {
+    # k_proxy_qr (profiles/launches_headline_exp3d_n4096.md): leaf level 0.324 MB read +
+    # 0.022 MB written, depth 2 0.343 MB + 0.375 MB; the family's two launches per step
+    "qr_h2_id_blocks": {"bytes": (324352 + 22016 + 343040 + 375040) // 2,
+                        "sources": ["csrc/keval.cu", "csrc/keval.cuh", "csrc/common.cuh",
+                                    "csrc/dense.cuh"],
+                        "sha16": "e9ccf92b8878d5d0"},
+}
 
 
 def source_fingerprint(files):
