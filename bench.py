@@ -660,6 +660,7 @@ def run_gpu(args):
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
         "at_scale": at_scale, "serving": serving,
         "clocks": clk.summary(), "kernels": family_table(prof, fp64_peak),
+        "tuning": native.tuning_report(),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

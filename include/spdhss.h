@@ -347,6 +347,17 @@ const char* spdhss_version(void);
 void spdhss_profile(int enable);
 int64_t spdhss_profile_report(char* buf, int64_t len);
 
+/* Launch-variant autotuning (no counterpart in the paper: a GPU launch detail).  The first
+ * launch of a tuned kind for a new shape bucket times each candidate variant once on a
+ * synthetic problem set of that shape (private stream) and keeps the fastest for the
+ * process, per device; only variants that leave the arithmetic unchanged are tuned (today
+ * the columns per CTA of the blocked triangular solve), so results never depend on the
+ * choice.  SPDHSS_TUNE=0 in the environment keeps the fixed launch rules.
+ * spdhss_tuning_report writes the choices, one line per key ("dev0 trsm_blk n64 c8 p256 ->
+ * 4  (1:ms 2:ms ...)"), NUL-terminated into the HOST buffer buf of len bytes (truncated if
+ * short) and returns the length the full report needs. */
+int64_t spdhss_tuning_report(char* buf, int64_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,4 +1,3 @@
-#include <unordered_set>
 // C ABI entry points (include/spdhss.h): argument checks, error capture, and the H^2 calls.
 #include <atomic>
 #include <cstdio>
@@ -6,8 +5,10 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <unordered_set>
 
 #include "h2.cuh"
+#include "tune.cuh"
 
 namespace spd {
 
@@ -207,6 +208,16 @@ void spdhss_profile(int enable) {
     g_acc.clear();
   }
   g_prof = enable != 0;
+}
+
+int64_t spdhss_tuning_report(char* buf, int64_t len) {
+  const std::string out = spd::tuning_report();
+  if (buf && len > 0) {
+    const int64_t k = std::min<int64_t>(len - 1, (int64_t)out.size());
+    std::memcpy(buf, out.data(), (size_t)k);
+    buf[k] = 0;
+  }
+  return (int64_t)out.size() + 1;
 }
 
 int64_t spdhss_profile_report(char* buf, int64_t len) {

@@ -4,9 +4,11 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "dense.cuh"
+#include "tune.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -904,14 +906,117 @@ static bool trsm_fits_blocked(int n) {
   return (size_t)n * sizeof(double) + TRB * 33 * sizeof(double) <= kTrsmMaxSmem;
 }
 
+template <int C>
+static void trsm_blk_go(const TrsmProb* probs, const int2* work, int64_t nwork, size_t smem,
+                        cudaStream_t s);
+
+// synthetic unit lower-triangular T (1e-3 below the diagonal) and B = 1, for timing
+__global__ void k_trsm_synth(double* __restrict__ T, int n, int64_t count, double* __restrict__ B,
+                             int64_t nb) {
+  const int64_t nt = (int64_t)n * n * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt + nb;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nt) {
+      const int64_t q = e % ((int64_t)n * n);
+      const int i = (int)(q % n), j = (int)(q / n);
+      T[e] = i == j ? 1.0 : (i > j ? 1e-3 : 0.0);
+    } else {
+      B[e - nt] = 1.0;
+    }
+  }
+}
+
+// Time of the blocked TRSM with v columns per CTA on `count` synthetic n x n problems of
+// ncol columns (private stream, CUDA events, three launches after a warm-up).
+static double trsm_time_variant(int v, int n, int ncol, int count) {
+  cudaStream_t ps;
+  SPD_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+  double ms = -1.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    StreamScope sc(ps);
+    DevBuf<double> T((size_t)count * n * n), B((size_t)count * n * ncol);
+    k_trsm_synth<<<1024, 256, 0, ps>>>(T.p, n, count, B.p, (int64_t)count * n * ncol);
+    SPD_LAUNCHED();
+    Batch<TrsmProb> bt;
+    for (int p = 0; p < count; ++p)
+      bt.push(TrsmProb{T.p + (int64_t)p * n * n, n, B.p + (int64_t)p * n * ncol, n, n, ncol, 1, 0});
+    bt.upload(ps);
+    std::vector<int2> w;
+    for (int p = 0; p < count; ++p)
+      for (int c = 0; c < ncol; c += v) w.push_back(make_int2(p, c));
+    DevBuf<int2> dw;
+    dw.upload(w, ps);
+    const size_t smem = (size_t)n * v * sizeof(double) + TRB * 33 * sizeof(double);
+    auto go = [&]() {
+      switch (v) {
+        case 1: trsm_blk_go<1>(bt.d.p, dw.p, (int64_t)w.size(), smem, ps); break;
+        case 2: trsm_blk_go<2>(bt.d.p, dw.p, (int64_t)w.size(), smem, ps); break;
+        case 4: trsm_blk_go<4>(bt.d.p, dw.p, (int64_t)w.size(), smem, ps); break;
+        default: trsm_blk_go<8>(bt.d.p, dw.p, (int64_t)w.size(), smem, ps); break;
+      }
+      SPD_LAUNCHED();
+    };
+    go();
+    SPD_CUDA(cudaEventCreate(&e0));
+    SPD_CUDA(cudaEventCreate(&e1));
+    SPD_CUDA(cudaEventRecord(e0, ps));
+    for (int r = 0; r < 3; ++r) go();
+    SPD_CUDA(cudaEventRecord(e1, ps));
+    SPD_CUDA(cudaEventSynchronize(e1));
+    float f = 0.f;
+    SPD_CUDA(cudaEventElapsedTime(&f, e0, e1));
+    ms = f / 3.0;
+  } catch (...) {
+    ms = -1.0;
+    cudaGetLastError();
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(ps);
+  cudaStreamDestroy(ps);
+  return ms;
+}
+
+static int pow2_at_least(int64_t x) {
+  int p = 1;
+  while (p < x && p < (1 << 30)) p *= 2;
+  return p;
+}
+
 static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_t* smem,
-                                   int64_t* nblk) {
-  int maxn = 0, maxc = 0;
+                                   int64_t* nblk, cudaStream_t s = nullptr) {
+  int maxn = 0, maxc = 0, nprob = 0;
   for (const auto& p : b.h)
-    if (p.n > 0 && trsm_fits_blocked(p.n)) { maxn = std::max(maxn, p.n); maxc = std::max(maxc, p.ncol); }
+    if (p.n > 0 && trsm_fits_blocked(p.n)) {
+      maxn = std::max(maxn, p.n);
+      maxc = std::max(maxc, p.ncol);
+      ++nprob;
+    }
   int cw = maxc <= 1 ? 1 : (maxc <= 2 ? 2 : (maxc <= 4 ? 4 : 8));
   while (cw > 1 && (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double) > kTrsmMaxSmem)
     cw /= 2;
+  // columns per CTA do not change a column's arithmetic: the width is tuned per device and
+  // shape bucket (the rule above when tuning is off, or while the stream is being captured)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (s) cudaStreamIsCapturing(s, &cap);
+  const char* forced = std::getenv("SPDHSS_TRSM_COLS");   // 1, 2, 4 or 8: a fixed width
+  const int fw = forced ? std::atoi(forced) : 0;
+  if (fw == 1 || fw == 2 || fw == 4 || fw == 8) {
+    cw = std::min(cw, fw);
+  } else if (nprob > 0 && cap == cudaStreamCaptureStatusNone && tuning_enabled()) {
+    const int bn = pow2_at_least(maxn), bc = std::min(pow2_at_least(maxc), 64);
+    const int bp = std::min(pow2_at_least(nprob), 4096);
+    std::vector<int> cands;
+    for (int v : {1, 2, 4, 8})
+      if (v <= cw) cands.push_back(v);
+    const std::string key = "trsm_blk n" + std::to_string(bn) + " c" + std::to_string(bc) +
+                            " p" + std::to_string(bp);
+    const int64_t fit = std::max<int64_t>(1, (int64_t(256) << 20) / ((int64_t)maxn * maxn * 8));
+    const int count = (int)std::min<int64_t>(bp, fit);
+    const int tn = maxn, tc = maxc;
+    cw = tuned_variant(key, cands, cw, [&](int v) { return trsm_time_variant(v, tn, tc, count); });
+  }
   *variant = cw;
   *smem = (size_t)maxn * cw * sizeof(double) + TRB * 33 * sizeof(double);
   std::vector<int2> work;
@@ -953,7 +1058,7 @@ static void trsm_go(const TrsmProb* probs, const int2* work, int64_t nwork, int6
 }
 
 void trsm_prepare(Batch<TrsmProb>& b, cudaStream_t s) {
-  std::vector<int2> w = trsm_work(b, &b.variant, &b.smem, &b.nfirst);
+  std::vector<int2> w = trsm_work(b, &b.variant, &b.smem, &b.nfirst, s);
   b.work.upload(w, s);
   b.nwork = (int64_t)w.size();
 }
@@ -982,7 +1087,7 @@ void trsm_launch(const Batch<TrsmProb>& b, cudaStream_t s) {
   int variant;
   size_t smem;
   int64_t nblk;
-  std::vector<int2> work = trsm_work(b, &variant, &smem, &nblk);
+  std::vector<int2> work = trsm_work(b, &variant, &smem, &nblk, s);
   if (work.empty()) return;
   DevBuf<int2> dw;
   dw.upload(work, s);

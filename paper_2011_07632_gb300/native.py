@@ -100,6 +100,8 @@ def lib():
         L.spdhss_batched_stats.argtypes = [_PI64]
         L.spdhss_profile_report.restype = ctypes.c_int64
         L.spdhss_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+        L.spdhss_tuning_report.restype = ctypes.c_int64
+        L.spdhss_tuning_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
         _lib = L
     return _lib
 
@@ -121,6 +123,20 @@ def profile_report() -> dict:
     return json.loads(buf.value.decode())
 
 
+def tuning_report() -> dict:
+    """The autotuned launch variants of this process: {key: chosen variant}."""
+    need = int(lib().spdhss_tuning_report(None, 0))
+    buf = ctypes.create_string_buffer(need + 16)
+    lib().spdhss_tuning_report(buf, need + 16)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        if " -> " in line:
+            k, v = line.split(" -> ", 1)
+            out[k] = int(v.split()[0])
+    return out
+
+
 def exported_symbols() -> list:
     return list(_SIGS) + ["spdhss_last_error", "spdhss_launch_count", "spdhss_version",
-                          "spdhss_profile", "spdhss_profile_report", "spdhss_batched_stats"]
+                          "spdhss_profile", "spdhss_profile_report", "spdhss_tuning_report",
+                          "spdhss_batched_stats"]
