@@ -22,13 +22,26 @@ constexpr int GM = 64, GN = 64, GK = 16;
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
+// A tile with t.w > 0 covers only the K range kparts[t.w - 1] = (k_lo, k_hi, slot) of the
+// problem's concatenated segments and writes its unscaled sums to the partial slots from
+// `slot` on (column c, row r at [c * 64 + r]); k_gemm_kreduce adds the parts in order.
 template <class T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ probs,
                                               const GemmSegT<T>* __restrict__ segs,
-                                              const int4* __restrict__ tiles) {
+                                              const int4* __restrict__ tiles,
+                                              const int4* __restrict__ kparts,
+                                              T* __restrict__ partial) {
   const int4 t = tiles[blockIdx.x];
   const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
+  int klo = 0, khi = 0x7fffffff;
+  T* pout = nullptr;
+  if (t.w > 0) {
+    const int4 kp = kparts[t.w - 1];
+    klo = kp.x;
+    khi = kp.y;
+    pout = partial + (int64_t)kp.z * (4 * GM);
+  }
   __shared__ T As[GK][GM + 1];
   __shared__ T Bs[GK][GN + 1];
   const int tid = threadIdx.x;
@@ -39,9 +52,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
+  int kbase = 0;   // offset of the segment in the concatenated K range
   for (int s = P.seg0; s < P.seg1; ++s) {
     const GemmSegT<T> S = segs[s];
-    for (int k0 = 0; k0 < S.K; k0 += GK) {
+    const int ks = max(0, klo - kbase), ke = min(S.K, khi - kbase);
+    kbase += S.K;
+    for (int k0 = ks; k0 < ke; k0 += GK) {
 #pragma unroll
       for (int r = 0; r < (GM * GK) / 256; ++r) {
         const int e = tid + 256 * r;
@@ -49,7 +65,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
         if (!S.tA) { mm = e % GM; kk = e / GM; } else { kk = e % GK; mm = e / GK; }
         const int gm = m0 + mm, gk = k0 + kk;
         T v = 0;
-        if (gm < P.M && gk < S.K)
+        if (gm < P.M && gk < ke)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
       }
@@ -60,12 +76,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
         if (!S.tB) { kk = e % GK; nn = e / GK; } else { nn = e % GN; kk = e / GN; }
         const int gn = n0 + nn, gk = k0 + kk;
         T v = 0;
-        if (gn < P.N && gk < S.K)
+        if (gn < P.N && gk < ke)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
       }
       __syncthreads();
-      const int kc = min(GK, S.K - k0);   // no FMA on the padding of a short segment
+      const int kc = min(GK, ke - k0);   // no FMA on the padding of a short segment
 #pragma unroll 4
       for (int kk = 0; kk < kc; ++kk) {
         T a[4], b[4];
@@ -80,6 +96,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
       }
       __syncthreads();
     }
+  }
+  if (pout) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pout[(tx + 16 * j) * GM + ty + 16 * i] = acc[i][j];
+    return;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -102,11 +125,21 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProbT<T>* __restrict__ p
 template <class T, int NB>
 __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__ probs,
                                                 const GemmSegT<T>* __restrict__ segs,
-                                                const int4* __restrict__ tiles) {
+                                                const int4* __restrict__ tiles,
+                                                const int4* __restrict__ kparts,
+                                                T* __restrict__ partial) {
   constexpr int MB = 64, KB = 32, CPT = NB / 4;
   const int4 t = tiles[blockIdx.x];
   const GemmProbT<T> P = probs[t.x];
   const int m0 = t.y, n0 = t.z;
+  int klo = 0, khi = 0x7fffffff;
+  T* pout = nullptr;
+  if (t.w > 0) {   // a K part of a split tile (as in k_gemm)
+    const int4 kp = kparts[t.w - 1];
+    klo = kp.x;
+    khi = kp.y;
+    pout = partial + (int64_t)kp.z * (4 * MB);
+  }
   __shared__ T As[KB][MB + 1];
   __shared__ T Bs[KB][NB + 1];
   const int tid = threadIdx.x;
@@ -114,9 +147,12 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
   T acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) acc[c] = 0;
+  int kbase = 0;
   for (int sg = P.seg0; sg < P.seg1; ++sg) {
     const GemmSegT<T> S = segs[sg];
-    for (int k0 = 0; k0 < S.K; k0 += KB) {
+    const int ks = max(0, klo - kbase), ke = min(S.K, khi - kbase);
+    kbase += S.K;
+    for (int k0 = ks; k0 < ke; k0 += KB) {
 #pragma unroll
       for (int r = 0; r < (MB * KB) / 256; ++r) {
         const int e = tid + 256 * r;
@@ -124,7 +160,7 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
         if (!S.tA) { mm = e % MB; kk = e / MB; } else { kk = e % KB; mm = e / KB; }
         const int gm = m0 + mm, gk = k0 + kk;
         T v = 0;
-        if (gm < P.M && gk < S.K)
+        if (gm < P.M && gk < ke)
           v = S.tA ? S.A[gk + (int64_t)gm * S.lda] : S.A[gm + (int64_t)gk * S.lda];
         As[kk][mm] = v;
       }
@@ -133,12 +169,12 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
         if (!S.tB) { kk = e % KB; nn = e / KB; } else { nn = e % NB; kk = e / NB; }
         const int gn = n0 + nn, gk = k0 + kk;
         T v = 0;
-        if (gn < P.N && gk < S.K)
+        if (gn < P.N && gk < ke)
           v = S.tB ? S.B[gn + (int64_t)gk * S.ldb] : S.B[gk + (int64_t)gn * S.ldb];
         Bs[kk][nn] = v;
       }
       __syncthreads();
-      const int kc = min(KB, S.K - k0);   // no FMA on the padding of a short segment
+      const int kc = min(KB, ke - k0);   // no FMA on the padding of a short segment
 #pragma unroll 8
       for (int kk = 0; kk < kc; ++kk) {
         const T a = As[kk][row];
@@ -147,6 +183,11 @@ __global__ void __launch_bounds__(256) k_gemm_n(const GemmProbT<T>* __restrict__
       }
       __syncthreads();
     }
+  }
+  if (pout) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) pout[(cg * CPT + c) * MB + row] = acc[c];
+    return;
   }
   const int gm = m0 + row;
   if (gm < P.M) {
@@ -258,23 +299,27 @@ __global__ void __launch_bounds__(256) k_gemm_k(const GemmProbT<T>* __restrict__
   }
 }
 
-// the K parts of a split tile: out = alpha * (sum of the slots in order) + beta * out
-template <class T, int NB>
+// the K parts of a split tile: out = alpha * (sum of the parts in order) + beta * out.
+// nparts[i] = parts | (slot width << 8): a part covers width / 4 slots of 4 columns x 64
+// rows (4 for the up-to-4-column variants, the tile width otherwise), parts consecutive.
+template <class T>
 __global__ void __launch_bounds__(64) k_gemm_kreduce(const GemmProbT<T>* __restrict__ probs,
                                                      const int4* __restrict__ reds,
                                                      const int* __restrict__ nparts,
                                                      const T* __restrict__ partial) {
   constexpr int MB = 64;
   const int4 r = reds[blockIdx.x];   // (problem, m0, n0, first slot)
-  const int np = nparts[blockIdx.x];
+  const int np = nparts[blockIdx.x] & 255, w = nparts[blockIdx.x] >> 8;
   const GemmProbT<T> P = probs[r.x];
   const int row = threadIdx.x, gm = r.y + row;
   if (gm >= P.M) return;
-  for (int c = 0; c < NB; ++c) {
+  const int64_t stride = (int64_t)(w / 4) * (4 * MB);
+  for (int c = 0; c < w; ++c) {
     const int gn = r.z + c;
     if (gn >= P.N) break;
-    T v0 = partial[(int64_t)r.w * (4 * MB) + c * MB + row];
-    for (int q = 1; q < np; ++q) v0 += partial[(int64_t)(r.w + q) * (4 * MB) + c * MB + row];
+    const T* src = partial + (int64_t)r.w * (4 * MB) + c * MB + row;
+    T v0 = src[0];
+    for (int q = 1; q < np; ++q) v0 += src[q * stride];
     T* cp = P.tC ? P.C + gn + (int64_t)gm * P.ldc : P.C + gm + (int64_t)gn * P.ldc;
     T v = (T)P.alpha * v0;
     if (P.beta != 0.0) v += (T)P.beta * (*cp);
@@ -300,10 +345,10 @@ static void gemm_dispatch(int nb, int g, const GemmProbT<T>* pr, const GemmSegT<
     case 1: k_gemm_k<T, 1><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
     case 2: k_gemm_k<T, 2><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
     case 4: k_gemm_k<T, 4><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
-    case 8: k_gemm_n<T, 8><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 16: k_gemm_n<T, 16><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    case 32: k_gemm_n<T, 32><<<g, 256, 0, s>>>(pr, sg, tl); break;
-    default: k_gemm<T><<<g, 256, 0, s>>>(pr, sg, tl); break;
+    case 8: k_gemm_n<T, 8><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
+    case 16: k_gemm_n<T, 16><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
+    case 32: k_gemm_n<T, 32><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
+    default: k_gemm<T><<<g, 256, 0, s>>>(pr, sg, tl, kp, partial); break;
   }
 }
 
@@ -398,25 +443,32 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
     // problem depends on that problem alone (its tile count and K), never on the other
     // problems of the launch, so that a product gives the same bits whichever launch it is
     // part of (one instance alone, or many merged).
-    if (v >= 1 && v <= 4) {
+    // Wider products with few tiles and a long K (the coupling and pair products of small
+    // problems: one tile, K in the thousands) split the same way, into parts of at least
+    // 256 (the partial tile of a part is written once, for 2 x 64 x 256 FMAs per column).
+    {
+      const bool narrow = v >= 1 && v <= 4;
+      const int ws = narrow ? 4 : tn;            // slot width of a part
+      const int kmin = narrow ? 128 : 256;       // K per part at least
       std::vector<int4> nt;
       for (const int4& t : vt) {
         int K = 0;
         for (int g = lprobs[t.x].seg0; g < lprobs[t.x].seg1; ++g) K += lsegs[g].K;
-        const int64_t ptiles = ceil_div((int64_t)lprobs[t.x].M, (int64_t)tm);
+        const int64_t ptiles = ceil_div((int64_t)lprobs[t.x].M, (int64_t)tm) *
+                               (narrow ? 1 : ceil_div((int64_t)lprobs[t.x].N, (int64_t)tn));
         const int want = ptiles >= 2 * 152
                              ? 1
                              : (int)std::min<int64_t>(16, ceil_div((int64_t)4 * 152, ptiles));
-        const int kp = std::min(want, (K + 127) / 128);
+        const int kp = std::min(want, narrow ? (K + kmin - 1) / kmin : K / kmin);
         if (kp <= 1) { nt.push_back(t); continue; }
         reds.push_back(make_int4(t.x, t.y, t.z, slot));
-        rednp.push_back(kp);
+        rednp.push_back(kp | (ws << 8));
         for (int q = 0; q < kp; ++q) {
           const int lo = (int)((int64_t)K * q / kp), hi = (int)((int64_t)K * (q + 1) / kp);
-          kparts.push_back(make_int4(lo, hi, slot + q, 0));
+          kparts.push_back(make_int4(lo, hi, slot + q * (ws / 4), 0));
           nt.push_back(make_int4(t.x, t.y, t.z, (int)kparts.size()));
         }
-        slot += kp;
+        slot += kp * (ws / 4);
       }
       vt.swap(nt);
     }
@@ -440,7 +492,7 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
     d_kparts.upload(kparts, s);
     d_reds.upload(reds, s);
     d_rednp.upload(rednp, s);
-    // slots are sized for the widest split variant (4 columns)
+    // slots of 4 columns x 64 rows; a part of a wider tile takes width / 4 of them
     d_partial.alloc(std::max(slot, 1) * (size_t)4 * 64);
   }
   d_segs.upload(lsegs, s);
@@ -506,8 +558,8 @@ void GemmBatchT<T>::launch(cudaStream_t s) const {
   }
   if (!reds.empty()) {
     // the reduction reads the slots with the 4-column stride used for every split variant
-    k_gemm_kreduce<T, 4><<<(unsigned)reds.size(), 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p,
-                                                                d_partial.p);
+    k_gemm_kreduce<T><<<(unsigned)reds.size(), 64, 0, s>>>(d_probs.p, d_reds.p, d_rednp.p,
+                                                            d_partial.p);
     SPD_LAUNCHED();
   }
 }
