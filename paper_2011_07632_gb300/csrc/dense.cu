@@ -424,6 +424,7 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
   }
   // tiles grouped by variant
   static const int kVariants[7] = {1, 2, 4, 8, 16, 32, 0};
+  std::vector<int> kt;   // K of every launched problem (filled on first use)
   kparts.clear();
   reds.clear();
   rednp.clear();
@@ -472,16 +473,28 @@ void GemmBatchT<T>::upload(cudaStream_t s) {
       }
       vt.swap(nt);
     }
-    // longest K first, so that the long tiles do not form the tail of the launch
+    // longest K first, so that the long tiles do not form the tail of the launch: a
+    // counting sort by the power of two of K (the order only schedules: every tile's
+    // arithmetic is its own)
     {
-      std::vector<int> kt(lprobs.size(), 0);
-      for (int q = 0; q < (int)lprobs.size(); ++q)
-        for (int g = lprobs[q].seg0; g < lprobs[q].seg1; ++g) kt[q] += lsegs[g].K;
-      auto klen = [&](const int4& t) {
-        return t.w > 0 ? kparts[t.w - 1].y - kparts[t.w - 1].x : kt[t.x];
+      if (kt.empty()) {
+        kt.assign(lprobs.size(), 0);
+        for (int q = 0; q < (int)lprobs.size(); ++q)
+          for (int g = lprobs[q].seg0; g < lprobs[q].seg1; ++g) kt[q] += lsegs[g].K;
+      }
+      auto bucket = [&](const int4& t) {
+        const int k = t.w > 0 ? kparts[t.w - 1].y - kparts[t.w - 1].x : kt[t.x];
+        int b = 0;
+        while (b < 31 && (1 << b) < k) ++b;
+        return 31 - b;   // long K first
       };
-      std::stable_sort(vt.begin(), vt.end(),
-                       [&](const int4& x, const int4& y) { return klen(x) > klen(y); });
+      int cnt[33] = {0};
+      std::vector<unsigned char> bk(vt.size());
+      for (size_t q = 0; q < vt.size(); ++q) { bk[q] = (unsigned char)bucket(vt[q]); ++cnt[bk[q] + 1]; }
+      for (int b = 0; b < 32; ++b) cnt[b + 1] += cnt[b];
+      std::vector<int4> sorted(vt.size());
+      for (size_t q = 0; q < vt.size(); ++q) sorted[cnt[bk[q]]++] = vt[q];
+      vt.swap(sorted);
     }
     vnb.push_back(v);
     vbeg.push_back((int64_t)tiles.size());
@@ -979,7 +992,7 @@ __global__ void k_trsm_synth(double* __restrict__ T, int n, int64_t count, doubl
 }
 
 // Time of the blocked TRSM with v columns per CTA on `count` synthetic n x n problems of
-// ncol columns (private stream, CUDA events, three launches after a warm-up).
+// ncol columns (private stream, CUDA events, two launches after a warm-up).
 static double trsm_time_variant(int v, int n, int ncol, int count) {
   cudaStream_t ps;
   SPD_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
@@ -1013,12 +1026,12 @@ static double trsm_time_variant(int v, int n, int ncol, int count) {
     SPD_CUDA(cudaEventCreate(&e0));
     SPD_CUDA(cudaEventCreate(&e1));
     SPD_CUDA(cudaEventRecord(e0, ps));
-    for (int r = 0; r < 3; ++r) go();
+    for (int r = 0; r < 2; ++r) go();
     SPD_CUDA(cudaEventRecord(e1, ps));
     SPD_CUDA(cudaEventSynchronize(e1));
     float f = 0.f;
     SPD_CUDA(cudaEventElapsedTime(&f, e0, e1));
-    ms = f / 3.0;
+    ms = f / 2.0;
   } catch (...) {
     ms = -1.0;
     cudaGetLastError();
@@ -1064,8 +1077,9 @@ static std::vector<int2> trsm_work(const Batch<TrsmProb>& b, int* variant, size_
       if (v <= cw) cands.push_back(v);
     const std::string key = "trsm_blk n" + std::to_string(bn) + " c" + std::to_string(bc) +
                             " p" + std::to_string(bp);
-    const int64_t fit = std::max<int64_t>(1, (int64_t(256) << 20) / ((int64_t)maxn * maxn * 8));
-    const int count = (int)std::min<int64_t>(bp, fit);
+    // the synthetic set: the bucket's problem count, at most 512 problems and 32 MB
+    const int64_t fit = std::max<int64_t>(1, (int64_t(32) << 20) / ((int64_t)maxn * maxn * 8));
+    const int count = (int)std::min<int64_t>(std::min<int64_t>(bp, 512), fit);
     const int tn = maxn, tc = maxc;
     cw = tuned_variant(key, cands, cw, [&](int v) { return trsm_time_variant(v, tn, tc, count); });
   }
