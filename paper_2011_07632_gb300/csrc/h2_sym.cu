@@ -381,15 +381,17 @@ static int sym_nc(int ncol) {
 }
 static int64_t align4(int64_t x) { return (x + 3) & ~int64_t(3); }
 
-// rows per job (multiple of 128, at most 512); SPDHSS_SYM_ROW_BLOCK selects 128 or 256
-// to exercise the row-split path on small problems
+// rows per job (multiple of 128, at most 512): 256 measured fastest on GB300 (n = 200,000
+// Gaussian, 8 columns: 11.0 ms against 11.7 ms for 512, 11.0 ms for 128: fewer idle
+// slices in a job, for partial sums over more row parts); SPDHSS_SYM_ROW_BLOCK selects
+// 128, 256 or 512
 static int sym_row_block() {
   const char* e = std::getenv("SPDHSS_SYM_ROW_BLOCK");
   if (e) {
     const int v = std::atoi(e);
     if (v == 128 || v == 256 || v == 512) return v;
   }
-  return 512;
+  return 256;
 }
 
 // columns per stage for a job of R rows: a multiple of CG x teams, a power of two,

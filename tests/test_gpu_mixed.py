@@ -46,12 +46,11 @@ def test_mixed_pcg_reaches_fp64_tolerance(nrhs):
 
 
 @pytest.mark.parametrize("nrhs,row_block", [(3, None), (8, None), (16, None), (8, "128"),
-                                            (13, "256")])
+                                            (13, "512")])
 def test_fp32_product_split_rows(nrhs, row_block, monkeypatch):
     """High-rank nodes (ranks and transfer-matrix heights above the 128-512 rows of one
     job): the FP32 product then splits their rows over several jobs and adds the partial
-    results in a fixed order.  SPDHSS_SYM_ROW_BLOCK lowers the rows per job so that every
-    level takes the split path."""
+    results in a fixed order.  SPDHSS_SYM_ROW_BLOCK sets the rows per job (default 256)."""
     api = need_gpu()
     if row_block:
         monkeypatch.setenv("SPDHSS_SYM_ROW_BLOCK", row_block)
@@ -60,7 +59,7 @@ def test_fp32_product_split_rows(nrhs, row_block, monkeypatch):
     h = api.H2(X, "gauss", 0.1, 1e-4, 128, 1e-8)
     off, _ = h.export_skeletons()
     k = np.diff(off)
-    assert k.max() > int(row_block or 512) // 2
+    assert k.max() > int(row_block or 256) // 2
     x = inputs.rhs(n, nrhs, 12)
     y64 = h.matmul(x).cpu().numpy()
     y32 = h.matmul_mixed(x).cpu().numpy()
