@@ -705,8 +705,8 @@ def serving_comparison(count, waves_only_stats=False):
     ell=0.1}; shift 1e-3; rank 50; 1..16 right-hand sides) served two ways on the same GPU:
     plain FP64, one request at a time; and the served mixed-precision batched form (waves
     of the requests admitted meanwhile, merged construction launches with the tensor-core
-    sampling, lockstep FP64 PCG, two waves overlapping).  Latency = arrival to last
-    solution on the host."""
+    sampling, lockstep PCG with the FP32 H^2 products merged over the wave, two waves
+    overlapping).  Latency = arrival to last solution on the host."""
     import torch
     from paper_2011_07632_gb300 import serve
     reqs = serve.synthetic_stream(count, rate=200.0, n_lo=1000, n_hi=16000, seed=1)
@@ -727,7 +727,8 @@ def serving_comparison(count, waves_only_stats=False):
             "speedup_requests_per_s": stw["requests_per_s"] / st1["requests_per_s"],
             "p99_ratio": stw["p99_latency_s"] / st1["p99_latency_s"],
             "max_rel_diff_mixed_vs_fp64_solutions": diff,
-            "pcg_iters_fp64": [int(np.max(r.iters[0])) for r in one if r.iters]}
+            "pcg_iters_fp64": [int(np.max(r.iters[0])) for r in one if r.iters],
+            "pcg_iters_mixed": [int(np.max(r.iters[0])) for r in wav if r.iters]}
 
 
 def run_serve(count):
@@ -767,7 +768,8 @@ def batch_instances(count, seed=3):
 
 def run_batch(count):
     """Batched level sweep (spdhss_build_batched + pcg_solve_batched) against the same
-    instances built and solved one at a time on the same stream."""
+    instances built and solved one at a time on the same stream; then the batched solve
+    with FP32 products (pcg_solve_batched_mixed) on the same construction."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -777,13 +779,13 @@ def run_batch(count):
                 rhs=torch.from_numpy(np.ascontiguousarray(i["rhs"])).cuda()) for i in insts]
     torch.cuda.synchronize()
 
-    def batched(ins):
+    def batched(ins, mixed=False):
         t0 = time.perf_counter()
         built, st, stats = api.build_batched(ins)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         X, its, rrs, st2 = api.pcg_solve_batched([b[0] for b in built], [b[2] for b in built],
-                                                 [i["rhs"] for i in ins], tol=1e-6)
+                                                 [i["rhs"] for i in ins], tol=1e-6, mixed=mixed)
         torch.cuda.synchronize()
         return built, st, stats, X, its, st2, t1 - t0, time.perf_counter() - t1
 
@@ -821,6 +823,15 @@ def run_batch(count):
     t_s = time.perf_counter() - t0
     c3 = native.launch_count()
     diff = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(xb, xs))
+    batched(dev[:4], mixed=True)         # warm-up of the FP32 plans' first use
+    c4 = native.launch_count()
+    built_m, st_m, _, X_m, its_m, st2_m, tb_m, ts_m = batched(dev, mixed=True)
+    c5 = native.launch_count()
+    xm = [x.cpu().numpy() for x in X_m]
+    del built_m, X_m
+    diff_m = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                 for a, b in zip(xm, xb))
+    im = [int(v[0]) for v in its_m]
     # device time of the batched kernels (library CUDA events), one more batched pass
     native.lib().spdhss_profile(1)
     res = batched(dev)
@@ -843,6 +854,11 @@ def run_batch(count):
         "pcg_iters": {"batched_max": max(ib), "single_max": max(its_s),
                       "max_abs_diff": max(abs(a - b) for a, b in zip(ib, its_s))},
         "max_rel_diff_batched_vs_single": diff,
+        "batched_mixed_pcg": {"solve_s": ts_m, "build_s": tb_m, "gpu_launches": c5 - c4,
+                              "converged": sum(v == native.OK for v in st2_m),
+                              "iters_max": max(im),
+                              "iters_max_abs_diff_vs_fp64": max(abs(a - b) for a, b in zip(im, ib)),
+                              "max_rel_diff_vs_fp64_solutions": diff_m},
         "batched_kernel_s": busy,
         "batched_top_kernels_ms": {k: round(v["ms"], 1) for k, v in top},
         "n_total": int(sum(i["points"].shape[0] for i in insts)),

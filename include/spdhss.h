@@ -311,7 +311,14 @@ spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, int64_t lda, 
  *   iters_out[i] / relres_out[i]: HOST arrays of nrhs[i] entries or NULL), the iterations
  *   of all instances in lockstep from one host thread: every stage of an iteration is one
  *   launch over all instances still iterating (an instance leaves when it has converged).
- *   status[i] per instance (NO_CONVERGENCE for one that missed the tolerance). */
+ *   status[i] per instance (NO_CONVERGENCE for one that missed the tolerance).
+ * pcg_solve_batched_mixed: pcg_solve_mixed for every instance in the same lockstep (the
+ *   precision mode's solve, Sec. 6.2 with FP32 products): the FP32 H^2 products of all
+ *   instances still iterating run as merged launches of their once-read plans, the ULV
+ *   solves, recurrences, FP64 true residuals (every 50 iterations and at convergence) and
+ *   the convergence test are those of pcg_solve_mixed.  Arguments as pcg_solve_batched,
+ *   nrhs[i] in [1, 16]; every instance's X, iterations and residuals are bit-identical to
+ *   its pcg_solve_mixed call. */
 spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
@@ -325,6 +332,12 @@ spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle
                                 const int64_t* ld, double relres_tol, int maxit,
                                 int* const* iters_out, double* const* relres_out, void* stream,
                                 spdhss_status* status);
+spdhss_status pcg_solve_batched_mixed(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                      const double* const* B, double* const* X,
+                                      const int* nrhs, const int64_t* ld, double relres_tol,
+                                      int maxit, int* const* iters_out,
+                                      double* const* relres_out, void* stream,
+                                      spdhss_status* status);
 /* Launches issued by the last batched call of the calling thread: merged[0] = launches of
  * the batched kernels after merging, merged[1] = the hand-overs they replaced. */
 void spdhss_batched_stats(int64_t* merged);

@@ -311,8 +311,10 @@ def build_batched(instances, stream=None):
     return out, [int(v) for v in st], (int(stats[0]), int(stats[1]))
 
 
-def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, stream=None):
-    """pcg_solve for every instance with the iterations in lockstep (pcg_solve_batched).
+def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, stream=None,
+                      mixed: bool = False):
+    """pcg_solve for every instance with the iterations in lockstep (pcg_solve_batched;
+    mixed=True: pcg_solve_mixed per instance, pcg_solve_batched_mixed, at most 16 columns).
     Bs: device tensors or arrays (n_i, nrhs_i).  Returns (list of X (n_i, nrhs_i) device
     tensors, list of iteration arrays, list of relres arrays, per-instance status codes)."""
     m = len(h2s)
@@ -324,7 +326,8 @@ def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, strea
     P = ctypes.c_void_p * m
     ld = np.array([h.n for h in h2s], np.int64)
     st = (ctypes.c_int * m)()
-    rc = N.lib().pcg_solve_batched(
+    fn = N.lib().pcg_solve_batched_mixed if mixed else N.lib().pcg_solve_batched
+    rc = fn(
         m, P(*[h._h.value for h in h2s]), P(*[u._h.value for u in ulvs]),
         P(*[b.data_ptr() for b in Bc]), P(*[x.data_ptr() for x in Xc]),
         (ctypes.c_int * m)(*nrhs), _i64(ld), float(tol), int(maxit),

@@ -498,7 +498,8 @@ void h2_matmul_mixed_impl(spdhss_h2_s* h2, const double* X, double* Y, int nrhs,
 void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ulv,
                       const double* const* B, double* const* X, const int* nrhs,
                       const int64_t* ld, double tol, int maxit, int* const* iters_out,
-                      double* const* relres_out, spdhss_status* status, cudaStream_t s);
+                      double* const* relres_out, spdhss_status* status, cudaStream_t s,
+                      int precision);
 }
 
 extern "C" {
@@ -688,15 +689,18 @@ spdhss_status spdhss_build_batched(int count, const double* const* points, const
   return batched_result("spdhss_build_batched", st, msg, status);
 }
 
-spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,
-                                const double* const* B, double* const* X, const int* nrhs,
-                                const int64_t* ld, double relres_tol, int maxit,
-                                int* const* iters_out, double* const* relres_out, void* stream,
-                                spdhss_status* status) {
+// pcg_solve_batched and pcg_solve_batched_mixed (precision 1: FP32 products)
+static spdhss_status pcg_batched_entry(const char* where, int precision, int count,
+                                       const h2_handle* h2, const ulv_handle* ulv,
+                                       const double* const* B, double* const* X,
+                                       const int* nrhs, const int64_t* ld, double relres_tol,
+                                       int maxit, int* const* iters_out,
+                                       double* const* relres_out, void* stream,
+                                       spdhss_status* status) {
   std::vector<spdhss_status> st;
   std::vector<std::string> msg;
   cudaStream_t s = (cudaStream_t)stream;
-  const spdhss_status outer = guarded("pcg_solve_batched", [&] {
+  const spdhss_status outer = guarded(where, [&] {
     SPD_REQUIRE(count >= 1, "count must be >= 1");
     SPD_REQUIRE(h2 && ulv && B && X && nrhs && ld, "NULL argument");
     SPD_REQUIRE(relres_tol > 0.0, "relres_tol must be > 0");
@@ -708,17 +712,37 @@ spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle
       SPD_REQUIRE(h2[i] && ulv[i] && B[i] && X[i], "NULL argument");
       SPD_REQUIRE(ulv[i]->hs->h2 == h2[i], "the ULV factorization belongs to another H2 matrix");
       SPD_REQUIRE(nrhs[i] >= 1, "nrhs must be >= 1");
+      SPD_REQUIRE(!precision || nrhs[i] <= 16, "nrhs must be in [1, 16]");
       SPD_REQUIRE(ld[i] >= h2[i]->th.n, "ld must be >= n");
     }
     std::vector<spdhss_h2_s*> hv(h2, h2 + count);
     std::vector<spdhss_ulv_s*> uv(ulv, ulv + count);
     pcg_batched_impl(count, hv.data(), uv.data(), B, X, nrhs, ld, relres_tol, maxit, iters_out,
-                     relres_out, st.data(), s);
+                     relres_out, st.data(), s, precision);
     for (int i = 0; i < count; ++i)
       if (st[i] == SPDHSS_NO_CONVERGENCE) msg[i] = "some column missed the tolerance";
   });
   if (outer != SPDHSS_OK) return outer;
-  return batched_result("pcg_solve_batched", st, msg, status);
+  return batched_result(where, st, msg, status);
+}
+
+spdhss_status pcg_solve_batched(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                const double* const* B, double* const* X, const int* nrhs,
+                                const int64_t* ld, double relres_tol, int maxit,
+                                int* const* iters_out, double* const* relres_out, void* stream,
+                                spdhss_status* status) {
+  return pcg_batched_entry("pcg_solve_batched", 0, count, h2, ulv, B, X, nrhs, ld, relres_tol,
+                           maxit, iters_out, relres_out, stream, status);
+}
+
+spdhss_status pcg_solve_batched_mixed(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                      const double* const* B, double* const* X,
+                                      const int* nrhs, const int64_t* ld, double relres_tol,
+                                      int maxit, int* const* iters_out,
+                                      double* const* relres_out, void* stream,
+                                      spdhss_status* status) {
+  return pcg_batched_entry("pcg_solve_batched_mixed", 1, count, h2, ulv, B, X, nrhs, ld,
+                           relres_tol, maxit, iters_out, relres_out, stream, status);
 }
 
 void spdhss_batched_stats(int64_t* merged) {

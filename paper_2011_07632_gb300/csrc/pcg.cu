@@ -7,6 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <memory>
+#include <utility>
 
 #include "ulv.cuh"
 
@@ -263,6 +266,14 @@ struct PcgGraph {
     if (g) cudaGraphDestroy(g);
   }
   bool ready() const { return ex != nullptr; }
+  // forget the captured iteration (its launches changed); the next steady one re-captures
+  void reset() {
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    ex = nullptr;
+    g = nullptr;
+    tried = false;
+  }
   template <class F>
   void capture(cudaStream_t s, F&& body) {
     if (tried) return;
@@ -301,10 +312,48 @@ struct PcgGraph {
   }
 };
 
+// At a residual refresh of the mixed-precision solve: a column still iterating whose FP64
+// true residual is more than twice its recursive one (the FP32 recursion no longer describes
+// the FP64 residual: the FP32 product's error, relative to the residual, has become
+// comparable to the residual itself, as for kernel matrices of large condition number)
+// also restarts its direction (beta = 0, flag 2).  Its iteration then proceeds as
+// iterative refinement: every block of iterations is an inner PCG for A d = r with the
+// FP32 product, started from the FP64 residual.  Columns whose recursion still holds keep
+// their direction (plain residual replacement).  Returns whether a flag changed.
+static bool refresh_restarts(const std::vector<double>& trel, const std::vector<double>& rr,
+                             const std::vector<double>& bn, std::vector<int>& hdone) {
+  bool any = false;
+  for (size_t c = 0; c < hdone.size(); ++c) {
+    if (hdone[c] != 0) continue;
+    if (trel[c] > 2.0 * std::sqrt(std::max(rr[c], 0.0)) / bn[c]) {
+      hdone[c] = 2;
+      any = true;
+    }
+  }
+  return any;
+}
+
+// At a residual refresh of the mixed-precision solve: whether a column still iterating has
+// a true residual above 0.9 of its value at the previous refresh (a whole block of
+// iterations without progress: the FP32 product's error relative to the residual is too
+// large for the refinement to contract).  The solve then takes FP64 products from here on,
+// every column restarting its direction.  tprev is updated to trel.
+static bool refresh_stalled(const std::vector<double>& trel, std::vector<double>& tprev,
+                            const std::vector<int>& hdone) {
+  bool stalled = false;
+  for (size_t c = 0; c < hdone.size(); ++c) {
+    if (hdone[c] == 0 && trel[c] > 0.9 * tprev[c]) stalled = true;
+    tprev[c] = trel[c];
+  }
+  return stalled;
+}
+
 // precision = 0: FP64 throughout.  precision = 1: the product with A inside the iteration
 // uses the FP32 copy of the H^2 matrix (FP32 kernel entries and accumulation); the ULV
 // preconditioner, the recurrences and every residual check stay FP64, and every
-// `refresh` iterations the recursive residual is replaced by the FP64 true residual.
+// `refresh` iterations the recursive residual is replaced by the FP64 true residual
+// (restarting the columns whose recursion has drifted, refresh_restarts; switching to FP64
+// products when a block of iterations made no progress, refresh_stalled).
 void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* X, int nrhs,
               int64_t ld, double tol, int maxit, int* iters_out, double* relres_out,
               bool& converged, cudaStream_t s, int precision = 0, int refresh = 50) {
@@ -363,6 +412,7 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
   }
   std::vector<int> hdone(nrhs, 0), hit(nrhs, 0);
   for (int c = 0; c < nrhs; ++c) hdone[c] = 0;
+  std::vector<double> tprev(nrhs, INFINITY);   // true residuals at the previous refresh
   // z = M^{-1} r, p = z, rz = r.z
   copy_vec(z, r.p, nc, s);
   if (PU) ulv_solve_sorted(u, *PU, s);
@@ -450,6 +500,18 @@ void pcg_impl(const spdhss_h2_s* h2c, spdhss_ulv_s* u, const double* B, double* 
       std::vector<double> trel;
       true_residual(trel, false);
       copy_vec(r.p, PR.ys.p, nc, s);
+      bool flags = false;
+      if (refresh_stalled(trel, tprev, hdone)) {
+        PF = nullptr;                               // FP64 products from here on
+        for (int c = 0; c < nrhs; ++c)
+          if (hdone[c] == 0) hdone[c] = 2;
+        graph.reset();
+        flags = true;
+      } else {
+        flags = refresh_restarts(trel, hrr, bn, hdone);
+      }
+      if (flags)
+        SPD_CUDA(cudaMemcpyAsync(done.p, hdone.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     }
     bool restart = false;
     for (int c = 0; c < nrhs; ++c) restart = restart || hdone[c] == 2;
@@ -542,6 +604,9 @@ struct Inst {
   H2Plan* PA = nullptr;
   H2Plan* PR = nullptr;
   UlvPlan* PU = nullptr;
+  H2PlanF* PF = nullptr;      // mixed precision: the FP32 plan of q = A p
+  bool fp64 = false;          // mixed precision: switched to FP64 products (refresh_stalled)
+  std::vector<double> tprev;  // mixed precision: true residuals at the previous refresh
   int64_t n = 0, ld = 0;
   int nrhs = 0, D = 0, nlev = 0;
   const double* B = nullptr;
@@ -583,7 +648,10 @@ CopyProb vcopy(double* dst, const double* src, int64_t count) {
   return c;
 }
 
-void build_merged(std::vector<Inst>& I, const Pools& pl, Merged& M, cudaStream_t s) {
+// mixed: the FP64 product steps only of the instances switched to FP64 products (the
+// others take q = A p from MergedF)
+void build_merged(std::vector<Inst>& I, const Pools& pl, Merged& M, cudaStream_t s,
+                  bool mixed = false) {
   M = Merged();
   int maxD = 0, maxlev = 0;
   for (auto& a : I)
@@ -599,18 +667,20 @@ void build_merged(std::vector<Inst>& I, const Pools& pl, Merged& M, cudaStream_t
     if (!a.active) continue;
     const H2Plan& P = *a.PA;
     const int64_t nc = a.n * a.nrhs;
-    gemm_cat(M.up_leaf, P.up_leaf);
-    for (size_t h = 0; h < P.up.size(); ++h) gemm_cat(M.up[h], P.up[h]);
-    // down[t] is depth t + 1, at height nd - t above the leaves; merged top first
-    const int nd = (int)P.down.size();
-    for (int t = 0; t < nd; ++t) gemm_cat(M.down[(maxD - 1) - (nd - t)], P.down[t]);
-    gemm_cat(M.leaf_out, P.leaf_out);
-    if (P.use_rowcoup) rowcoup_cat(M.rowcoup, P.rowcoup);
-    else gemm_cat(M.coupling, P.coupling);
-    if (P.near_rows) rowcoup_cat(M.near_r, P.near_r);
-    else if (P.near_stored) gemm_cat(M.near_g, P.near_g);
-    else M.near_direct.push_back(k);
-    if (P.yhat.n > 0) M.zero_yhat.push(vcopy(P.yhat.p, nullptr, (int64_t)P.yhat.n));
+    if (!mixed || a.fp64) {
+      gemm_cat(M.up_leaf, P.up_leaf);
+      for (size_t h = 0; h < P.up.size(); ++h) gemm_cat(M.up[h], P.up[h]);
+      // down[t] is depth t + 1, at height nd - t above the leaves; merged top first
+      const int nd = (int)P.down.size();
+      for (int t = 0; t < nd; ++t) gemm_cat(M.down[(maxD - 1) - (nd - t)], P.down[t]);
+      gemm_cat(M.leaf_out, P.leaf_out);
+      if (P.use_rowcoup) rowcoup_cat(M.rowcoup, P.rowcoup);
+      else gemm_cat(M.coupling, P.coupling);
+      if (P.near_rows) rowcoup_cat(M.near_r, P.near_r);
+      else if (P.near_stored) gemm_cat(M.near_g, P.near_g);
+      else M.near_direct.push_back(k);
+      if (P.yhat.n > 0) M.zero_yhat.push(vcopy(P.yhat.p, nullptr, (int64_t)P.yhat.n));
+    }
     // ULV solve by level from the leaves; every root after every forward level
     const UlvPlan& U = *a.PU;
     for (int l = 0; l < a.nlev; ++l) {
@@ -683,12 +753,151 @@ void run_ulv_merged(const Merged& M, cudaStream_t s) {
   }
 }
 
+// FP64 <-> FP32 copies of several instances' vectors in one launch, element by element
+// with the rounding of convert_d2f / convert_f2d
+struct ConvProb {
+  double* d;
+  float* f;
+  int64_t count;
+};
+
+__global__ void k_convert_b(const ConvProb* __restrict__ probs, int to_float) {
+  const ConvProb P = probs[blockIdx.y];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (to_float) P.f[e] = (float)P.d[e];
+    else P.d[e] = (double)P.f[e];
+  }
+}
+
+// q = A p in FP32 for all instances of a mixed solve.  Step t of every instance's once-read
+// plan (its upward levels with their partial sums, the couplings and their sums, its
+// downward levels) goes into one launch per column count, the near fields into one launch
+// per kernel kind and column block.  Every job, sum and near-field problem keeps its own
+// arithmetic (the jobs are independent, each output entry is summed by one thread in a
+// fixed order, the near-field problems keep the column block and segment split of their
+// own plan), so each instance's product is bit-identical to h2_plan_run of its FP32 plan.
+// Instances whose FP32 plan has no once-read form run that plan on their own.
+struct MergedF {
+  std::vector<std::map<int, std::unique_ptr<SymBatch>>> sym;   // per step, by column count
+  std::vector<std::unique_ptr<SymSumBatch>> sum;                // per step
+  std::map<std::pair<int, int>, std::unique_ptr<NearBatchT<float>>> near;   // (kind, cb)
+  std::vector<int> direct;
+  std::vector<ConvProb> to_f, to_d;
+  DevBuf<ConvProb> d_to_f, d_to_d;
+  int64_t max_count = 0;
+};
+
+void build_merged_f(const std::vector<Inst>& I, MergedF& F, cudaStream_t s) {
+  for (int k = 0; k < (int)I.size(); ++k) {
+    const Inst& a = I[k];
+    if (!a.active || a.fp64) continue;
+    const H2PlanF& P = *a.PF;
+    const int64_t nc = a.n * a.nrhs;
+    F.to_f.push_back(ConvProb{a.PA->xs.p, P.xs.p, nc});
+    F.to_d.push_back(ConvProb{a.PA->ys.p, P.ys.p, nc});
+    F.max_count = std::max(F.max_count, nc);
+    if (!P.sym) { F.direct.push_back(k); continue; }
+    const std::vector<PlanStep>& steps = P.sym->steps;
+    if (F.sym.size() < steps.size()) {
+      F.sym.resize(steps.size());
+      F.sum.resize(steps.size());
+    }
+    for (size_t t = 0; t < steps.size(); ++t) {
+      const SymBatch* b = steps[t].sym.get();
+      if (b && !b->jobs.empty()) {
+        std::unique_ptr<SymBatch>& m = F.sym[t][b->nc];
+        if (!m) {
+          m.reset(new SymBatch());
+          m->nc = b->nc;
+          m->ncol = b->ncol;
+          m->tag = b->tag;
+        }
+        m->jobs.insert(m->jobs.end(), b->jobs.begin(), b->jobs.end());
+        m->ncol = std::max(m->ncol, b->ncol);
+        m->bytes += b->bytes;
+        m->flops += b->flops;
+      }
+      const SymSumBatch* u = steps[t].sum.get();
+      if (u && !u->jobs.empty()) {
+        std::unique_ptr<SymSumBatch>& m = F.sum[t];
+        if (!m) {
+          m.reset(new SymSumBatch());
+          m->ncol = u->ncol;
+          m->tag = u->tag;
+        }
+        const int off = (int)m->srcs.size();
+        m->srcs.insert(m->srcs.end(), u->srcs.begin(), u->srcs.end());
+        for (SymSum j : u->jobs) {
+          j.s0 += off;
+          j.s1 += off;
+          m->jobs.push_back(j);
+        }
+        m->ncol = std::max(m->ncol, u->ncol);
+        m->bytes += u->bytes;
+      }
+    }
+    // the near field as its own launch gets it: the instance's points and kernel parameters
+    for (NearProbT<float> p : P.near.probs) {
+      SPD_REQUIRE(p.cb != 0, "mixed batched PCG: FP32 near-field plan not uploaded");
+      if (!p.xs) {
+        p.xs = a.h2->td.xs.p;
+        p.ldx = a.h2->th.n;
+        p.dim = a.h2->th.dim;
+        p.inv_ell = a.h2->kfn.inv_ell;
+        p.shift = a.h2->kfn.shift;
+      }
+      std::unique_ptr<NearBatchT<float>>& m = F.near[std::make_pair(a.h2->kfn.kind, p.cb)];
+      if (!m) {
+        m.reset(new NearBatchT<float>());
+        m->tag = P.near.tag;
+      }
+      const int so = (int)m->segs.size();
+      m->segs.insert(m->segs.end(), P.near.segs.begin() + p.seg0, P.near.segs.begin() + p.seg1);
+      p.seg1 = so + (p.seg1 - p.seg0);
+      p.seg0 = so;
+      m->probs.push_back(p);
+    }
+  }
+  for (auto& st : F.sym)
+    for (auto& kv : st) kv.second->upload(s);
+  for (auto& u : F.sum)
+    if (u) u->upload(s);
+  for (auto& kv : F.near) kv.second->upload(s);
+  F.d_to_f.upload(F.to_f, s);
+  F.d_to_d.upload(F.to_d, s);
+}
+
+void convert_merged(const MergedF& F, bool to_float, cudaStream_t s) {
+  if (F.to_f.empty()) return;
+  const unsigned gx = (unsigned)std::min<int64_t>(ceil_div(F.max_count, 256), 152 * 16);
+  k_convert_b<<<dim3(gx, (unsigned)F.to_f.size()), 256, 0, s>>>(
+      to_float ? F.d_to_f.p : F.d_to_d.p, to_float ? 1 : 0);
+  SPD_LAUNCHED();
+}
+
+void run_h2_merged_f(const std::vector<Inst>& I, const MergedF& F, cudaStream_t s) {
+  convert_merged(F, true, s);
+  for (size_t t = 0; t < F.sym.size(); ++t) {
+    for (const auto& kv : F.sym[t]) kv.second->launch(s);
+    if (F.sum[t]) F.sum[t]->launch(s);
+  }
+  for (const auto& kv : F.near) {
+    KernelFn k{};
+    k.kind = kv.first.first;
+    kv.second->launch(k, nullptr, 0, 0, s);
+  }
+  for (int k : F.direct) h2_plan_run(I[k].h2, *I[k].PF, s);
+  convert_merged(F, false, s);
+}
+
 }  // namespace
 
 void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ulv,
                       const double* const* B, double* const* X, const int* nrhs,
                       const int64_t* ld, double tol, int maxit, int* const* iters_out,
-                      double* const* relres_out, spdhss_status* status, cudaStream_t s) {
+                      double* const* relres_out, spdhss_status* status, cudaStream_t s,
+                      int precision) {
   std::vector<Inst> I(count);
   Pools pl;
   for (int k = 0; k < count; ++k) {
@@ -716,6 +925,8 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
     a.PA = get_plan(a.nrhs);
     a.PR = get_plan(-a.nrhs);
     a.PU = &ulv_plan(a.u, a.nrhs, s);
+    if (precision) a.PF = &h2_plan_f(a.h2, a.nrhs, s);
+    a.tprev.assign(a.nrhs, INFINITY);
   }
   pl.sc.alloc((size_t)std::max<int64_t>(4 * pl.NC, 1));
   pl.done.alloc((size_t)std::max<int64_t>(pl.NC, 1));
@@ -772,7 +983,12 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
     for (int c = 0; c < a.nrhs; ++c) rel[c] = std::sqrt(std::max(h[c], 0.0)) / a.bn[c];
   };
   Merged M;
-  build_merged(I, pl, M, s);
+  build_merged(I, pl, M, s, precision != 0);
+  std::unique_ptr<MergedF> F;
+  if (precision) {
+    F.reset(new MergedF());
+    build_merged_f(I, *F, s);
+  }
   std::vector<double> hrr(pl.NC);
   int nactive = count;
   // Converged instances stay in the merged launches (their updates are masked by the done
@@ -781,6 +997,7 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
   int merged_active = count;
   for (int it = 1; it <= maxit && nactive > 0; ++it) {
     run_h2_merged(I, M, s);                                   // q = A p
+    if (F) run_h2_merged_f(I, *F, s);                         // ... in FP32 where mixed
     { std::vector<DotProb> v = M.d_pq; dots_merged(v, s); }
     { std::vector<VecProb> v = M.v_axpy; vec_merged(v, s); }
     { std::vector<DotProb> v = M.d_rr; dots_merged(v, s); }
@@ -821,8 +1038,37 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
       if (all) { a.active = false; --nactive; changed_set = true; }
     }
     if (nactive == 0) break;
-    if (changed_set && 3 * nactive <= 2 * merged_active) {
-      build_merged(I, pl, M, s);
+    // mixed precision: every 50 iterations the recursive residual of each instance still
+    // iterating on FP32 products is replaced by its FP64 true residual b - A x, with the
+    // restarts and the switch to FP64 products of pcg_impl
+    bool switched = false;
+    if (F && it % 50 == 0)
+      for (auto& a : I) {
+        if (!a.active || a.fp64) continue;
+        std::vector<double> trel;
+        true_residual(a, trel);
+        copy_vec(a.r.p, a.PR->ys.p, a.n * a.nrhs, s);
+        bool flags = false;
+        if (refresh_stalled(trel, a.tprev, a.hdone)) {
+          a.fp64 = true;
+          switched = true;
+          for (int c = 0; c < a.nrhs; ++c)
+            if (a.hdone[c] == 0) a.hdone[c] = 2;
+          flags = true;
+        } else {
+          std::vector<double> arr(hrr.begin() + a.so, hrr.begin() + a.so + a.nrhs);
+          flags = refresh_restarts(trel, arr, a.bn, a.hdone);
+        }
+        if (flags)
+          SPD_CUDA(cudaMemcpyAsync(pl.dn(a), a.hdone.data(), a.nrhs * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+      }
+    if (switched || (changed_set && 3 * nactive <= 2 * merged_active)) {
+      build_merged(I, pl, M, s, precision != 0);
+      if (F) {
+        F.reset(new MergedF());
+        build_merged_f(I, *F, s);
+      }
       merged_active = nactive;
     }
     copy_launch(M.z_from_r, s);

@@ -72,6 +72,9 @@ _SIGS = {
     "pcg_solve_batched": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                           ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
+    "pcg_solve_batched_mixed": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
+                                ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
 }
 
 

@@ -4,7 +4,8 @@ Two forms share the admission policy.  Server.run gives every admitted request a
 slot and a CUDA stream of its own (one-request-at-a-time with one slot); Server.run_waves
 gathers the requests admitted while earlier waves are on the GPU into the next wave,
 served by the batched ABI (merged construction launches in the precision mode, lockstep
-PCG), with two waves overlapping on the device.
+PCG with the FP32 H^2 products merged over the wave), with two waves overlapping on the
+device.
 
 Requests (points, kernel, shift, HSS rank, one or more blocks of right-hand sides) arrive
 over time.  A request is admitted as soon as its arrival time has passed, a worker slot is
@@ -278,9 +279,11 @@ class GpuExecutor:
 class WaveExecutor:
     """Runs a wave of requests through the batched C ABI on one CUDA stream per wave slot:
     spdhss_build_batched (H^2, SPD-HSS in the given precision mode, ULV, with the batched
-    kernel launches of all requests of the wave merged step by step), then
-    pcg_solve_batched for every block of right-hand sides (the iterations of all requests
-    in lockstep).  Every request's result equals the one it gets alone (a wave of one)."""
+    kernel launches of all requests of the wave merged step by step), then, for every block
+    of right-hand sides, the iterations of all requests in lockstep: in the precision mode
+    (precision >= 1) pcg_solve_batched_mixed (FP32 H^2 products, FP64 preconditioner and
+    residuals; blocks of at most 16 columns), else pcg_solve_batched.  Every request's
+    result equals the one it gets alone (a wave of one)."""
 
     def __init__(self, slots: int, precision: int = 1):
         import torch
@@ -305,10 +308,13 @@ class WaveExecutor:
             nblk = max(len(r.rhs) for r in reqs)
             for j in range(nblk):
                 ks = [k for k, r in enumerate(reqs) if j < len(r.rhs)]
+                mixed = self.precision > 0 and all(
+                    np.asarray(reqs[k].rhs[j]).reshape(reqs[k].unknowns, -1).shape[1] <= 16
+                    for k in ks)
                 X, its, rrs, st = api.pcg_solve_batched(
                     [built[k][0] for k in ks], [built[k][2] for k in ks],
                     [np.asfortranarray(reqs[k].rhs[j]) for k in ks], tol=reqs[ks[0]].relres,
-                    maxit=reqs[ks[0]].maxit, stream=s)
+                    maxit=reqs[ks[0]].maxit, stream=s, mixed=mixed)
                 for k, x, it, rr in zip(ks, X, its, rrs):
                     outs[k][0].append(x.cpu().numpy())
                     outs[k][1].append(it)
