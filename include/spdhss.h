@@ -318,7 +318,17 @@ spdhss_status spdhss_gemm_f32(int M, int N, int K, const float* A, int64_t lda, 
  *   solves, recurrences, FP64 true residuals (every 50 iterations and at convergence) and
  *   the convergence test are those of pcg_solve_mixed.  Arguments as pcg_solve_batched,
  *   nrhs[i] in [1, 16]; every instance's X, iterations and residuals are bit-identical to
- *   its pcg_solve_mixed call. */
+ *   its pcg_solve_mixed call.
+ * pcg_solve_batched_ex: pcg_solve_batched (precision 0) or pcg_solve_batched_mixed
+ *   (precision 1) that reports every instance as soon as it has finished, for callers that
+ *   return results one by one (a serving loop): when instance i stops iterating (every
+ *   column converged), its X[i], iters_out[i], relres_out[i] and status[i] are written,
+ *   `stream` is synchronized, and on_done(user, i, status of i) is called on the calling
+ *   thread, before the other instances continue; instances that run out of iterations are
+ *   reported at the end.  Results are bit-identical to the calls without the callback.  The
+ *   callback must not destroy any handle of the call (the remaining iterations may still
+ *   launch kernels over a finished instance's data) and must not call into the library on
+ *   `stream`.  on_done may be NULL. */
 spdhss_status spdhss_build_batched(int count, const double* const* points, const int64_t* n,
                                    const int* dim, const spdhss_kernel_desc* kernel,
                                    const int* leaf_size, const double* tol, const int* rank,
@@ -338,6 +348,13 @@ spdhss_status pcg_solve_batched_mixed(int count, const h2_handle* h2, const ulv_
                                       int maxit, int* const* iters_out,
                                       double* const* relres_out, void* stream,
                                       spdhss_status* status);
+typedef void (*spdhss_done_fn)(void* user, int instance, spdhss_status status);
+spdhss_status pcg_solve_batched_ex(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                   const double* const* B, double* const* X, const int* nrhs,
+                                   const int64_t* ld, double relres_tol, int maxit,
+                                   int* const* iters_out, double* const* relres_out,
+                                   void* stream, spdhss_status* status, int precision,
+                                   spdhss_done_fn on_done, void* user);
 /* Launches issued by the last batched call of the calling thread: merged[0] = launches of
  * the batched kernels after merging, merged[1] = the hand-overs they replaced. */
 void spdhss_batched_stats(int64_t* merged);

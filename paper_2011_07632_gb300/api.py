@@ -312,11 +312,14 @@ def build_batched(instances, stream=None):
 
 
 def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, stream=None,
-                      mixed: bool = False):
+                      mixed: bool = False, on_done=None):
     """pcg_solve for every instance with the iterations in lockstep (pcg_solve_batched;
     mixed=True: pcg_solve_mixed per instance, pcg_solve_batched_mixed, at most 16 columns).
     Bs: device tensors or arrays (n_i, nrhs_i).  Returns (list of X (n_i, nrhs_i) device
-    tensors, list of iteration arrays, list of relres arrays, per-instance status codes)."""
+    tensors, list of iteration arrays, list of relres arrays, per-instance status codes).
+    on_done(i, status, X_i, iters_i, relres_i), if given, is called as soon as instance i
+    has finished (pcg_solve_batched_ex), with its final results; it must not destroy the
+    instances' handles."""
     m = len(h2s)
     Bc = [_colmajor(b) for b in Bs]
     Xc = [torch.empty_like(b) for b in Bc]
@@ -326,13 +329,19 @@ def pcg_solve_batched(h2s, ulvs, Bs, tol: float = 1e-6, maxit: int = 3000, strea
     P = ctypes.c_void_p * m
     ld = np.array([h.n for h in h2s], np.int64)
     st = (ctypes.c_int * m)()
-    fn = N.lib().pcg_solve_batched_mixed if mixed else N.lib().pcg_solve_batched
-    rc = fn(
-        m, P(*[h._h.value for h in h2s]), P(*[u._h.value for u in ulvs]),
-        P(*[b.data_ptr() for b in Bc]), P(*[x.data_ptr() for x in Xc]),
-        (ctypes.c_int * m)(*nrhs), _i64(ld), float(tol), int(maxit),
-        P(*[ctypes.addressof(a) for a in its]), P(*[ctypes.addressof(a) for a in rrs]),
-        _stream(stream), st)
+    args = (m, P(*[h._h.value for h in h2s]), P(*[u._h.value for u in ulvs]),
+            P(*[b.data_ptr() for b in Bc]), P(*[x.data_ptr() for x in Xc]),
+            (ctypes.c_int * m)(*nrhs), _i64(ld), float(tol), int(maxit),
+            P(*[ctypes.addressof(a) for a in its]), P(*[ctypes.addressof(a) for a in rrs]),
+            _stream(stream), st)
+    if on_done is not None:
+        def _done(_user, k, status):
+            on_done(k, int(status), Xc[k].t(), np.array(list(its[k])), np.array(list(rrs[k])))
+        cb = N.DONE_FN(_done)   # referenced until the call returns
+        rc = N.lib().pcg_solve_batched_ex(*args, 1 if mixed else 0, cb, None)
+    else:
+        fn = N.lib().pcg_solve_batched_mixed if mixed else N.lib().pcg_solve_batched
+        rc = fn(*args)
     if any(v not in (N.OK, N.NO_CONVERGENCE) for v in st) or (
             rc != N.OK and all(v == N.OK for v in st)):
         N.check(rc)

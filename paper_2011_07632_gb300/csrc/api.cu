@@ -499,7 +499,7 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
                       const double* const* B, double* const* X, const int* nrhs,
                       const int64_t* ld, double tol, int maxit, int* const* iters_out,
                       double* const* relres_out, spdhss_status* status, cudaStream_t s,
-                      int precision);
+                      int precision, spdhss_done_fn on_done, void* user);
 }
 
 extern "C" {
@@ -696,7 +696,8 @@ static spdhss_status pcg_batched_entry(const char* where, int precision, int cou
                                        const int* nrhs, const int64_t* ld, double relres_tol,
                                        int maxit, int* const* iters_out,
                                        double* const* relres_out, void* stream,
-                                       spdhss_status* status) {
+                                       spdhss_status* status, spdhss_done_fn on_done = nullptr,
+                                       void* user = nullptr) {
   std::vector<spdhss_status> st;
   std::vector<std::string> msg;
   cudaStream_t s = (cudaStream_t)stream;
@@ -718,7 +719,7 @@ static spdhss_status pcg_batched_entry(const char* where, int precision, int cou
     std::vector<spdhss_h2_s*> hv(h2, h2 + count);
     std::vector<spdhss_ulv_s*> uv(ulv, ulv + count);
     pcg_batched_impl(count, hv.data(), uv.data(), B, X, nrhs, ld, relres_tol, maxit, iters_out,
-                     relres_out, st.data(), s, precision);
+                     relres_out, st.data(), s, precision, on_done, user);
     for (int i = 0; i < count; ++i)
       if (st[i] == SPDHSS_NO_CONVERGENCE) msg[i] = "some column missed the tolerance";
   });
@@ -743,6 +744,21 @@ spdhss_status pcg_solve_batched_mixed(int count, const h2_handle* h2, const ulv_
                                       spdhss_status* status) {
   return pcg_batched_entry("pcg_solve_batched_mixed", 1, count, h2, ulv, B, X, nrhs, ld,
                            relres_tol, maxit, iters_out, relres_out, stream, status);
+}
+
+spdhss_status pcg_solve_batched_ex(int count, const h2_handle* h2, const ulv_handle* ulv,
+                                   const double* const* B, double* const* X, const int* nrhs,
+                                   const int64_t* ld, double relres_tol, int maxit,
+                                   int* const* iters_out, double* const* relres_out,
+                                   void* stream, spdhss_status* status, int precision,
+                                   spdhss_done_fn on_done, void* user) {
+  if (precision != 0 && precision != 1) {
+    set_last_error("pcg_solve_batched_ex: precision must be 0 or 1");
+    return SPDHSS_EINVAL;
+  }
+  return pcg_batched_entry("pcg_solve_batched_ex", precision, count, h2, ulv, B, X, nrhs, ld,
+                           relres_tol, maxit, iters_out, relres_out, stream, status, on_done,
+                           user);
 }
 
 void spdhss_batched_stats(int64_t* merged) {

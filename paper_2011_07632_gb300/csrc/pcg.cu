@@ -897,7 +897,7 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
                       const double* const* B, double* const* X, const int* nrhs,
                       const int64_t* ld, double tol, int maxit, int* const* iters_out,
                       double* const* relres_out, spdhss_status* status, cudaStream_t s,
-                      int precision) {
+                      int precision, spdhss_done_fn on_done, void* user) {
   std::vector<Inst> I(count);
   Pools pl;
   for (int k = 0; k < count; ++k) {
@@ -982,6 +982,40 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
     rel.resize(a.nrhs);
     for (int c = 0; c < a.nrhs; ++c) rel[c] = std::sqrt(std::max(h[c], 0.0)) / a.bn[c];
   };
+  // the outputs of instance k: its final true residuals, iterations and solution; then, with
+  // a callback, the stream is synchronized and the caller told
+  std::vector<char> finished(count, 0);
+  auto finish = [&](int k) {
+    Inst& a = I[k];
+    std::vector<double> trel;
+    true_residual(a, trel);
+    bool conv = true;
+    for (int c = 0; c < a.nrhs; ++c) {
+      if (iters_out && iters_out[k]) iters_out[k][c] = a.hit[c];
+      if (relres_out && relres_out[k]) relres_out[k][c] = trel[c];
+      conv = conv && trel[c] <= tol;
+    }
+    const int64_t* perm = a.h2->td.perm.p;
+    if (!is_device_pointer(a.X)) {
+      DevBuf<double> tmp((size_t)a.ld * a.nrhs);
+      if (a.ld > a.n)
+        SPD_CUDA(cudaMemcpyAsync(tmp.p, a.X, (size_t)a.ld * a.nrhs * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+      permute_from_sorted(a.x.p, tmp.p, a.ld, a.n, a.nrhs, perm, s);
+      SPD_CUDA(cudaMemcpyAsync(a.X, tmp.p, (size_t)a.ld * a.nrhs * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      SPD_CUDA(cudaStreamSynchronize(s));
+    } else {
+      permute_from_sorted(a.x.p, a.X, a.ld, a.n, a.nrhs, perm, s);
+    }
+    const spdhss_status st = conv ? SPDHSS_OK : SPDHSS_NO_CONVERGENCE;
+    if (status) status[k] = st;
+    finished[k] = 1;
+    if (on_done) {
+      SPD_CUDA(cudaStreamSynchronize(s));
+      on_done(user, k, st);
+    }
+  };
   Merged M;
   build_merged(I, pl, M, s, precision != 0);
   std::unique_ptr<MergedF> F;
@@ -1005,7 +1039,8 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
                              cudaMemcpyDeviceToHost, s));
     SPD_CUDA(cudaStreamSynchronize(s));
     bool changed_set = false;
-    for (auto& a : I) {
+    for (int k = 0; k < count; ++k) {
+      Inst& a = I[k];
       if (!a.active) continue;
       bool any_pass = false;
       for (int c = 0; c < a.nrhs; ++c) {
@@ -1035,7 +1070,12 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
       }
       bool all = true;
       for (int c = 0; c < a.nrhs; ++c) all = all && a.hdone[c] == 1;
-      if (all) { a.active = false; --nactive; changed_set = true; }
+      if (all) {
+        a.active = false;
+        --nactive;
+        changed_set = true;
+        if (on_done) finish(k);   // x no longer changes: its outputs now, as at the end
+      }
     }
     if (nactive == 0) break;
     // mixed precision: every 50 iterations the recursive residual of each instance still
@@ -1086,32 +1126,9 @@ void pcg_batched_impl(int count, spdhss_h2_s* const* h2, spdhss_ulv_s* const* ul
                                  cudaMemcpyHostToDevice, s));
     }
   }
-  // final true residuals, outputs
-  for (int k = 0; k < count; ++k) {
-    Inst& a = I[k];
-    std::vector<double> trel;
-    true_residual(a, trel);
-    bool conv = true;
-    for (int c = 0; c < a.nrhs; ++c) {
-      if (iters_out && iters_out[k]) iters_out[k][c] = a.hit[c];
-      if (relres_out && relres_out[k]) relres_out[k][c] = trel[c];
-      conv = conv && trel[c] <= tol;
-    }
-    const int64_t* perm = a.h2->td.perm.p;
-    if (!is_device_pointer(a.X)) {
-      DevBuf<double> tmp((size_t)a.ld * a.nrhs);
-      if (a.ld > a.n)
-        SPD_CUDA(cudaMemcpyAsync(tmp.p, a.X, (size_t)a.ld * a.nrhs * sizeof(double),
-                                 cudaMemcpyHostToDevice, s));
-      permute_from_sorted(a.x.p, tmp.p, a.ld, a.n, a.nrhs, perm, s);
-      SPD_CUDA(cudaMemcpyAsync(a.X, tmp.p, (size_t)a.ld * a.nrhs * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
-      SPD_CUDA(cudaStreamSynchronize(s));
-    } else {
-      permute_from_sorted(a.x.p, a.X, a.ld, a.n, a.nrhs, perm, s);
-    }
-    if (status) status[k] = conv ? SPDHSS_OK : SPDHSS_NO_CONVERGENCE;
-  }
+  // final true residuals, outputs (of the instances not finished early)
+  for (int k = 0; k < count; ++k)
+    if (!finished[k]) finish(k);
   SPD_CUDA(cudaStreamSynchronize(s));
 }
 

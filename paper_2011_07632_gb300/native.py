@@ -36,6 +36,9 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 _PI64 = ctypes.POINTER(ctypes.c_int64)
 
+# void (*)(void* user, int instance, spdhss_status status): pcg_solve_batched_ex's callback
+DONE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
+
 _SIGS = {
     "h2_build": [_P, _I64, _I, KernelDesc, _I, _D, _P, ctypes.POINTER(_P)],
     "h2_matmul": [_P, _P, _P, _I, _I64, _P],
@@ -75,6 +78,10 @@ _SIGS = {
     "pcg_solve_batched_mixed": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                 ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I)],
+    "pcg_solve_batched_ex": [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                             ctypes.POINTER(_P), ctypes.POINTER(_I), _PI64, _D, _I,
+                             ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_I), _I,
+                             DONE_FN, _P],
 }
 
 

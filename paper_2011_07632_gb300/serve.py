@@ -168,7 +168,9 @@ class Server:
         `wave_slots` wave workers takes every queued request (up to `max_wave`) as one wave
         the moment it is free, so that requests arriving while waves are on the GPU join
         the next wave and two waves overlap on the device.  `execute_wave(requests, slot)`
-        returns one (x blocks, iteration arrays, relres arrays) per request."""
+        returns one (x blocks, iteration arrays, relres arrays[, finish time]) per request;
+        a finish time (on this server's clock) makes that the request's finish, else the
+        wave's return is.  Memory is released when the wave returns."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         t0 = self.clock()
         cv = threading.Condition()
@@ -193,8 +195,12 @@ class Server:
                 done = self.clock() - t0
                 with cv:
                     for k, (req, fp, admitted) in enumerate(wave):
-                        xs, its, rrs = outs[k] if outs is not None else ([], [], [])
-                        results.append(Result(req.rid, xs, its, rrs, req.arrival, admitted, done,
+                        out = outs[k] if outs is not None else ([], [], [])
+                        xs, its, rrs = out[:3]
+                        fin = done
+                        if len(out) > 3 and out[3] is not None:
+                            fin = min(done, out[3] - t0)
+                        results.append(Result(req.rid, xs, its, rrs, req.arrival, admitted, fin,
                                               fp, err))
                         state["in_use"] -= fp
                     state["busy"] -= 1
@@ -283,12 +289,17 @@ class WaveExecutor:
     of right-hand sides, the iterations of all requests in lockstep: in the precision mode
     (precision >= 1) pcg_solve_batched_mixed (FP32 H^2 products, FP64 preconditioner and
     residuals; blocks of at most 16 columns), else pcg_solve_batched.  Every request's
-    result equals the one it gets alone (a wave of one)."""
+    result equals the one it gets alone (a wave of one).  A request is finished when its
+    last block's solution has reached the host, which the batched solve reports per request
+    as soon as that request has converged (pcg_solve_batched_ex), not when the wave's
+    slowest one has; its finish time (on `clock`, the server's clock) is returned with it.
+    The wave's handles are released together at its end."""
 
-    def __init__(self, slots: int, precision: int = 1):
+    def __init__(self, slots: int, precision: int = 1, clock: Callable[[], float] = time.perf_counter):
         import torch
         self.torch = torch
         self.precision = int(precision)
+        self.clock = clock
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
 
     def __call__(self, reqs: Sequence[Request], slot: int):
@@ -300,6 +311,7 @@ class WaveExecutor:
                       oversample=r.oversample, seed=r.seed, precision=self.precision)
                  for r in reqs]
         outs = [([], [], []) for _ in reqs]
+        fin = [None] * len(reqs)
         with torch.cuda.stream(s):
             built, status, _ = api.build_batched(insts, stream=s)
             bad = [k for k, v in enumerate(status) if v != 0]
@@ -311,19 +323,29 @@ class WaveExecutor:
                 mixed = self.precision > 0 and all(
                     np.asarray(reqs[k].rhs[j]).reshape(reqs[k].unknowns, -1).shape[1] <= 16
                     for k in ks)
+                got = {}
+
+                def done(i, status, x, it, rr, ks=ks, j=j):
+                    k = ks[i]
+                    got[k] = x.cpu().numpy()
+                    if j == len(reqs[k].rhs) - 1:
+                        fin[k] = self.clock()
+
                 X, its, rrs, st = api.pcg_solve_batched(
                     [built[k][0] for k in ks], [built[k][2] for k in ks],
                     [np.asfortranarray(reqs[k].rhs[j]) for k in ks], tol=reqs[ks[0]].relres,
-                    maxit=reqs[ks[0]].maxit, stream=s, mixed=mixed)
+                    maxit=reqs[ks[0]].maxit, stream=s, mixed=mixed, on_done=done)
                 for k, x, it, rr in zip(ks, X, its, rrs):
-                    outs[k][0].append(x.cpu().numpy())
+                    outs[k][0].append(got[k] if k in got else x.cpu().numpy())
                     outs[k][1].append(it)
                     outs[k][2].append(rr)
+                    if fin[k] is None and j == len(reqs[k].rhs) - 1:
+                        fin[k] = self.clock()
             for h, hs, u in built:
                 u.close()
                 hs.close()
                 h.close()
-        return outs
+        return [(xs, its, rrs, fin[k]) for k, (xs, its, rrs) in enumerate(outs)]
 
 
 def synthetic_stream(count: int, rate: float, n_lo: int, n_hi: int, seed: int = 1,

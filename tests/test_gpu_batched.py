@@ -1,5 +1,5 @@
 """Batched level sweep over independent instances (spdhss_build_batched, pcg_solve_batched,
-pcg_solve_batched_mixed):
+pcg_solve_batched_mixed, pcg_solve_batched_ex):
 every instance's results are bit-identical to its one-instance build and solve, instances
 inside a batch match the oracle, the launches are merged, and a failing instance leaves the
 others intact."""
@@ -109,6 +109,33 @@ def test_mixed_batched_pcg_is_bit_identical_to_single_mixed_solves(precision):
         assert np.array_equal(rr, rr1)
         assert np.array_equal(x.cpu().numpy(), x1.cpu().numpy())
         assert np.all(rr <= 1e-6)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batched_pcg_reports_each_instance_when_it_finishes(mixed):
+    """pcg_solve_batched_ex: every instance reported once, in the order its iterations ended
+    (non-decreasing counts), with the results of the call without the callback."""
+    api = need_gpu()
+    insts = _instances(6, seed=10)
+    built, status, _ = api.build_batched(insts)
+    assert status == [native.OK] * len(insts)
+    Bs = [inputs.rhs(i["points"].shape[0], 1 + (k % 4), 90 + k) for k, i in enumerate(insts)]
+    hs, us = [b[0] for b in built], [b[2] for b in built]
+    X0, its0, rrs0, st0 = api.pcg_solve_batched(hs, us, Bs, tol=1e-6, mixed=mixed)
+    seen = []
+
+    def done(k, status, x, it, rr):
+        seen.append((k, status, x.cpu().numpy(), it, rr))
+
+    X1, its1, rrs1, st1 = api.pcg_solve_batched(hs, us, Bs, tol=1e-6, mixed=mixed, on_done=done)
+    assert st1 == st0 == [native.OK] * len(insts)
+    assert sorted(k for k, *_ in seen) == list(range(len(insts)))
+    ends = [int(np.max(it)) for _, _, _, it, _ in seen]
+    assert ends == sorted(ends)
+    for k, status, x, it, rr in seen:
+        assert status == native.OK
+        assert np.array_equal(x, X0[k].cpu().numpy()) and np.array_equal(x, X1[k].cpu().numpy())
+        assert np.array_equal(it, its0[k]) and np.array_equal(rr, rrs0[k])
 
 
 def test_mixed_pcg_converges_on_ill_conditioned_instances():

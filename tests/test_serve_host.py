@@ -139,3 +139,26 @@ def test_failed_wave_frees_its_memory():
     res, st = srv.run_waves(_reqs(8, gap=0.01), execute_wave, wave_slots=1, max_wave=4)
     assert st["completed"] + st["failed"] == 8 and st["failed"] >= 1
     assert all(r.error is None for r in res if r.rid >= 4)
+
+
+def test_wave_requests_finish_at_their_own_finish_times():
+    """An executor that reports a finish time per request (the batched solve's per-instance
+    completion) gives each request that finish, not the wave's return; memory is still
+    released when the wave returns."""
+    def execute_wave(reqs, slot):
+        t = []
+        for k, r in enumerate(reqs):
+            time.sleep(0.01)
+            t.append(time.perf_counter())
+        time.sleep(0.05)
+        return [([np.zeros((r.n, 1))], [np.array([1])], [np.array([0.0])], t[k])
+                for k, r in enumerate(reqs)]
+
+    srv = serve.Server(None, hbm_budget=10**12, footprint=lambda r: 10)
+    reqs = [serve.Request(**{**r.__dict__, "arrival": 0.0}) for r in _reqs(4)]
+    res, st = srv.run_waves(reqs, execute_wave, wave_slots=1, max_wave=4)
+    assert st["completed"] == 4
+    fin = [r.finished for r in sorted(res, key=lambda r: r.rid)]
+    assert fin == sorted(fin) and fin[-1] - fin[0] >= 0.025
+    assert st["wall_s"] - fin[-1] >= 0.04       # the wave returned later
+    assert srv.trace[-1][1] == 0
