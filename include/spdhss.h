@@ -258,10 +258,15 @@ spdhss_status pcg_solve(h2_handle h2, ulv_handle ulv, const double* B, double* X
  * (made on the first mixed call and kept in the handle), FP32 near-field kernel entries and
  * FP32 accumulation; X and Y are FP64.  Relative error ~1e-6.  nrhs in [1, 16].
  * pcg_solve_mixed: pcg_solve whose products with A inside the iteration are the FP32
- * product; the ULV preconditioner, the recurrences and the residuals stay FP64, the
- * recursive residual is replaced by the FP64 true residual every 50 iterations, and
- * convergence is declared on the FP64 true residual.  Arguments as pcg_solve, nrhs in
- * [1, 16]. */
+ * product; the ULV preconditioner, the recurrences and the residuals stay FP64, and
+ * convergence is declared on the FP64 true residual.  Every 50 iterations the recursive
+ * residual is replaced by the FP64 true residual; a column whose true residual is above
+ * twice its recursive one also restarts its direction (the solve then proceeds as
+ * iterative refinement with FP32 inner iterations), and when a block of 50 iterations has
+ * lowered some column's true residual by less than 10% the remaining iterations use the
+ * FP64 product (all columns restarting): kernel systems whose solution is dominated by
+ * the smallest eigenvalues put the FP32 product's error close to the residual itself.
+ * Arguments as pcg_solve, nrhs in [1, 16]. */
 spdhss_status h2_matmul_mixed(h2_handle h2, const double* X, double* Y, int nrhs, int64_t ld,
                               void* stream);
 spdhss_status pcg_solve_mixed(h2_handle h2, ulv_handle ulv, const double* B, double* X,
