@@ -859,6 +859,7 @@ void build_merged_f(const std::vector<Inst>& I, MergedF& F, cudaStream_t s) {
       m->probs.push_back(p);
     }
   }
+  SPD_REQUIRE(F.to_f.size() <= 65535, "mixed batched PCG: at most 65535 instances per call");
   for (auto& st : F.sym)
     for (auto& kv : st) kv.second->upload(s);
   for (auto& u : F.sum)
