@@ -25,8 +25,11 @@ bool tuning_enabled() {
 int tuned_variant(const std::string& key, const std::vector<int>& cands, int fallback,
                   const std::function<double(int)>& time_ms) {
   if (!tuning_enabled() || cands.size() < 2) return fallback;
-  int dev = 0;
-  SPD_CUDA(cudaGetDevice(&dev));
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {   // no device (a host-only caller): one cache
+    cudaGetLastError();
+    dev = -1;
+  }
   const std::string k = "dev" + std::to_string(dev) + " " + key;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(k);
